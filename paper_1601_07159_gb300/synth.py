@@ -1,0 +1,176 @@
+"""Seeded synthetic inputs: orbitals and target vectors on a periodic grid.
+
+This module builds *inputs* only. It holds none of the exchange / ACE
+arithmetic, imports nothing else from this package and nothing from the
+oracle, so the oracle (test infrastructure) and the CUDA path can both be fed
+from it without sharing method code.
+
+Workloads are shaped like the silicon runs of Sec. 4 (Si8/Si64/Si216/Si512,
+Gamma-point, plane-wave basis):
+
+* cubic cell of edge ``L`` (bohr) sampled on an ``n^3`` grid, x fastest;
+* reciprocal vectors G = 2*pi*m/L with the wrapped FFT index m;
+* orbital coefficients c(G) = (a + i b)/sqrt(2) * exp(-|G|^2 / (2 E_cut)) on
+  the sphere |G|^2/2 <= E_cut (E_cut = 10 Ha), zero outside, a, b ~ N(0, 1);
+* real Gamma-point orbitals enforce c(-G) = conj c(G) and a real c(0);
+* phi(r) = sum_G c(G) exp(i G.r), then a QR factorisation of sqrt(dV)*Phi
+  with diag(R) > 0 makes the columns orthonormal in the discrete inner
+  product <f, g> = dV sum_r conj(f) g (the orthonormality of Eq. HF);
+* target vectors psi use the same recipe with seed + 500, normalised but not
+  orthogonalised against Phi.
+
+Arrays are numpy, shape (count, n, n, n) = [orbital][z][y][x], FP64
+(complex128, or float64 for real Gamma-point systems).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+ECUT_HA = 10.0
+SEED_BASE = 1601071590
+SHAPE_SEED_BATCHED = 1601074590
+
+
+@dataclasses.dataclass(frozen=True)
+class System:
+    """Shape of one periodic system (one cubic cell)."""
+
+    n: int                 # grid points per edge
+    L: float               # cell edge (bohr)
+    n_occ: int             # exchange orbitals N
+    n_bands: int           # target vectors psi
+    real: bool = False     # real Gamma-point orbitals
+    kernel: str = "bare"   # "bare" or "erfc"
+    omega: float = 0.0     # screening parameter (bohr^-1) for "erfc"
+
+    @property
+    def ng(self) -> int:
+        return self.n ** 3
+
+    @property
+    def volume(self) -> float:
+        return self.L ** 3
+
+    @property
+    def dv(self) -> float:
+        return self.volume / self.ng
+
+
+# The five workloads, sizes per the silicon runs of Sec. 4 (Eq. numbering of
+# the paper is used in docstrings elsewhere).
+GAMMA_24 = System(n=24, L=10.0, n_occ=8, n_bands=16, real=True, kernel="bare")
+SI64_48 = System(n=48, L=20.5, n_occ=128, n_bands=192, kernel="erfc", omega=0.106)
+DIFF_64 = System(n=64, L=20.5 * 64 / 48, n_occ=256, n_bands=384, kernel="bare")
+SI512_96 = System(n=96, L=41.0, n_occ=1024, n_bands=1536, kernel="erfc", omega=0.106)
+
+WORKLOADS = {
+    "gamma24_n8_fp64": (1, GAMMA_24),
+    "si64_48cube_n128": (2, SI64_48),
+    "diff_64cube_n256": (4, DIFF_64),
+    "si512_96cube_n1024": (5, SI512_96),
+}
+
+
+def batched_systems(count: int = 64, seed: int = SHAPE_SEED_BATCHED):
+    """Uneven batch: edges uniform in {32,36,40,48,64}, N uniform in [16,128],
+    bands = floor(1.5 N), L scaled so the grid spacing matches the 48^3 cell."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    edges = np.array([32, 36, 40, 48, 64])
+    out = []
+    for _ in range(count):
+        n = int(edges[rng.integers(0, len(edges))])
+        nocc = int(rng.integers(16, 129))
+        out.append(System(n=n, L=20.5 * n / 48, n_occ=nocc,
+                          n_bands=(3 * nocc) // 2, kernel="bare"))
+    return out
+
+
+def seed_for(config_index: int, system_index: int = 0) -> int:
+    return SEED_BASE + 1000 * config_index + system_index
+
+
+def wavevector_sq(n: int, L: float) -> np.ndarray:
+    """|G|^2 on the wrapped n^3 index grid, array [z][y][x]."""
+    m = np.fft.fftfreq(n, d=1.0 / n)
+    g = 2.0 * math.pi * m / L
+    gz, gy, gx = np.meshgrid(g, g, g, indexing="ij")
+    return gx * gx + gy * gy + gz * gz
+
+
+def _coefficients(rng, sysm: System, count: int, ecut: float) -> np.ndarray:
+    n = sysm.n
+    g2 = wavevector_sq(n, sysm.L)
+    sphere = 0.5 * g2 <= ecut
+    decay = np.where(sphere, np.exp(-g2 / (2.0 * ecut)), 0.0)
+    a = rng.standard_normal((count, n, n, n))
+    b = rng.standard_normal((count, n, n, n))
+    c = (a + 1j * b) / math.sqrt(2.0) * decay
+    if sysm.real:
+        # Hermitian symmetry c(-G) = conj c(G): average with the mirrored conjugate.
+        idx = (-np.arange(n)) % n
+        mirror = np.conj(c[:, idx][:, :, idx][:, :, :, idx])
+        c = 0.5 * (c + mirror)
+        c[:, 0, 0, 0] = c[:, 0, 0, 0].real
+    return c
+
+
+def _to_real_space(c: np.ndarray) -> np.ndarray:
+    ng = c.shape[1] * c.shape[2] * c.shape[3]
+    return np.fft.ifftn(c, axes=(1, 2, 3)) * ng
+
+
+def orbitals(sysm: System, seed: int, ecut: float = ECUT_HA) -> np.ndarray:
+    """Orthonormal exchange orbitals Phi, shape (N, n, n, n)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    phi = _to_real_space(_coefficients(rng, sysm, sysm.n_occ, ecut))
+    if sysm.real:
+        phi = phi.real
+    a = math.sqrt(sysm.dv) * phi.reshape(sysm.n_occ, -1).T
+    q, r = np.linalg.qr(a)
+    sgn = np.sign(np.real(np.diag(r)))
+    sgn[sgn == 0] = 1.0
+    q = q * sgn[None, :]
+    out = (q.T / math.sqrt(sysm.dv)).reshape(sysm.n_occ, sysm.n, sysm.n, sysm.n)
+    return np.ascontiguousarray(out)
+
+
+def targets(sysm: System, seed: int, count: int | None = None,
+            ecut: float = ECUT_HA) -> np.ndarray:
+    """Target vectors psi (bands), each normalised, shape (count, n, n, n)."""
+    count = sysm.n_bands if count is None else count
+    rng = np.random.Generator(np.random.PCG64(seed + 500))
+    psi = _to_real_space(_coefficients(rng, sysm, count, ecut))
+    if sysm.real:
+        psi = psi.real
+    nrm = np.sqrt(sysm.dv * np.sum(np.abs(psi) ** 2, axis=(1, 2, 3)))
+    return np.ascontiguousarray(psi / nrm[:, None, None, None])
+
+
+def plane_wave_orbitals(n: int, L: float, mvecs) -> np.ndarray:
+    """phi_i(r) = exp(i k_i.r)/sqrt(Omega) for integer wavevector indices m_i
+    (k_i = 2*pi*m_i/L), shape (len(mvecs), n, n, n)."""
+    x = np.arange(n) * (L / n)
+    z3, y3, x3 = np.meshgrid(x, x, x, indexing="ij")
+    out = []
+    for (mx, my, mz) in mvecs:
+        k = 2.0 * math.pi / L
+        out.append(np.exp(1j * k * (mx * x3 + my * y3 + mz * z3)))
+    return np.array(out) / math.sqrt(L ** 3)
+
+
+def random_unitary(count: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed))
+    a = rng.standard_normal((count, count)) + 1j * rng.standard_normal((count, count))
+    q, r = np.linalg.qr(a)
+    return q * (np.diag(r) / np.abs(np.diag(r)))[None, :]
+
+
+def directions(shape, count: int, seed: int, dv: float) -> np.ndarray:
+    """Seeded complex Gaussian directions D normalised to dV ||D||^2 = 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = rng.standard_normal((count,) + tuple(shape)) + 1j * rng.standard_normal((count,) + tuple(shape))
+    nrm = np.sqrt(dv * np.sum(np.abs(d) ** 2, axis=tuple(range(1, d.ndim))))
+    return d / nrm.reshape((count,) + (1,) * len(shape))
