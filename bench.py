@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the ACE hot path on one GB300 (or N independent replicas).
+
+A step is one pass of the whole path on the Si64-like 48^3 workload (L = 20.5
+bohr, N = 128 orbitals, 192 bands, complex, screened kernel omega = 0.106):
+ace_build (W over the 8256 unique pair FFT-Poisson solves, M = dV Phi^* W,
+FP64 Cholesky and L^{-1}, Xi = W L^{-*}, E_x) followed by ace_apply on the 192
+bands. The metric is unique pair FFT-Poisson solves per second of whole steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (its own system): the
+work is partitioned into independent problems, no data-path collective;
+value = pairs over all ranks / max-over-ranks time ("scaling": "weak").
+--impl reference times the FP64 CPU oracle on this host (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1601_07159_gb300 import synth  # noqa: E402
+
+WORKLOAD = "si64_48cube_n128"
+METRIC = "pair FFT-Poisson solves/s"
+UNIT = "pair-solves/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def workload_config(s):
+    return {"workload": WORKLOAD, "grid": f"{s.n}^3", "L_bohr": s.L, "n_occ": s.n_occ,
+            "n_bands": s.n_bands, "kernel": f"erfc omega={s.omega}" if s.kernel == "erfc" else "bare",
+            "orbitals": "seeded Gaussian-decaying plane waves |G|^2/2<=10 Ha, QR-orthonormal",
+            "precision": "fp32 pair/FFT path and GEMMs, fp64 Cholesky and L^-1",
+            "l2": "working set > L2 every step (no flush needed)"}
+
+
+def unique_pairs(n):
+    return n * (n + 1) // 2
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = max(mx, float(r[1]))
+                for k, nm in enumerate(names):
+                    if r[4 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def physical_gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        items = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(items) and items[local_rank].isdigit():
+            return int(items[local_rank])
+    return local_rank
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_step(phi, psi, kern, dv, cols):
+    """Time the FP64 oracle on a bounded sample of one step: `cols` columns of W
+    (each N ordered pair solves, Eq. applyVX2), scaled to all N columns, plus the
+    dense part (M, Cholesky, Xi, apply) at full size. The dense part is timed on
+    the stand-in W = -Phi (same shapes, -M = I positive definite), since its cost
+    does not depend on the values. Returns (estimated seconds per step, detail)."""
+    import oracle
+    n_occ = phi.shape[0]
+    t0 = time.perf_counter()
+    oracle.exchange_apply(phi, phi[cols], kern)
+    t_cols = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    w_stand = -phi
+    M = oracle.overlap_M(phi, w_stand, dv)
+    Lc = oracle.cholesky_neg(M)
+    xi = oracle.xi_from(w_stand, Lc)
+    t_dense = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.ace_apply(xi, psi, dv)
+    t_apply = time.perf_counter() - t0
+    t_w = t_cols * n_occ / len(cols)
+    return t_w + t_dense + t_apply, {"t_cols_s": t_cols, "t_w_est_s": t_w, "t_dense_s": t_dense,
+                                     "t_apply_s": t_apply}
+
+
+def make_inputs(s, rank=0):
+    seed = synth.seed_for(2, rank)
+    phi = synth.orbitals(s, seed)
+    psi = synth.targets(s, seed)
+    return phi, psi
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    s = synth.SI64_48
+    phi, psi = make_inputs(s)
+    kern = oracle.coulomb_kernel((s.n,) * 3, (s.L,) * 3, s.kernel, s.omega)
+    cols = [0]
+    for _ in range(args.warmup):
+        oracle_step(phi, psi, kern, s.dv, cols)
+    total_t, total_pairs = 0.0, 0
+    for k in range(args.steps):
+        t, _ = oracle_step(phi, psi, kern, s.dv, [(37 * k) % s.n_occ])
+        total_t += t
+        total_pairs += unique_pairs(s.n_occ)
+    value = total_pairs / total_t
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(s),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: 1 of 128 W columns (128 ordered FFT-Poisson solves) "
+                                       "scaled x128, plus full-size M/Cholesky/Xi/apply"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1601_07159_gb300 import build_lib
+    if rank == 0 or world == 1:
+        build_lib.build()
+    if dist:
+        dist.barrier()
+    from paper_1601_07159_gb300 import ace
+
+    s = synth.SI64_48
+    phi, psi = make_inputs(s, rank)
+    plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega)
+    td = torch.complex64
+    phi_h = torch.from_numpy(phi).to(td).pin_memory()
+    psi_h = torch.from_numpy(psi).to(td).pin_memory()
+    phi_d = phi_h.cuda()
+    psi_d = psi_h.cuda()
+    xi_d = plan.empty(s.n_occ)
+    y_d = plan.empty(s.n_bands)
+    y_h = torch.empty(y_d.shape, dtype=td).pin_memory()
+    ex_h = torch.empty((), dtype=torch.float64).pin_memory()
+
+    def step():
+        out = plan.build(phi_d, want_w=False, want_m=False, xi=xi_d)
+        plan.apply(xi_d, psi_d, out=y_d)
+        return out["Ex"]
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    code, piv = plan.status()
+    if code != 0:
+        raise RuntimeError(f"ace_build status {code} (pivot {piv})")
+    torch.cuda.synchronize()
+
+    K = args.steps
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    batches_per_build = None
+    plan.profile_begin(max_events=5 * (K + 1) * 64)
+    clocks = ClockSampler(physical_gpu_index(local))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        plan.build(phi_d, want_w=False, want_m=False, xi=xi_d)
+        ev[k][1].record(stream)
+        plan.apply(xi_d, psi_d, out=y_d)
+        ev[k][2].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    prof = plan.profile_end()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    apply_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    pairs = unique_pairs(s.n_occ)
+    value = pairs * K * world / (elapsed_ms / 1e3)
+
+    # end to end through the public API: pinned host inputs -> device -> results back
+    Ke = max(3, K // 5)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(Ke):
+        phi_d.copy_(phi_h, non_blocking=True)
+        psi_d.copy_(psi_h, non_blocking=True)
+        ex_d = step()
+        y_h.copy_(y_d, non_blocking=True)
+        ex_h.copy_(ex_d, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = pairs * Ke * world / (e2e_ms / 1e3)
+    h2d = phi_h.numel() * phi_h.element_size() + psi_h.numel() * psi_h.element_size()
+    d2h = y_h.numel() * y_h.element_size() + 8
+
+    # roofline of the pair FFT-Poisson pipeline (passes A-D), per build
+    hbm, peak_kind = peaks()
+    ng = s.ng
+    alg_bytes = 32.0 * ng * pairs + 2.0 * s.n_occ * ng * 8
+    pair_ms = prof["pair_ms"] / K
+    achieved = alg_bytes / (pair_ms / 1e3) / 1e9
+    pass_alg = {"A": 8.0 * ng * pairs, "B": 16.0 * ng * pairs, "C": 16.0 * ng * pairs,
+                "D": 8.0 * ng * pairs + 2.0 * s.n_occ * ng * 8 * 2}
+    passes = {}
+    for k, ms in prof["pass_ms"].items():
+        per = ms / K
+        passes[k] = {"ms_per_build": per, "share": ms / max(prof["pair_ms"], 1e-12),
+                     "alg_GBps": pass_alg[k] / (per / 1e3) / 1e9 if per > 0 else None}
+
+    # plain-FP64 form of the same build (denominator of the mixed-vs-FP64 ratio)
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = ace.Plan(s.n, s.L, s.n_occ, dtype="c128", kernel=s.kernel, omega=s.omega)
+        phi64 = torch.from_numpy(phi).cuda()
+        xi64 = plan64.empty(s.n_occ)
+        plan64.build(phi64, want_w=False, want_m=False, xi=xi64)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for _ in range(2):
+            plan64.build(phi64, want_w=False, want_m=False, xi=xi64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_ms = f0.elapsed_time(f1) / 2
+        fp64 = {"fp64_ms_per_build": fp64_ms, "mixed_vs_fp64_build_speedup": fp64_ms / build_ms}
+        del plan64, phi64, xi64
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        kern = oracle.coulomb_kernel((s.n,) * 3, (s.L,) * 3, s.kernel, s.omega)
+        t1, _ = oracle_step(phi, psi, kern, s.dv, [0])
+        ncols = int(max(1, min(s.n_occ, 15.0 / max(t1, 1e-3))))
+        cols = list(range(0, s.n_occ, max(1, s.n_occ // ncols)))[:ncols]
+        t, det = oracle_step(phi, psi, kern, s.dv, cols)
+        cpu = {"value": pairs / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{len(cols)} of {s.n_occ} W columns ({len(cols) * s.n_occ} ordered FFT-Poisson "
+                         f"solves) scaled to a full build, plus full-size M/Cholesky/Xi/apply",
+               "detail": det}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+                "warmup": args.warmup, "ms_per_step": elapsed_ms / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(s),
+                "ms_per_build": build_ms, "ms_per_apply": apply_ms,
+                "roofline": {"kernel": "pair FFT-Poisson pipeline (passes A-D, per ace_build)",
+                             "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "peak_kind": peak_kind,
+                             "alg_bytes_per_launch": alg_bytes,
+                             "alg_model": "32 B/point/unique pair + Phi read + W write",
+                             "ms_per_launch": pair_ms, "traffic": None, "passes": passes},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": Ke},
+                "gpu_launches": prof["launches"] + 0,
+                "clocks": clk}
+        if fp64:
+            line.update(fp64)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

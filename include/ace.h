@@ -1,0 +1,157 @@
+/*
+ * ace.h -- C ABI of the GB300 (sm_103a) adaptively compressed exchange path.
+ *
+ * Method: L. Lin, "Adaptively Compressed Exchange Operator" (arXiv:1601.07159).
+ *   Eq. applyVX / applyVX2 : (V_X[phi] psi)(r) = -sum_j phi_j(r) int phi_j(r') psi(r') K(r-r') dr'
+ *   Eq. W                  : W_i = V_X[phi] phi_i
+ *   Eq. ACEconstruct2      : M_kl = <phi_k, W_l>,  -M = L L^*   (Sec. 3, Cholesky step)
+ *   Eq. Wtilde             : Xi = W L^{-*}
+ *   Eq. ACE                : V_ACE psi = -Xi (Xi^* psi)
+ *   Eq. EX / EX_ACE        : E_x = -1/2 sum_ij (rho_ij | K | rho_ij) = 1/2 Re tr M
+ *   Eq. EXSR               : screened kernel erfc(omega r)/r
+ *
+ * Discretisation (all entry points): a periodic orthorhombic cell L[0] x L[1] x
+ * L[2] sampled on n x n x n points; dV = Omega / N_g. Inner products are
+ * <f, g> = dV sum_r conj(f(r)) g(r). The Poisson-type solve is
+ *   v(r) = sum_G K(G) rho_hat(G) e^{iG.r},  rho_hat(G) = N_g^-1 sum_r rho(r) e^{-iG.r},
+ * with K(G) = alpha * 4 pi/|G|^2 (ACE_KERNEL_BARE, K(0) = 0 by default) or
+ * alpha * (4 pi/|G|^2)(1 - exp(-|G|^2 / 4 omega^2)) (ACE_KERNEL_ERFC, K(0) =
+ * alpha * pi / omega^2 by default). Complex orbitals use the Hermitian form
+ * V_X(r, r') = -sum_j phi_j(r) conj(phi_j(r')) K(r - r').
+ *
+ * Conventions shared by every entry point:
+ *  - Array arguments are DEVICE pointers owned by the caller. Layout is
+ *    orbital-major, x fastest: element (b, z, y, x) of an array of `count`
+ *    vectors is at offset ((b * n + z) * n + y) * n + x elements. Storage type is
+ *    the plan's dtype: ACE_DTYPE_R64 (double, real Gamma-point orbitals),
+ *    ACE_DTYPE_C128 (interleaved double complex) or ACE_DTYPE_C64 (interleaved
+ *    float complex). Pointers must be 16-byte aligned.
+ *  - Work runs asynchronously on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) on the current device, which must be the plan's device.
+ *    The return code reports host-side validation and launch errors only;
+ *    device-side failures (non-positive Cholesky pivot, non-finite pivot) are
+ *    recorded in the plan's status word, read by ace_status_sync.
+ *  - The library does not allocate on these calls: scratch memory is the
+ *    caller's `ws` of at least ace_workspace_size() bytes (256-byte aligned).
+ *  - A plan may be used by one stream at a time. Errors never throw across the
+ *    ABI; ace_last_error() returns the calling thread's last message.
+ */
+#ifndef ACE_H
+#define ACE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  ACE_OK = 0,
+  ACE_ERR_ARG = -1,          /* invalid argument (null pointer, size, alignment) */
+  ACE_ERR_NOT_POSDEF = -2,   /* -M not positive definite (device status) */
+  ACE_ERR_NONFINITE = -3,    /* NaN / Inf met in the Cholesky pivot (device status) */
+  ACE_ERR_WORKSPACE = -4,    /* ws_bytes smaller than ace_workspace_size() */
+  ACE_ERR_CUDA = -5,         /* a CUDA runtime call or launch failed */
+  ACE_ERR_TIMEOUT = -6,      /* reserved: a bounded device wait ran out */
+  ACE_ERR_UNSUPPORTED = -7   /* grid edge / dtype combination not built */
+} ace_status;
+
+typedef enum { ACE_DTYPE_R64 = 0, ACE_DTYPE_C128 = 1, ACE_DTYPE_C64 = 2 } ace_dtype;
+typedef enum { ACE_KERNEL_BARE = 0, ACE_KERNEL_ERFC = 1 } ace_kernel;
+typedef enum {
+  ACE_OP_EXCHANGE_APPLY = 0, ACE_OP_BUILD = 1, ACE_OP_APPLY = 2, ACE_OP_ENERGY_GRAD = 3
+} ace_op;
+
+typedef struct {
+  int n;             /* grid points per edge (cubic grid n^3); see ace_supported_edge */
+  double L[3];       /* cell edges Lx, Ly, Lz (bohr), > 0 */
+  int n_occ;         /* N: number of exchange orbitals phi, >= 1 */
+  int dtype;         /* ace_dtype. R64/C128: FP64 throughout. C64: FP32 pair/FFT path and
+                        FP32 GEMMs, FP64 Cholesky and triangular inverse. */
+  int kernel;        /* ace_kernel */
+  double omega;      /* screening parameter (bohr^-1) for ACE_KERNEL_ERFC, > 0 */
+  double g0_value;   /* K(G=0) before alpha; NaN selects the default (0 bare, pi/omega^2 erfc) */
+  double alpha;      /* overall kernel scale (1 = Hartree-Fock; 0.25 for PBE0/HSE fractions) */
+  int max_pairs;     /* pair solves in flight per batch (0 = library default); sets the
+                        size of the pair-spectrum scratch in the workspace */
+  int tile;          /* orbitals per pair tile, 1..8 (0 = default 8) */
+} ace_desc;
+
+typedef struct ace_plan ace_plan;
+
+/* Nonzero when grid edge n is compiled in for the dtype (register-resident FFT
+ * lengths; radices 2, 3, 4, 5). */
+int ace_supported_edge(int n, int dtype);
+
+/* Validate *desc and build a plan on the current device: Coulomb kernel table,
+ * FFT twiddles (FP64 host sin/cos), the pair-tile schedule and small FP64 N x N
+ * buffers. Returns ACE_ERR_ARG / ACE_ERR_UNSUPPORTED / ACE_ERR_CUDA on failure
+ * and leaves *out NULL. Allocates; not for the hot path. */
+ace_status ace_plan_create(const ace_desc* desc, ace_plan** out);
+
+/* Free a plan and its device buffers (synchronises the device). NULL is a no-op. */
+ace_status ace_plan_destroy(ace_plan* plan);
+
+/* Bytes of scratch `ws` the entry point `op` needs for n_b target vectors
+ * (ignored for ACE_OP_BUILD / ACE_OP_ENERGY_GRAD). 0 on invalid input. */
+size_t ace_workspace_size(const ace_plan* plan, int op, int n_b);
+
+/* Y = V_X[Phi] Psi (Eq. applyVX2): N x n_b pair solves, no pair symmetry.
+ * Phi: N vectors, Psi: n_b vectors, Y: n_b vectors (overwritten). Y must not
+ * alias Phi or Psi. */
+ace_status ace_exchange_apply(ace_plan* plan, const void* Phi, const void* Psi, int n_b,
+                              void* Y, void* ws, size_t ws_bytes, void* stream);
+
+/* ACE construction (Alg. 2, steps 2-3): W = V_X[Phi] Phi with N(N+1)/2 unique
+ * pair solves (v_ij = conj(v_ji) halves the work), M = dV Phi^* W made
+ * Hermitian, -M = L L^* (FP64), Xi = W L^{-*}.
+ * Phi: N vectors (orthonormal in <.,.> for Eq. ACEcond to hold, not checked).
+ * W_out: N vectors or NULL. Xi_out: N vectors (required).
+ * M_out: NULL or device double[N*N] (R64) / double[2*N*N] (complex, interleaved),
+ *        row-major M[k][l].
+ * Ex_out: NULL or device double[1] = 1/2 Re tr M (Eq. EX_ACE with psi = phi).
+ * A non-positive pivot stops the factorisation and is reported through
+ * ace_status_sync (ACE_ERR_NOT_POSDEF, info = 1-based pivot); Xi is then undefined. */
+ace_status ace_build(ace_plan* plan, const void* Phi, void* W_out, void* Xi_out,
+                     double* M_out, double* Ex_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Y = V_ACE Psi = -Xi (dV Xi^* Psi) (Eq. ACE). Xi: N vectors from ace_build,
+ * Psi and Y: n_b vectors; Y must not alias Xi or Psi. No Poisson solves. */
+ace_status ace_apply(ace_plan* plan, const void* Xi, const void* Psi, int n_b, void* Y,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* E_x[Phi] (Eq. EX, via Parseval: -1/2 sum_ij Omega sum_G K |rho_hat_ij|^2, FP64
+ * accumulation) into device Ex_out[0]; when grad_out is non-NULL also
+ * grad_out = grad_scale * 2 dV W (the gradient dE/dRe(phi) + i dE/dIm(phi);
+ * W recomputed, pair potentials never stored). */
+ace_status ace_exchange_energy_grad(ace_plan* plan, const void* Phi, double* Ex_out,
+                                    void* grad_out, double grad_scale, void* ws,
+                                    size_t ws_bytes, void* stream);
+
+/* Synchronise `stream` and read the plan's device status word: returns ACE_OK,
+ * ACE_ERR_NOT_POSDEF or ACE_ERR_NONFINITE; *info (if non-NULL) gets the
+ * 1-based Cholesky pivot that failed, 0 otherwise. Clears the status. */
+ace_status ace_status_sync(ace_plan* plan, void* stream, int* info);
+
+/* Instrumentation (no counterpart in the paper; for benchmarks and profiles).
+ * ace_profile_begin: create `max_events` CUDA events (allocates; call outside
+ * timed or captured regions) and from now on record one event before each pair
+ * pass launch and one after the batch, so pass durations can be summed; resets
+ * the kernel-launch counter. Recording stops silently when the events run out.
+ * ace_profile_end: synchronise the device, then write ms_out[0..4] = total
+ * milliseconds of pass A (pair product + xy FFT), pass B (z FFT, kernel, inverse
+ * z FFT), pass C (inverse xy FFT), pass D (accumulate) and their sum over the
+ * recorded batches, and counts_out[0..2] = recorded batches, kernel launches by
+ * this plan since ace_profile_begin, batches not recorded; frees the events.
+ * Either output may be NULL. */
+ace_status ace_profile_begin(ace_plan* plan, int max_events);
+ace_status ace_profile_end(ace_plan* plan, double* ms_out, long long* counts_out);
+
+/* Message for the calling thread's last failed call ("" if none). */
+const char* ace_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACE_H */

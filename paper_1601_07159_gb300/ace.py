@@ -1,0 +1,270 @@
+"""ctypes binding over the C ABI of include/ace.h.
+
+Argument marshalling only: every step of the exchange / ACE path runs in the
+CUDA kernels of libace.so. PyTorch supplies device memory and the current
+stream. Importing this module loads the library and raises ImportError when it
+has not been built (``paper_1601_07159_gb300.build_lib``); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libace.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libace.so not built ({LIB_PATH}); run python -m paper_1601_07159_gb300.build_lib")
+_lib = ctypes.CDLL(LIB_PATH)
+
+ACE_OK = 0
+ACE_ERR_ARG = -1
+ACE_ERR_NOT_POSDEF = -2
+ACE_ERR_NONFINITE = -3
+ACE_ERR_WORKSPACE = -4
+ACE_ERR_CUDA = -5
+ACE_ERR_TIMEOUT = -6
+ACE_ERR_UNSUPPORTED = -7
+
+DTYPES = {"r64": 0, "c128": 1, "c64": 2}
+TORCH_DTYPES = {"r64": torch.float64, "c128": torch.complex128, "c64": torch.complex64}
+KERNELS = {"bare": 0, "erfc": 1}
+OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD = 0, 1, 2, 3
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("L", ctypes.c_double * 3),
+        ("n_occ", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("omega", ctypes.c_double),
+        ("g0_value", ctypes.c_double),
+        ("alpha", ctypes.c_double),
+        ("max_pairs", ctypes.c_int),
+        ("tile", ctypes.c_int),
+    ]
+
+
+_vp = ctypes.c_void_p
+_lib.ace_supported_edge.argtypes = [ctypes.c_int, ctypes.c_int]
+_lib.ace_supported_edge.restype = ctypes.c_int
+_lib.ace_last_error.argtypes = []
+_lib.ace_last_error.restype = ctypes.c_char_p
+_lib.ace_plan_create.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(_vp)]
+_lib.ace_plan_create.restype = ctypes.c_int
+_lib.ace_plan_destroy.argtypes = [_vp]
+_lib.ace_plan_destroy.restype = ctypes.c_int
+_lib.ace_workspace_size.argtypes = [_vp, ctypes.c_int, ctypes.c_int]
+_lib.ace_workspace_size.restype = ctypes.c_size_t
+_lib.ace_exchange_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+_lib.ace_exchange_apply.restype = ctypes.c_int
+_lib.ace_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+_lib.ace_build.restype = ctypes.c_int
+_lib.ace_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+_lib.ace_apply.restype = ctypes.c_int
+_lib.ace_exchange_energy_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_size_t, _vp]
+_lib.ace_exchange_energy_grad.restype = ctypes.c_int
+_lib.ace_status_sync.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int)]
+_lib.ace_status_sync.restype = ctypes.c_int
+_lib.ace_profile_begin.argtypes = [_vp, ctypes.c_int]
+_lib.ace_profile_begin.restype = ctypes.c_int
+_lib.ace_profile_end.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
+_lib.ace_profile_end.restype = ctypes.c_int
+
+
+class AceError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ace error {code}: {msg}")
+        self.code = code
+
+
+def _check(code: int):
+    if code != ACE_OK:
+        raise AceError(code, _lib.ace_last_error().decode())
+
+
+def supported_edge(n: int, dtype: str) -> bool:
+    return bool(_lib.ace_supported_edge(n, DTYPES[dtype]))
+
+
+def lib():
+    """The loaded ctypes library (for tests that call the C ABI directly)."""
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Plan:
+    """An ACE plan on the current CUDA device (see ace_plan_create)."""
+
+    def __init__(self, n: int, L, n_occ: int, dtype: str = "c64", kernel: str = "bare",
+                 omega: float = 0.0, g0: float | None = None, alpha: float = 1.0,
+                 max_pairs: int = 0, tile: int = 0):
+        if isinstance(L, (int, float)):
+            L = (float(L),) * 3
+        d = Desc()
+        d.n = n
+        d.L[0], d.L[1], d.L[2] = L
+        d.n_occ = n_occ
+        d.dtype = DTYPES[dtype]
+        d.kernel = KERNELS[kernel]
+        d.omega = omega
+        d.g0_value = math.nan if g0 is None else g0
+        d.alpha = alpha
+        d.max_pairs = max_pairs
+        d.tile = tile
+        h = _vp()
+        _check(_lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)))
+        self._h = h
+        self.n, self.L, self.n_occ, self.dtype = n, tuple(L), n_occ, dtype
+        self.ng = n ** 3
+        self.volume = L[0] * L[1] * L[2]
+        self.dv = self.volume / self.ng
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.tdtype = TORCH_DTYPES[dtype]
+        self._ws = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ace_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- helpers
+    def workspace_size(self, op: int, n_b: int = 0) -> int:
+        return int(_lib.ace_workspace_size(self._h, op, n_b))
+
+    def workspace(self, op: int, n_b: int = 0) -> torch.Tensor:
+        nbytes = max(self.workspace_size(op, n_b), 256)
+        ws = self._ws.get(op)
+        if ws is None or ws.numel() < nbytes:
+            ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self._ws[op] = ws
+        return ws
+
+    def _vec(self, t: torch.Tensor, name: str) -> torch.Tensor:
+        if t.dtype != self.tdtype:
+            raise TypeError(f"{name}: expected {self.tdtype}, got {t.dtype}")
+        if t.device != self.device:
+            raise ValueError(f"{name}: expected device {self.device}")
+        if t.dim() != 4 or tuple(t.shape[1:]) != (self.n,) * 3:
+            raise ValueError(f"{name}: expected shape (count, {self.n}, {self.n}, {self.n})")
+        if not t.is_contiguous():
+            raise ValueError(f"{name}: must be contiguous")
+        return t
+
+    def empty(self, count: int) -> torch.Tensor:
+        return torch.empty((count, self.n, self.n, self.n), dtype=self.tdtype, device=self.device)
+
+    # ---------------------------------------------------------------- entry points
+    def exchange_apply(self, phi, psi, out=None):
+        """Y = V_X[phi] psi (Eq. applyVX2)."""
+        self._vec(phi, "phi")
+        self._vec(psi, "psi")
+        nb = psi.shape[0]
+        y = self.empty(nb) if out is None else self._vec(out, "out")
+        ws = self.workspace(OP_EXCHANGE_APPLY, nb)
+        _check(_lib.ace_exchange_apply(self._h, _ptr(phi), _ptr(psi), nb, _ptr(y), _ptr(ws),
+                                       ws.numel(), _stream()))
+        return y
+
+    def build(self, phi, want_w: bool = True, want_m: bool = True, xi=None, w=None):
+        """ACE construction: W, M, Xi and E_x = 1/2 Re tr M (Alg. 2 steps 2-3)."""
+        self._vec(phi, "phi")
+        N = self.n_occ
+        if phi.shape[0] != N:
+            raise ValueError("phi must hold n_occ vectors")
+        xi = self.empty(N) if xi is None else self._vec(xi, "xi")
+        if want_w and w is None:
+            w = self.empty(N)
+        m = None
+        if want_m:
+            shape = (N, N) if self.dtype == "r64" else (N, N, 2)
+            m = torch.empty(shape, dtype=torch.float64, device=self.device)
+        ex = torch.empty((), dtype=torch.float64, device=self.device)
+        ws = self.workspace(OP_BUILD)
+        _check(_lib.ace_build(self._h, _ptr(phi), _ptr(w), _ptr(xi), _ptr(m), _ptr(ex), _ptr(ws),
+                              ws.numel(), _stream()))
+        if m is not None and self.dtype != "r64":
+            m = torch.view_as_complex(m)
+        return {"Xi": xi, "W": w, "M": m, "Ex": ex}
+
+    def apply(self, xi, psi, out=None):
+        """Y = V_ACE psi = -Xi (dV Xi^* psi) (Eq. ACE)."""
+        self._vec(xi, "xi")
+        self._vec(psi, "psi")
+        nb = psi.shape[0]
+        y = self.empty(nb) if out is None else self._vec(out, "out")
+        ws = self.workspace(OP_APPLY, nb)
+        _check(_lib.ace_apply(self._h, _ptr(xi), _ptr(psi), nb, _ptr(y), _ptr(ws), ws.numel(),
+                              _stream()))
+        return y
+
+    def energy_grad(self, phi, grad: bool = False, grad_scale: float = 1.0, out=None):
+        """E_x (Eq. EX) and optionally grad_scale * 2 dV W."""
+        self._vec(phi, "phi")
+        ex = torch.empty((), dtype=torch.float64, device=self.device)
+        g = None
+        if grad:
+            g = self.empty(self.n_occ) if out is None else self._vec(out, "out")
+        ws = self.workspace(OP_ENERGY_GRAD)
+        _check(_lib.ace_exchange_energy_grad(self._h, _ptr(phi), _ptr(ex), _ptr(g), grad_scale,
+                                             _ptr(ws), ws.numel(), _stream()))
+        return ex, g
+
+    def profile_begin(self, max_events: int = 4096):
+        _check(_lib.ace_profile_begin(self._h, max_events))
+
+    def profile_end(self) -> dict:
+        """Pass durations (ms) over the recorded batches and the launch count."""
+        ms = (ctypes.c_double * 5)()
+        cnt = (ctypes.c_longlong * 3)()
+        _check(_lib.ace_profile_end(self._h, ms, cnt))
+        return {"pass_ms": {"A": ms[0], "B": ms[1], "C": ms[2], "D": ms[3]}, "pair_ms": ms[4],
+                "batches": cnt[0], "launches": cnt[1], "dropped": cnt[2]}
+
+    def status(self) -> tuple[int, int]:
+        """(code, pivot) of the device status word after synchronising."""
+        info = ctypes.c_int(0)
+        code = _lib.ace_status_sync(self._h, _stream(), ctypes.byref(info))
+        return code, info.value
+
+
+class ExchangeEnergy(torch.autograd.Function):
+    """E_x[Phi] with a hand-written adjoint: backward recomputes W through the
+    pair kernels (pair potentials are never stored) and returns
+    grad_output * 2 dV W, the gradient dE/dRe(phi) + i dE/dIm(phi)."""
+
+    @staticmethod
+    def forward(ctx, phi, plan: Plan):
+        ex, _ = plan.energy_grad(phi, grad=False)
+        ctx.plan = plan
+        ctx.save_for_backward(phi)
+        return ex
+
+    @staticmethod
+    def backward(ctx, g_out):
+        (phi,) = ctx.saved_tensors
+        _, g = ctx.plan.energy_grad(phi, grad=True, grad_scale=float(g_out.item()))
+        return g, None
+
+
+def exchange_energy(phi: torch.Tensor, plan: Plan) -> torch.Tensor:
+    return ExchangeEnergy.apply(phi, plan)

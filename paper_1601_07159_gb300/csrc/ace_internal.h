@@ -1,0 +1,70 @@
+// Internal declarations shared by the host API and the kernel translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ace {
+
+constexpr int kMaxTiles = 64;   // pair tiles per batch (one kernel launch covers a batch)
+constexpr int kTileMax = 8;     // orbitals per tile side (register accumulators in pass D)
+
+// One tile of pair solves.
+//  kind 0: off-diagonal symmetric tile, pairs (l, r) for l in [l0, l0+nl), r in [r0, r0+nr);
+//          each pair feeds W_r (through conj(phi_l) phi_r) and W_l (through the conjugate).
+//  kind 1: diagonal symmetric tile (l0 == r0, nl == nr), pairs l <= r.
+//  kind 2: rectangular one-sided tile, pairs (l, r) feed Out_r only (V_X[Phi] Psi).
+// Pair q of a tile lives in slot slot0 + q of the batch's spectrum scratch;
+// the order is row-major over (l, r) (upper triangle for kind 1).
+struct TileDesc {
+  int l0, nl, r0, nr, kind, slot0;
+};
+struct Batch {
+  int ntiles;
+  int npairs;
+  TileDesc t[kMaxTiles];
+};
+
+__host__ __device__ inline int tile_pairs(const TileDesc& d) {
+  return d.kind == 1 ? d.nl * (d.nl + 1) / 2 : d.nl * d.nr;
+}
+
+// Launchers (pair_f32.cu / pair_f64.cu). Return false if edge n is not compiled.
+struct PairLaunch {
+  int n;                 // grid edge
+  long long ld;          // elements per vector (n^3)
+  const void* X;         // l-side vectors (phi)
+  const void* Y;         // r-side vectors (phi or psi)
+  void* OutX;            // accumulators for the l side (symmetric tiles)
+  void* OutY;            // accumulators for the r side
+  void* S;               // spectrum scratch, max_pairs * n^3 complex
+  const void* Kt;        // kernel table K(G) alpha / N_g, layout [kz][kx][ky]
+  double* Epart;         // per-block energy partials (nullable)
+  double scale;          // Out -= scale * sum
+  const double* tw;      // host FP64 twiddles exp(-2 pi i k/n), 2n doubles
+  bool real_io;          // R64 vectors
+  int mode;              // 0: W / Y accumulate; 1: energy only; 2: energy + accumulate
+  cudaEvent_t* ev;       // nullable: 5 events recorded around passes A, B, C, D
+};
+// Kernel launches issued by one pair batch for a mode (4, or 2 for energy only).
+inline int pair_batch_launches(int mode) { return mode == 1 ? 2 : 4; }
+bool launch_pair_batch_f32(const PairLaunch& L, const Batch& b, cudaStream_t st);
+bool launch_pair_batch_f64(const PairLaunch& L, const Batch& b, cudaStream_t st);
+bool pair_edge_supported_f32(int n);
+bool pair_edge_supported_f64(int n);
+int energy_blocks(int n, int npairs, bool f64);
+
+// Dense kernels (dense.cu).
+void launch_gram(bool f64, bool real_in, const void* A, int na, const void* B, int nb, long long ld,
+                 long long ng, double* part, int splits, cudaStream_t st);
+int gram_splits(long long ng);
+void launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
+                        bool real_out, double* out, double* out_trace_half, cudaStream_t st);
+void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,
+                  long long ld, long long ng, double alpha, void* Out, cudaStream_t st);
+void launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
+                         cudaStream_t st);
+void launch_energy_reduce(const double* part, int count, double factor, double* out, cudaStream_t st);
+void launch_zero(void* p, size_t bytes, cudaStream_t st);
+
+}  // namespace ace

@@ -1,0 +1,356 @@
+// Dense steps of the ACE construction and apply (Sec. 3):
+//   M = dV Phi^* W  (Eq. ACEconstruct2)       -> gram + gram_reduce
+//   -M = L L^*, L^{-1} (FP64)                  -> cholesky_inv
+//   Xi = W L^{-*}    (Eq. Wtilde)              -> outer with C = L^{-*}
+//   C = dV Xi^* psi, Y = -Xi C   (Eq. ACE)     -> gram + gram_reduce, outer
+//   E_x reductions (Eq. EX / EX_ACE)           -> energy_reduce, trace in gram_reduce
+//
+// Arrays of vectors are orbital-major [count][N_g] (x fastest); small matrices
+// are row-major FP64 (complex interleaved). The GEMMs run on CUDA cores in the
+// vectors' precision with a deterministic split-K reduction in FP64.
+#include <cmath>
+
+#include "ace_internal.h"
+#include "fft_reg.cuh"
+
+namespace ace {
+
+// ---------------------------------------------------------------- gram
+// part[s][a][b] = sum_{g in chunk s} conj(A[a][g]) B[b][g]   (complex, FP64 out)
+constexpr int GT = 64;   // output tile edge
+constexpr int GK = 16;   // K chunk per shared-memory stage
+
+template <typename R, bool REAL>
+__global__ void __launch_bounds__(256)
+gram_kernel(const void* __restrict__ A, int na, const void* __restrict__ B, int nb, long long ld,
+            long long ng, double* __restrict__ part, long long chunk) {
+  __shared__ cplx<R> As[GK][GT + 1];
+  __shared__ cplx<R> Bs[GK][GT + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int a0 = blockIdx.x * GT, b0 = blockIdx.y * GT;
+  const long long g_begin = (long long)blockIdx.z * chunk;
+  const long long g_end = g_begin + chunk < ng ? g_begin + chunk : ng;
+  cplx<R> acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmk<cplx<R>>(R(0), R(0));
+
+  for (long long g0 = g_begin; g0 < g_end; g0 += GK) {
+    // load 64 rows x 16 columns of A and B: 1024 elements each, 4 per thread
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int idx = threadIdx.x + 256 * e;
+      const int row = idx >> 4, col = idx & 15;
+      const long long g = g0 + col;
+      cplx<R> va = cmk<cplx<R>>(R(0), R(0)), vb = va;
+      if (g < g_end) {
+        if (a0 + row < na) {
+          const long long o = (long long)(a0 + row) * ld + g;
+          if constexpr (REAL) va.x = static_cast<const R*>(A)[o];
+          else va = static_cast<const cplx<R>*>(A)[o];
+        }
+        if (b0 + row < nb) {
+          const long long o = (long long)(b0 + row) * ld + g;
+          if constexpr (REAL) vb.x = static_cast<const R*>(B)[o];
+          else vb = static_cast<const cplx<R>*>(B)[o];
+        }
+      }
+      As[col][row] = va;
+      Bs[col][row] = vb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < GK; ++k) {
+      cplx<R> av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cadd(acc[i][j], cmulc(av[i], bv[j]));
+    }
+    __syncthreads();
+  }
+  double* out = part + (long long)blockIdx.z * na * nb * 2;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty + 16 * i;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tx + 16 * j;
+      if (a < na && b < nb) {
+        out[2 * ((long long)a * nb + b)] = (double)acc[i][j].x;
+        out[2 * ((long long)a * nb + b) + 1] = (double)acc[i][j].y;
+      }
+    }
+  }
+}
+
+int gram_splits(long long ng) {
+  // ~1.2k-point chunks keep the FP32 partial sums short while filling the GPU
+  long long s = (ng + 1023) / 1024;
+  if (s > 256) s = 256;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+void launch_gram(bool f64, bool real_in, const void* A, int na, const void* B, int nb, long long ld,
+                 long long ng, double* part, int splits, cudaStream_t st) {
+  long long chunk = (ng + splits - 1) / splits;
+  chunk = (chunk + GK - 1) / GK * GK;
+  const dim3 grid((na + GT - 1) / GT, (nb + GT - 1) / GT, splits);
+  if (f64) {
+    if (real_in) gram_kernel<double, true><<<grid, 256, 0, st>>>(A, na, B, nb, ld, ng, part, chunk);
+    else gram_kernel<double, false><<<grid, 256, 0, st>>>(A, na, B, nb, ld, ng, part, chunk);
+  } else {
+    gram_kernel<float, false><<<grid, 256, 0, st>>>(A, na, B, nb, ld, ng, part, chunk);
+  }
+}
+
+// out[a][b] = scale * sum_s part[s][a][b]; hermitize -> (X + X^*)/2;
+// real_out -> imaginary parts dropped (real Gamma-point case).
+// out_trace_half (nullable) <- 1/2 Re tr(out) (computed by block (0,0)).
+__global__ void gram_reduce_kernel(const double* __restrict__ part, int splits, int na, int nb,
+                                   double scale, int hermitize, int real_out, double* __restrict__ out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)na * nb) return;
+  const int a = (int)(idx / nb), b = (int)(idx % nb);
+  const long long stride = (long long)na * nb * 2;
+  double re = 0.0, im = 0.0;
+  for (int s = 0; s < splits; ++s) {
+    re += part[s * stride + 2 * idx];
+    im += part[s * stride + 2 * idx + 1];
+  }
+  if (hermitize) {
+    const long long t = (long long)b * nb + a;
+    double re2 = 0.0, im2 = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      re2 += part[s * stride + 2 * t];
+      im2 += part[s * stride + 2 * t + 1];
+    }
+    re = 0.5 * (re + re2);
+    im = 0.5 * (im - im2);
+  }
+  if (real_out) {
+    out[idx] = scale * re;
+  } else {
+    out[2 * idx] = scale * re;
+    out[2 * idx + 1] = scale * im;
+  }
+}
+
+__global__ void trace_half_kernel(const double* __restrict__ m, int n, int real, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) s += real ? m[(long long)k * n + k] : m[2 * ((long long)k * n + k)];
+  *out = 0.5 * s;
+}
+
+void launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
+                        bool real_out, double* out, double* out_trace_half, cudaStream_t st) {
+  const long long total = (long long)na * nb;
+  gram_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, splits, na, nb, scale,
+                                                                      hermitize, real_out, out);
+  if (out_trace_half) trace_half_kernel<<<1, 32, 0, st>>>(out, na, real_out, out_trace_half);
+}
+
+// ---------------------------------------------------------------- outer
+// Out[b][g] = alpha * sum_k A[k][g] C[k][b]   (C: FP64 complex [nk][nb])
+constexpr int OG = 128;  // g per block
+constexpr int OB = 16;   // b per block
+constexpr int OK = 16;   // k per stage
+
+template <typename R, bool REAL>
+__global__ void __launch_bounds__(256)
+outer_kernel(const void* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
+             long long ng, double alpha, void* __restrict__ Out) {
+  __shared__ cplx<R> As[OK][OG];
+  __shared__ cplx<R> Cs[OK][OB];
+  const int tg = threadIdx.x & 63, tb = threadIdx.x >> 6;   // 64 x 4
+  const long long g0 = (long long)blockIdx.x * OG;
+  const int b0 = blockIdx.y * OB;
+  cplx<R> acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmk<cplx<R>>(R(0), R(0));
+  for (int k0 = 0; k0 < nk; k0 += OK) {
+#pragma unroll
+    for (int e = 0; e < (OK * OG) / 256; ++e) {
+      const int idx = threadIdx.x + 256 * e;
+      const int kk = idx / OG, gg = idx % OG;
+      const long long g = g0 + gg;
+      cplx<R> v = cmk<cplx<R>>(R(0), R(0));
+      if (k0 + kk < nk && g < ng) {
+        const long long o = (long long)(k0 + kk) * ld + g;
+        if constexpr (REAL) v.x = static_cast<const R*>(A)[o];
+        else v = static_cast<const cplx<R>*>(A)[o];
+      }
+      As[kk][gg] = v;
+    }
+    {
+      const int kk = threadIdx.x / OB, bb = threadIdx.x % OB;
+      cplx<R> c = cmk<cplx<R>>(R(0), R(0));
+      if (k0 + kk < nk && b0 + bb < nb) {
+        const long long o = 2 * ((long long)(k0 + kk) * nb + b0 + bb);
+        c = cmk<cplx<R>>((R)C[o], (R)C[o + 1]);
+      }
+      Cs[kk][bb] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < OK; ++k) {
+      cplx<R> av[2], cv[4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) av[i] = As[k][tg + 64 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cv[j] = Cs[k][tb * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = cadd(acc[i][j], cmul(av[i], cv[j]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const long long g = g0 + tg + 64 * i;
+    if (g >= ng) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tb * 4 + j;
+      if (b >= nb) continue;
+      const long long o = (long long)b * ld + g;
+      if constexpr (REAL) static_cast<R*>(Out)[o] = (R)alpha * acc[i][j].x;
+      else static_cast<cplx<R>*>(Out)[o] = cscale(acc[i][j], (R)alpha);
+    }
+  }
+}
+
+void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,
+                  long long ld, long long ng, double alpha, void* Out, cudaStream_t st) {
+  const dim3 grid((unsigned)((ng + OG - 1) / OG), (nb + OB - 1) / OB);
+  if (f64) {
+    if (real_io) outer_kernel<double, true><<<grid, 256, 0, st>>>(A, nk, C, nb, ld, ng, alpha, Out);
+    else outer_kernel<double, false><<<grid, 256, 0, st>>>(A, nk, C, nb, ld, ng, alpha, Out);
+  } else {
+    outer_kernel<float, false><<<grid, 256, 0, st>>>(A, nk, C, nb, ld, ng, alpha, Out);
+  }
+}
+
+// ---------------------------------------------------------------- Cholesky + inverse (FP64)
+// work: 2 * n * n doubles (complex, row-major) receiving -M, factored in place
+// to L (lower). status[0] = ACE_ERR_NOT_POSDEF / ACE_ERR_NONFINITE, status[1] =
+// 1-based pivot, on failure. Single CTA, right-looking, one column per step.
+__global__ void __launch_bounds__(1024)
+cholesky_kernel(const double* __restrict__ M, int n, double* __restrict__ A, int* status) {
+  __shared__ int fail;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (long long i = tid; i < (long long)n * n; i += nt) {
+    A[2 * i] = -M[2 * i];
+    A[2 * i + 1] = -M[2 * i + 1];
+  }
+  if (tid == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double d = A[2 * ((long long)j * n + j)];
+      if (!isfinite(d)) {
+        fail = 1;
+        status[0] = -3;
+        status[1] = j + 1;
+      } else if (!(d > 0.0)) {
+        fail = 1;
+        status[0] = -2;
+        status[1] = j + 1;
+      } else {
+        A[2 * ((long long)j * n + j)] = sqrt(d);
+        A[2 * ((long long)j * n + j) + 1] = 0.0;
+      }
+    }
+    __syncthreads();
+    if (fail) return;
+    const double inv = 1.0 / A[2 * ((long long)j * n + j)];
+    for (int i = j + 1 + tid; i < n; i += nt) {
+      A[2 * ((long long)i * n + j)] *= inv;
+      A[2 * ((long long)i * n + j) + 1] *= inv;
+    }
+    __syncthreads();
+    const int rem = n - j - 1;
+    for (long long e = tid; e < (long long)rem * rem; e += nt) {
+      const int i = j + 1 + (int)(e / rem), k = j + 1 + (int)(e % rem);
+      if (k > i) continue;
+      const double ar = A[2 * ((long long)i * n + j)], ai = A[2 * ((long long)i * n + j) + 1];
+      const double br = A[2 * ((long long)k * n + j)], bi = A[2 * ((long long)k * n + j) + 1];
+      // A[i][k] -= L[i][j] conj(L[k][j])
+      A[2 * ((long long)i * n + k)] -= ar * br + ai * bi;
+      A[2 * ((long long)i * n + k) + 1] -= ai * br - ar * bi;
+    }
+    __syncthreads();
+  }
+  for (long long e = tid; e < (long long)n * n; e += nt) {
+    const int i = (int)(e / n), k = (int)(e % n);
+    if (k > i) { A[2 * e] = 0.0; A[2 * e + 1] = 0.0; }
+  }
+}
+
+// X = L^{-1} column by column (thread = column c, forward substitution), then
+// LinvH[c][i] = conj(X[i][c]) so that Xi[k] = sum_i W[i] LinvH[i][k].
+__global__ void tri_inv_kernel(const double* __restrict__ Lm, int n, double* __restrict__ X,
+                               double* __restrict__ LinvH, const int* status) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n || status[0] != 0) return;
+  for (int i = 0; i < n; ++i) {
+    double sr = 0.0, si = 0.0;
+    if (i >= c) {
+      sr = (i == c) ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) {
+        const double lr = Lm[2 * ((long long)i * n + k)], li = Lm[2 * ((long long)i * n + k) + 1];
+        const double xr = X[2 * ((long long)k * n + c)], xi = X[2 * ((long long)k * n + c) + 1];
+        sr -= lr * xr - li * xi;
+        si -= lr * xi + li * xr;
+      }
+      const double d = Lm[2 * ((long long)i * n + i)];
+      sr /= d;
+      si /= d;
+    }
+    X[2 * ((long long)i * n + c)] = sr;
+    X[2 * ((long long)i * n + c) + 1] = si;
+    LinvH[2 * ((long long)c * n + i)] = sr;
+    LinvH[2 * ((long long)c * n + i) + 1] = -si;
+  }
+}
+
+void launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
+                         cudaStream_t st) {
+  double* A = work;                       // 2 n^2
+  double* X = work + 2 * (long long)n * n;  // 2 n^2
+  cholesky_kernel<<<1, 1024, 0, st>>>(M, n, A, status);
+  tri_inv_kernel<<<(n + 31) / 32, 32, 0, st>>>(A, n, X, LinvH, status);
+}
+
+// ---------------------------------------------------------------- reductions
+__global__ void energy_reduce_kernel(const double* __restrict__ part, int count, double factor,
+                                     double* out) {
+  __shared__ double red[1024];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = factor * red[0];
+}
+
+void launch_energy_reduce(const double* part, int count, double factor, double* out, cudaStream_t st) {
+  energy_reduce_kernel<<<1, 1024, 0, st>>>(part, count, factor, out);
+}
+
+void launch_zero(void* p, size_t bytes, cudaStream_t st) { cudaMemsetAsync(p, 0, bytes, st); }
+
+}  // namespace ace

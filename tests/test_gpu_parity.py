@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (Frobenius-relative, ||x - x_ref|| / ||x_ref||):
+* FP64 storage (r64, c128): 1e-10 on every output;
+* FP32 storage (c64): 1e-6 on W, V_X psi, E_x (FFT path in FP32 with FP64
+  twiddles; the bound is the one the FP32 mode is specified to meet), 1e-5 on
+  M, Xi and V_ACE psi (FP32 GEMMs over N_g ~ 1e5 terms; Xi also carries the
+  conditioning of L), 1e-5 on the gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1601_07159_gb300 import synth
+from tests.conftest import rel
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"c128": dict(w=1e-10, m=1e-10, xi=1e-10, y=1e-10, e=1e-10, g=1e-10),
+       "r64": dict(w=1e-10, m=1e-10, xi=1e-10, y=1e-10, e=1e-10, g=1e-10),
+       "c64": dict(w=1e-6, m=1e-5, xi=1e-5, y=1e-6, e=1e-6, g=1e-5)}
+
+
+@pytest.fixture(scope="module")
+def ace():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_07159_gb300 import build_lib
+    build_lib.build()
+    from paper_1601_07159_gb300 import ace as mod
+    return mod
+
+
+def _ecut(n, L):
+    # sphere well inside the grid's Nyquist box: |G|^2/2 <= 0.3 (pi n / L)^2
+    return min(synth.ECUT_HA, 0.3 * (math.pi * n / L) ** 2)
+
+
+def _inputs(n, L, nocc, nb, dtype, kernel, omega, seed):
+    s = synth.System(n=n, L=L, n_occ=nocc, n_bands=nb, real=(dtype == "r64"), kernel=kernel, omega=omega)
+    phi = synth.orbitals(s, seed, ecut=_ecut(n, L))
+    psi = synth.targets(s, seed, ecut=_ecut(n, L))
+    kern = oracle.coulomb_kernel((n, n, n), (L, L, L), kernel, omega)
+    return s, phi, psi, kern
+
+
+def _dev(a, dtype, ace):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(ace.TORCH_DTYPES[dtype]).cuda()
+
+
+def _host(t):
+    return t.detach().cpu().numpy().astype(np.complex128 if t.is_complex() else np.float64)
+
+
+CASES = [
+    # n, L, N, nb, dtype, kernel, omega
+    (8, 6.0, 5, 3, "c128", "erfc", 0.5),
+    (12, 7.0, 11, 7, "c128", "bare", 0.0),       # N = 8 + 3: ragged tile
+    (16, 8.0, 9, 4, "c64", "erfc", 0.3),
+    (20, 8.0, 6, 5, "c64", "bare", 0.0),         # radix 5
+    (24, 10.0, 8, 16, "r64", "bare", 0.0),       # the real Gamma-point 24^3 workload
+    (32, 11.0, 13, 9, "c64", "erfc", 0.106),
+    (36, 12.0, 10, 6, "c64", "erfc", 0.106),     # radix 3 x 3
+    (40, 14.0, 7, 3, "c128", "bare", 0.0),
+    (48, 20.5, 17, 5, "c64", "erfc", 0.106),     # the 48^3 edge, ragged N
+    (64, 27.3, 12, 4, "c64", "bare", 0.0),
+]
+
+
+@pytest.mark.parametrize("n,L,nocc,nb,dtype,kernel,omega", CASES)
+def test_build_apply_energy_parity(ace, n, L, nocc, nb, dtype, kernel, omega):
+    s, phi, psi, kern = _inputs(n, L, nocc, nb, dtype, kernel, omega, seed=1000 + n)
+    ref = oracle.ace_build(phi, kern, s.dv)
+    tol = TOL[dtype]
+    plan = ace.Plan(n, L, nocc, dtype=dtype, kernel=kernel, omega=omega)
+    phi_d, psi_d = _dev(phi, dtype, ace), _dev(psi, dtype, ace)
+
+    out = plan.build(phi_d)
+    code, piv = plan.status()
+    assert code == 0, (code, piv)
+    assert rel(_host(out["W"]), ref["W"]) < tol["w"]
+    m_ref = ref["M"].real if dtype == "r64" else ref["M"]
+    assert rel(_host(out["M"]), m_ref) < tol["m"]
+    assert rel(_host(out["Xi"]), ref["Xi"]) < tol["xi"]
+    assert abs(out["Ex"].item() - ref["Ex"]) < tol["e"] * abs(ref["Ex"])
+
+    y = plan.exchange_apply(phi_d, psi_d)
+    assert rel(_host(y), oracle.exchange_apply(phi, psi, kern)) < tol["y"]
+
+    ya = plan.apply(out["Xi"], psi_d)
+    assert rel(_host(ya), oracle.ace_apply(ref["Xi"], psi, s.dv)) < tol["xi"]
+
+    e_direct = oracle.energy_direct(phi, kern, s.volume)
+    ex, g = plan.energy_grad(phi_d, grad=True, grad_scale=0.75)
+    assert abs(ex.item() - e_direct) < tol["e"] * abs(e_direct)
+    assert rel(_host(g), 0.75 * oracle.energy_grad(phi, kern, s.dv)) < tol["g"]
+    ex_only, none = plan.energy_grad(phi_d, grad=False)
+    assert none is None and abs(ex_only.item() - ex.item()) <= 1e-12 * abs(ex.item())
+
+
+def test_bitwise_reproducible(ace):
+    s, phi, psi, kern = _inputs(24, 10.0, 19, 5, "c64", "erfc", 0.3, seed=5)
+    plan = ace.Plan(24, 10.0, 19, dtype="c64", kernel="erfc", omega=0.3, max_pairs=100, tile=4)
+    phi_d = _dev(phi, "c64", ace)
+    a = plan.build(phi_d)
+    b = plan.build(phi_d)
+    assert torch.equal(a["W"], b["W"]) and torch.equal(a["Xi"], b["Xi"])
+    # a different tile / batch schedule gives the same W to rounding
+    plan2 = ace.Plan(24, 10.0, 19, dtype="c64", kernel="erfc", omega=0.3, max_pairs=64, tile=8)
+    c = plan2.build(phi_d)
+    ref = oracle.exchange_W(phi, kern)
+    assert rel(_host(c["W"]), ref) < 1e-6 and rel(_host(a["W"]), ref) < 1e-6
+
+
+def test_single_orbital_and_empty(ace):
+    s, phi, psi, kern = _inputs(16, 8.0, 1, 2, "c128", "erfc", 0.4, seed=9)
+    plan = ace.Plan(16, 8.0, 1, dtype="c128", kernel="erfc", omega=0.4)
+    phi_d = _dev(phi, "c128", ace)
+    out = plan.build(phi_d)
+    assert rel(_host(out["W"]), oracle.exchange_W(phi, kern)) < 1e-10
+    empty = torch.empty((0, 16, 16, 16), dtype=torch.complex128, device="cuda")
+    y = plan.exchange_apply(phi_d, empty)
+    assert y.shape[0] == 0
+    assert plan.apply(out["Xi"], empty).shape[0] == 0
+
+
+def test_errors_reported(ace):
+    n, L = 16, 8.0
+    s, phi, psi, kern = _inputs(n, L, 4, 2, "c128", "bare", 0.0, seed=3)
+    plan = ace.Plan(n, L, 4, dtype="c128")
+    phi_d = _dev(phi, "c128", ace)
+    # workspace too small
+    lib = ace.lib()
+    import ctypes
+    y = plan.empty(2)
+    tiny = torch.empty(256, dtype=torch.uint8, device="cuda")
+    code = lib.ace_exchange_apply(plan._h, ctypes.c_void_p(phi_d.data_ptr()), ctypes.c_void_p(phi_d.data_ptr()),
+                                  2, ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(tiny.data_ptr()), 256, None)
+    assert code == ace.ACE_ERR_WORKSPACE
+    # aliasing output
+    with pytest.raises(ace.AceError) as ei:
+        plan.exchange_apply(phi_d, phi_d[:2].contiguous(), out=phi_d[:2])
+    assert ei.value.code in (ace.ACE_ERR_ARG,)
+    # -M singular: two identical orbitals -> non-positive pivot, reported on the status word
+    dup = phi.copy()
+    dup[3] = dup[2]
+    plan.build(_dev(dup, "c128", ace))
+    code, piv = plan.status()
+    assert code == ace.ACE_ERR_NOT_POSDEF and piv == 4
+    # non-finite input -> non-finite pivot
+    bad = phi.copy()
+    bad[0, 0, 0, 0] = np.nan
+    plan.build(_dev(bad, "c128", ace))
+    code, piv = plan.status()
+    assert code == ace.ACE_ERR_NONFINITE and piv == 1
+    # status clears after a good build
+    plan.build(phi_d)
+    assert plan.status() == (0, 0)
+
+
+def test_autograd_gradient_fd(ace):
+    """Gradient of E_x through the autograd Function: against the oracle and
+    against central differences of FP64 GPU energies (h = 1e-4)."""
+    n, L = 16, 8.0
+    s, phi, psi, kern = _inputs(n, L, 3, 1, "c128", "bare", 0.0, seed=21)
+    plan = ace.Plan(n, L, 3, dtype="c128")
+    phi_d = _dev(phi, "c128", ace).requires_grad_(True)
+    e = ace.exchange_energy(phi_d, plan)
+    (2.5 * e).backward()
+    g = _host(phi_d.grad)
+    assert rel(g, 2.5 * oracle.energy_grad(phi, kern, s.dv)) < 1e-10
+    h = 1e-4
+    errs = []
+    for d in synth.directions(phi.shape, 8, 77, s.dv):
+        dd = _dev(d, "c128", ace)
+        ep = plan.energy_grad(phi_d.detach() + h * dd)[0].item()
+        em = plan.energy_grad(phi_d.detach() - h * dd)[0].item()
+        fd = 2.5 * (ep - em) / (2 * h)
+        an = float(np.real(np.vdot(g, d)))
+        errs.append(abs(fd - an) / max(abs(an), 1e-12))
+    assert max(errs) < 1e-5
+
+
+def test_si64_full_size_sampled(ace):
+    """The 48^3, N = 128, 192-band screened workload in the launch
+    configuration the bench times (default plan): W, M on sampled orbitals
+    against the oracle; V_ACE Phi = W, E_x(1/2 tr M) = E_x(Parseval), and the
+    exchange apply on sampled bands."""
+    s = synth.SI64_48
+    seed = synth.seed_for(2)
+    phi = synth.orbitals(s, seed)
+    kern = oracle.coulomb_kernel((s.n,) * 3, (s.L,) * 3, s.kernel, s.omega)
+    plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega)
+    phi_d = _dev(phi, "c64", ace)
+    out = plan.build(phi_d)
+    assert plan.status() == (0, 0)
+    W = _host(out["W"])
+    M = _host(out["M"])
+    for i in (0, 37, 127):
+        w_ref = -np.sum(phi * oracle.poisson(np.conj(phi) * phi[i][None], kern), axis=0)
+        assert rel(W[i], w_ref) < 1e-6
+        m_col = s.dv * (np.conj(phi.reshape(s.n_occ, -1)) @ w_ref.ravel())
+        assert rel(M[:, i], m_col) < 1e-5
+    # Eq. ACEcond on the GPU's own outputs
+    vphi = plan.apply(out["Xi"], phi_d)
+    assert rel(_host(vphi), W) < 1e-5
+    ex, _ = plan.energy_grad(phi_d)
+    assert abs(ex.item() - out["Ex"].item()) < 2e-6 * abs(ex.item())
+    psi = synth.targets(s, seed, count=4)
+    y = plan.exchange_apply(phi_d, _dev(psi, "c64", ace))
+    assert rel(_host(y), oracle.exchange_apply(phi, psi, kern)) < 1e-6
