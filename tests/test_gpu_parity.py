@@ -144,9 +144,11 @@ def test_errors_reported(ace):
     with pytest.raises(ace.AceError) as ei:
         plan.exchange_apply(phi_d, phi_d[:2].contiguous(), out=phi_d[:2])
     assert ei.value.code in (ace.ACE_ERR_ARG,)
-    # -M singular: two identical orbitals -> non-positive pivot, reported on the status word
+    # -M singular: a zero orbital makes row/column 4 of M exactly zero, so the
+    # 4th pivot is exactly 0 -> reported on the status word (two equal orbitals
+    # would only give a rounding-level pivot of either sign)
     dup = phi.copy()
-    dup[3] = dup[2]
+    dup[3] = 0.0
     plan.build(_dev(dup, "c128", ace))
     code, piv = plan.status()
     assert code == ace.ACE_ERR_NOT_POSDEF and piv == 4
