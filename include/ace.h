@@ -148,6 +148,27 @@ ace_status ace_status_sync(ace_plan* plan, void* stream, int* info);
 ace_status ace_profile_begin(ace_plan* plan, int max_events);
 ace_status ace_profile_end(ace_plan* plan, double* ms_out, long long* counts_out);
 
+/* Size of the device array behind ace_apply_static (bytes, per GPU). */
+#define ACE_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* ace_apply_static: the same operation as ace_apply, Y = -Xi (dV Xi^* Psi),
+ * for callers that cannot allocate device memory or pass a workspace (for
+ * instance a plugin whose host application owns all device memory, or a
+ * fixed-latency loop where an allocation could block). The paper has no
+ * counterpart; this is a deployment variant of the apply.
+ * Its scratch is a file-scope device array of ACE_STATIC_SCRATCH_BYTES that
+ * every GPU loading the library keeps until the process exits; it holds
+ * 2 * n_occ * n_b complex FP64 values at least, so n_occ * n_b must be at
+ * most ACE_STATIC_SCRATCH_BYTES / 32 (524288), else ACE_ERR_ARG and nothing
+ * runs. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make it before any stream
+ * capture. All calls on a device share the array: calls that may overlap on
+ * the GPU (other streams, other plans) race and must be serialised by the
+ * caller. Nothing needs clearing between calls. Results equal ace_apply's up
+ * to the order of the split-K sums. Calls no allocator. */
+ace_status ace_apply_static(ace_plan* plan, const void* Xi, const void* Psi, int n_b, void* Y,
+                            void* stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char* ace_last_error(void);
 

@@ -72,6 +72,8 @@ _lib.ace_exchange_energy_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, _
 _lib.ace_exchange_energy_grad.restype = ctypes.c_int
 _lib.ace_status_sync.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int)]
 _lib.ace_status_sync.restype = ctypes.c_int
+_lib.ace_apply_static.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+_lib.ace_apply_static.restype = ctypes.c_int
 _lib.ace_profile_begin.argtypes = [_vp, ctypes.c_int]
 _lib.ace_profile_begin.restype = ctypes.c_int
 _lib.ace_profile_end.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
@@ -216,6 +218,15 @@ class Plan:
         _check(_lib.ace_apply(self._h, _ptr(xi), _ptr(psi), nb, _ptr(y), _ptr(ws), ws.numel(),
                               _stream()))
         return y
+
+    def apply_static(self, xi, psi, out):
+        """ace_apply_static: the apply without a workspace (the library's own
+        static device scratch; calls on one device must not overlap)."""
+        self._vec(xi, "xi")
+        self._vec(psi, "psi")
+        self._vec(out, "out")
+        _check(_lib.ace_apply_static(self._h, _ptr(xi), _ptr(psi), psi.shape[0], _ptr(out), _stream()))
+        return out
 
     def energy_grad(self, phi, grad: bool = False, grad_scale: float = 1.0, out=None):
         """E_x (Eq. EX) and optionally grad_scale * 2 dV W."""

@@ -217,6 +217,19 @@ PairLaunch base_launch(const ace_plan* p) {
 
 }  // namespace
 
+ace_status ace_internal_plan_info(const ace_plan* p, int* device, int* n_occ, long long* ng,
+                                  double* dv, int* f64, int* real) {
+  *device = p->device;
+  *n_occ = p->d.n_occ;
+  *ng = p->ng;
+  *dv = p->dv;
+  *f64 = p->f64 ? 1 : 0;
+  *real = p->real ? 1 : 0;
+  return ACE_OK;
+}
+
+ace_status ace_internal_set_error(ace_status s, const char* msg) { return fail(s, msg); }
+
 extern "C" {
 
 int ace_supported_edge(int n, int dtype) {
