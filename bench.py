@@ -47,6 +47,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--max-pairs", type=int, default=0, help="pair solves per batch (0 = plan default)")
+    p.add_argument("--tile", type=int, default=0, help="orbitals per tile side (0 = plan default)")
     return p.parse_args()
 
 
@@ -215,7 +217,8 @@ def run_ours(args):
 
     s = synth.SI64_48
     phi, psi = make_inputs(s, rank)
-    plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega)
+    plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega,
+                    max_pairs=args.max_pairs, tile=args.tile)
     td = torch.complex64
     phi_h = torch.from_numpy(phi).to(td).pin_memory()
     psi_h = torch.from_numpy(psi).to(td).pin_memory()

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libace.so")
-SOURCES = ["pair_f32.cu", "pair_f64.cu", "dense.cu", "ace_api.cu", "apply_static.cu"]
+SOURCES = ["pair_f32.cu", "pair_f64.cu", "dense.cu", "chol.cu", "ace_api.cu", "apply_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -241,96 +241,7 @@ void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C
   }
 }
 
-// ---------------------------------------------------------------- Cholesky + inverse (FP64)
-// work: 2 * n * n doubles (complex, row-major) receiving -M, factored in place
-// to L (lower). status[0] = ACE_ERR_NOT_POSDEF / ACE_ERR_NONFINITE, status[1] =
-// 1-based pivot, on failure. Single CTA, right-looking, one column per step.
-__global__ void __launch_bounds__(1024)
-cholesky_kernel(const double* __restrict__ M, int n, double* __restrict__ A, int* status) {
-  __shared__ int fail;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (long long i = tid; i < (long long)n * n; i += nt) {
-    A[2 * i] = -M[2 * i];
-    A[2 * i + 1] = -M[2 * i + 1];
-  }
-  if (tid == 0) fail = 0;
-  __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (tid == 0) {
-      const double d = A[2 * ((long long)j * n + j)];
-      if (!isfinite(d)) {
-        fail = 1;
-        status[0] = -3;
-        status[1] = j + 1;
-      } else if (!(d > 0.0)) {
-        fail = 1;
-        status[0] = -2;
-        status[1] = j + 1;
-      } else {
-        A[2 * ((long long)j * n + j)] = sqrt(d);
-        A[2 * ((long long)j * n + j) + 1] = 0.0;
-      }
-    }
-    __syncthreads();
-    if (fail) return;
-    const double inv = 1.0 / A[2 * ((long long)j * n + j)];
-    for (int i = j + 1 + tid; i < n; i += nt) {
-      A[2 * ((long long)i * n + j)] *= inv;
-      A[2 * ((long long)i * n + j) + 1] *= inv;
-    }
-    __syncthreads();
-    const int rem = n - j - 1;
-    for (long long e = tid; e < (long long)rem * rem; e += nt) {
-      const int i = j + 1 + (int)(e / rem), k = j + 1 + (int)(e % rem);
-      if (k > i) continue;
-      const double ar = A[2 * ((long long)i * n + j)], ai = A[2 * ((long long)i * n + j) + 1];
-      const double br = A[2 * ((long long)k * n + j)], bi = A[2 * ((long long)k * n + j) + 1];
-      // A[i][k] -= L[i][j] conj(L[k][j])
-      A[2 * ((long long)i * n + k)] -= ar * br + ai * bi;
-      A[2 * ((long long)i * n + k) + 1] -= ai * br - ar * bi;
-    }
-    __syncthreads();
-  }
-  for (long long e = tid; e < (long long)n * n; e += nt) {
-    const int i = (int)(e / n), k = (int)(e % n);
-    if (k > i) { A[2 * e] = 0.0; A[2 * e + 1] = 0.0; }
-  }
-}
-
-// X = L^{-1} column by column (thread = column c, forward substitution), then
-// LinvH[c][i] = conj(X[i][c]) so that Xi[k] = sum_i W[i] LinvH[i][k].
-__global__ void tri_inv_kernel(const double* __restrict__ Lm, int n, double* __restrict__ X,
-                               double* __restrict__ LinvH, const int* status) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= n || status[0] != 0) return;
-  for (int i = 0; i < n; ++i) {
-    double sr = 0.0, si = 0.0;
-    if (i >= c) {
-      sr = (i == c) ? 1.0 : 0.0;
-      for (int k = c; k < i; ++k) {
-        const double lr = Lm[2 * ((long long)i * n + k)], li = Lm[2 * ((long long)i * n + k) + 1];
-        const double xr = X[2 * ((long long)k * n + c)], xi = X[2 * ((long long)k * n + c) + 1];
-        sr -= lr * xr - li * xi;
-        si -= lr * xi + li * xr;
-      }
-      const double d = Lm[2 * ((long long)i * n + i)];
-      sr /= d;
-      si /= d;
-    }
-    X[2 * ((long long)i * n + c)] = sr;
-    X[2 * ((long long)i * n + c) + 1] = si;
-    LinvH[2 * ((long long)c * n + i)] = sr;
-    LinvH[2 * ((long long)c * n + i) + 1] = -si;
-  }
-}
-
-void launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
-                         cudaStream_t st) {
-  double* A = work;                       // 2 n^2
-  double* X = work + 2 * (long long)n * n;  // 2 n^2
-  cholesky_kernel<<<1, 1024, 0, st>>>(M, n, A, status);
-  tri_inv_kernel<<<(n + 31) / 32, 32, 0, st>>>(A, n, X, LinvH, status);
-}
+// Cholesky + inverse (FP64): chol.cu
 
 // ---------------------------------------------------------------- reductions
 __global__ void energy_reduce_kernel(const double* __restrict__ part, int count, double factor,

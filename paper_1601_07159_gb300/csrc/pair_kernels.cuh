@@ -79,7 +79,7 @@ template <typename R, int N> __host__ __device__ constexpr int plane_items() {
 
 // ---------------------------------------------------------------- pass A
 template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(N * plane_items<R, N>())
+__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
 pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
   constexpr int IPB = plane_items<R, N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -170,7 +170,7 @@ pass_b_kernel(const __grid_constant__ PairParams<R, N> P) {
 
 // ---------------------------------------------------------------- pass C
 template <typename R, int N>
-__global__ void __launch_bounds__(N * plane_items<R, N>())
+__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
 pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
   constexpr int IPB = plane_items<R, N>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -214,6 +214,63 @@ __device__ __forceinline__ void rmw_out(void* base, long long idx, cplx<R> acc, 
   }
 }
 
+// Full tiles (kTileMax orbitals per side): no runtime guards, so all loads of
+// the tile's pair potentials can be issued back to back. v is read once, so it
+// is loaded with the streaming (evict-first) hint.
+template <typename R, int N, bool REAL>
+__device__ __forceinline__ void pass_d_full_diag(const PairParams<R, N>& P, const TileDesc& d,
+                                                 const cplx<R>* __restrict__ V, long long g) {
+  constexpr long long NG = (long long)N * N * N;
+  constexpr int B = kTileMax;
+  cplx<R> x[B], acc[B];
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    acc[o] = cmk<cplx<R>>(R(0), R(0));
+    x[o] = load_vec<R, REAL>(P.X, (long long)(d.l0 + o) * P.ld + g);
+  }
+#pragma unroll
+  for (int li = 0; li < B; ++li) {
+#pragma unroll
+    for (int ri = li; ri < B; ++ri) {
+      const int q = li * B - li * (li - 1) / 2 + (ri - li);
+      const cplx<R> v = __ldcs(V + (long long)q * NG);
+      acc[ri] = cadd(acc[ri], cmul(x[li], v));
+      if (ri != li) acc[li] = cadd(acc[li], cmulc(v, x[ri]));
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < B; ++o) rmw_out<R, REAL>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
+}
+
+template <typename R, int N, bool REAL>
+__device__ __forceinline__ void pass_d_full_off(const PairParams<R, N>& P, const TileDesc& d,
+                                                const cplx<R>* __restrict__ V, long long g) {
+  constexpr long long NG = (long long)N * N * N;
+  constexpr int B = kTileMax;
+  cplx<R> xl[B], yr[B], al[B], ar[B];
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    al[o] = cmk<cplx<R>>(R(0), R(0));
+    ar[o] = al[o];
+    xl[o] = load_vec<R, REAL>(P.X, (long long)(d.l0 + o) * P.ld + g);
+    yr[o] = load_vec<R, REAL>(P.Y, (long long)(d.r0 + o) * P.ld + g);
+  }
+#pragma unroll
+  for (int li = 0; li < B; ++li) {
+#pragma unroll
+    for (int ri = 0; ri < B; ++ri) {
+      const cplx<R> v = __ldcs(V + (long long)(li * B + ri) * NG);
+      ar[ri] = cadd(ar[ri], cmul(xl[li], v));
+      al[li] = cadd(al[li], cmulc(v, yr[ri]));
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    rmw_out<R, REAL>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+    rmw_out<R, REAL>(P.OutX, (long long)(d.l0 + o) * P.ld + g, al[o], P.scale);
+  }
+}
+
 template <typename R, int N, bool REAL>
 __global__ void __launch_bounds__(256)
 pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
@@ -222,7 +279,11 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
   if (g >= NG) return;
   const TileDesc d = P.batch.t[blockIdx.y];
   const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
-  if (d.kind == 1) {
+  if (d.kind == 1 && d.nl == kTileMax) {
+    pass_d_full_diag<R, N, REAL>(P, d, V, g);
+  } else if (d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
+    pass_d_full_off<R, N, REAL>(P, d, V, g);
+  } else if (d.kind == 1) {
     cplx<R> x[kTileMax], acc[kTileMax];
 #pragma unroll
     for (int o = 0; o < kTileMax; ++o) {
@@ -319,6 +380,9 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
     cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   }
   PairParams<R, N> P;
   fill_params<R, N>(P, L, b);
