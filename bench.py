@@ -49,6 +49,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--max-pairs", type=int, default=0, help="pair solves per batch (0 = plan default)")
     p.add_argument("--tile", type=int, default=0, help="orbitals per tile side (0 = plan default)")
+    p.add_argument("--lanes", type=int, default=0, help="concurrent batch streams (0 = plan default)")
+    p.add_argument("--eager", action="store_true", help="launch batches eagerly (per-pass timings)")
     return p.parse_args()
 
 
@@ -218,7 +220,8 @@ def run_ours(args):
     s = synth.SI64_48
     phi, psi = make_inputs(s, rank)
     plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega,
-                    max_pairs=args.max_pairs, tile=args.tile)
+                    max_pairs=args.max_pairs, tile=args.tile, lanes=args.lanes,
+                    graphs=not args.eager)
     td = torch.complex64
     phi_h = torch.from_numpy(phi).to(td).pin_memory()
     psi_h = torch.from_numpy(psi).to(td).pin_memory()
@@ -310,6 +313,9 @@ def run_ours(args):
                 "D": 8.0 * ng * pairs + 2.0 * s.n_occ * ng * 8 * 2}
     passes = {}
     for k, ms in prof["pass_ms"].items():
+        if not math.isfinite(ms):     # graph replay: per-pass shares come from the ncu launch list
+            passes = None
+            break
         per = ms / K
         passes[k] = {"ms_per_build": per, "share": ms / max(prof["pair_ms"], 1e-12),
                      "alg_GBps": pass_alg[k] / (per / 1e3) / 1e9 if per > 0 else None}

@@ -76,7 +76,14 @@ typedef struct {
   int max_pairs;     /* pair solves in flight per batch (0 = library default); sets the
                         size of the pair-spectrum scratch in the workspace */
   int tile;          /* orbitals per pair tile, 1..8 (0 = default 8) */
+  int lanes;         /* concurrent batch streams inside one call, 1..8 (0 = default 2);
+                        the pair scratch is lanes * max_pairs slots */
+  int flags;         /* ACE_FLAG_* */
 } ace_desc;
+
+/* Launch each pair batch eagerly instead of replaying a captured CUDA graph
+ * (graphs are keyed by the call's pointers; see ace_build). */
+#define ACE_FLAG_NO_GRAPH 1
 
 typedef struct ace_plan ace_plan;
 
@@ -103,7 +110,14 @@ size_t ace_workspace_size(const ace_plan* plan, int op, int n_b);
 ace_status ace_exchange_apply(ace_plan* plan, const void* Phi, const void* Psi, int n_b,
                               void* Y, void* ws, size_t ws_bytes, void* stream);
 
-/* ACE construction (Alg. 2, steps 2-3): W = V_X[Phi] Phi with N(N+1)/2 unique
+/* Graphs: ace_exchange_apply, ace_build and ace_exchange_energy_grad record the
+ * kernels of their pair-solve section into a CUDA graph on first use with a
+ * given set of pointers (and n_b), keep up to 8 such graphs per plan, and
+ * replay them on later calls with the same pointers; a call with new pointers
+ * captures a new graph (a few milliseconds, on a plan-owned stream). The
+ * graph is launched on `stream`, so ordering with the caller's work is kept.
+ *
+ * ACE construction (Alg. 2, steps 2-3): W = V_X[Phi] Phi with N(N+1)/2 unique
  * pair solves (v_ij = conj(v_ji) halves the work), M = dV Phi^* W made
  * Hermitian, -M = L L^* (FP64), Xi = W L^{-*}.
  * Phi: N vectors (orthonormal in <.,.> for Eq. ACEcond to hold, not checked).

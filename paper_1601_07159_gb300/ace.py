@@ -48,6 +48,8 @@ class Desc(ctypes.Structure):
         ("alpha", ctypes.c_double),
         ("max_pairs", ctypes.c_int),
         ("tile", ctypes.c_int),
+        ("lanes", ctypes.c_int),
+        ("flags", ctypes.c_int),
     ]
 
 
@@ -113,7 +115,7 @@ class Plan:
 
     def __init__(self, n: int, L, n_occ: int, dtype: str = "c64", kernel: str = "bare",
                  omega: float = 0.0, g0: float | None = None, alpha: float = 1.0,
-                 max_pairs: int = 0, tile: int = 0):
+                 max_pairs: int = 0, tile: int = 0, lanes: int = 0, graphs: bool = True):
         if isinstance(L, (int, float)):
             L = (float(L),) * 3
         d = Desc()
@@ -127,6 +129,8 @@ class Plan:
         d.alpha = alpha
         d.max_pairs = max_pairs
         d.tile = tile
+        d.lanes = lanes
+        d.flags = 0 if graphs else 1
         h = _vp()
         _check(_lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h

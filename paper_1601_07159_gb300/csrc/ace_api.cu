@@ -1,8 +1,11 @@
 // C ABI of the ACE hot path: plan creation (kernel table, twiddles, pair-tile
-// schedule), workspace sizing and the four entry points of include/ace.h.
+// schedule), workspace sizing, CUDA-graph replay of the pair-solve section and
+// the entry points of include/ace.h.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -28,6 +31,28 @@ ace_status cuda_check(const char* what) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+constexpr int kMaxLanes = 8;
+constexpr int kMaxGraphs = 8;
+
+// Batches in the order they run; batches of one round write disjoint outputs
+// and may run concurrently.
+struct Schedule {
+  std::vector<Batch> batches;
+  std::vector<int> round;
+};
+
+struct GraphEntry {
+  uintptr_t key[8] = {};
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+  unsigned long long last_use = 0;
+};
+
+struct ProfRec {
+  size_t first;   // index of the first event
+  int kind;       // 0: 5 events around passes A..D of one batch; 1: 2 events around a section
+};
+
 }  // namespace
 
 struct ace_plan {
@@ -39,25 +64,34 @@ struct ace_plan {
   bool f64 = false, real = false;
   size_t csize = 0;              // bytes per complex scratch element
   size_t vsize = 0;              // bytes per stored vector element
-  int max_pairs = 0, tile = 0;
+  int max_pairs = 0, tile = 0, lanes = 1;
+  bool graphs = true;
   std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
-  std::vector<Batch> build_batches;
+  Schedule build;                // symmetric schedule of the W build
+  std::deque<std::pair<int, Schedule>> rect;   // one-sided schedules by n_b
   void* Kt = nullptr;            // kernel table (float or double)
   double* Mc = nullptr;          // 2 N^2, M (complex, row-major)
-  double* work = nullptr;        // 4 N^2, Cholesky factor + inverse
+  double* work = nullptr;        // 4 N^2, Cholesky work (global fallback)
   double* LinvH = nullptr;       // 2 N^2, L^{-*}
   int* status = nullptr;         // [code, pivot]
+  cudaStream_t cap = nullptr;    // capture stream
+  cudaStream_t lane[kMaxLanes] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kMaxLanes] = {};
+  std::vector<GraphEntry> graph_cache;
+  unsigned long long use_clock = 0;
   long long launches = 0;        // kernel launches issued (instrumentation)
-  std::vector<cudaEvent_t> ev;   // profiling events (5 per recorded batch)
+  std::vector<cudaEvent_t> ev;   // profiling events
   size_t ev_used = 0;
   long long ev_dropped = 0;
+  std::vector<ProfRec> prof;
 };
 
 namespace {
 
 // Tournament ("circle") schedule over orbital blocks: every round pairs each
 // block with exactly one other, so the tiles of a round write disjoint outputs.
-std::vector<Batch> make_sym_schedule(int N, int b, int max_pairs) {
+Schedule make_sym_schedule(int N, int b, int max_pairs) {
   const int B = (N + b - 1) / b;
   auto blk = [&](int I, int& o0, int& no) { o0 = I * b; no = (I * b + b <= N) ? b : N - I * b; };
   std::vector<std::vector<TileDesc>> rounds;
@@ -77,8 +111,7 @@ std::vector<Batch> make_sym_schedule(int N, int b, int max_pairs) {
       tiles.push_back(t);
     }
     rounds.push_back(tiles);
-    // rotate all but the first entry
-    const int last = arr[Bp - 1];
+    const int last = arr[Bp - 1];   // rotate all but the first entry
     for (int i = Bp - 1; i > 1; --i) arr[i] = arr[i - 1];
     arr[1] = last;
   }
@@ -92,33 +125,40 @@ std::vector<Batch> make_sym_schedule(int N, int b, int max_pairs) {
     diag.push_back(t);
   }
   rounds.push_back(diag);
-  std::vector<Batch> out;
+  Schedule out;
+  int rid = 0;
   for (auto& r : rounds) {
     Batch cur{};
     for (auto& t : r) {
       const int np = tile_pairs(t);
       if (cur.ntiles > 0 && (cur.npairs + np > max_pairs || cur.ntiles == kMaxTiles)) {
-        out.push_back(cur);
+        out.batches.push_back(cur);
+        out.round.push_back(rid);
         cur = Batch{};
       }
       t.slot0 = cur.npairs;
       cur.t[cur.ntiles++] = t;
       cur.npairs += np;
     }
-    if (cur.ntiles > 0) out.push_back(cur);
+    if (cur.ntiles > 0) {
+      out.batches.push_back(cur);
+      out.round.push_back(rid);
+    }
+    ++rid;
   }
   return out;
 }
 
 // One-sided schedule for V_X[Phi] Psi: r-blocks of Psi (<= b), l-chunks of Phi;
-// a batch holds tiles of one l-chunk, so its tiles write distinct Psi blocks.
-std::vector<Batch> make_rect_schedule(int N, int nb, int b, int max_pairs) {
-  std::vector<Batch> out;
+// a round holds the tiles of one l-chunk, which write distinct Psi blocks.
+Schedule make_rect_schedule(int N, int nb, int b, int max_pairs) {
+  Schedule out;
   const int nrb = (nb + b - 1) / b;
   int lc = max_pairs / b;
   if (lc < 1) lc = 1;
   if (lc > N) lc = N;
-  for (int l0 = 0; l0 < N; l0 += lc) {
+  int rid = 0;
+  for (int l0 = 0; l0 < N; l0 += lc, ++rid) {
     const int nl = (l0 + lc <= N) ? lc : N - l0;
     Batch cur{};
     for (int R = 0; R < nrb; ++R) {
@@ -130,14 +170,18 @@ std::vector<Batch> make_rect_schedule(int N, int nb, int b, int max_pairs) {
       t.kind = 2;
       const int np = tile_pairs(t);
       if (cur.ntiles > 0 && (cur.npairs + np > max_pairs || cur.ntiles == kMaxTiles)) {
-        out.push_back(cur);
+        out.batches.push_back(cur);
+        out.round.push_back(rid);
         cur = Batch{};
       }
       t.slot0 = cur.npairs;
       cur.t[cur.ntiles++] = t;
       cur.npairs += np;
     }
-    if (cur.ntiles > 0) out.push_back(cur);
+    if (cur.ntiles > 0) {
+      out.batches.push_back(cur);
+      out.round.push_back(rid);
+    }
   }
   return out;
 }
@@ -151,7 +195,9 @@ struct WsLayout {
   size_t total = 0;
 };
 
-int epart_count(const ace_plan* p) { return energy_blocks(p->n, p->max_pairs, p->f64) + 1; }
+int epart_per_lane(const ace_plan* p) { return energy_blocks(p->n, p->max_pairs, p->f64) + 1; }
+size_t slot_bytes(const ace_plan* p) { return (size_t)p->ng * p->csize; }
+size_t lane_bytes(const ace_plan* p) { return align256((size_t)p->max_pairs * slot_bytes(p)); }
 
 WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   WsLayout L;
@@ -160,8 +206,9 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   const int N = p->d.n_occ;
   const int splits = gram_splits(p->ng);
   if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD)
-    L.S = take((size_t)p->max_pairs * p->ng * p->csize);
-  if (op == ACE_OP_ENERGY_GRAD) L.Epart = (double*)take((size_t)epart_count(p) * sizeof(double));
+    L.S = take((size_t)p->lanes * lane_bytes(p));
+  if (op == ACE_OP_ENERGY_GRAD)
+    L.Epart = (double*)take((size_t)p->lanes * epart_per_lane(p) * sizeof(double));
   if (op == ACE_OP_BUILD) {
     L.part = (double*)take((size_t)splits * N * N * 2 * sizeof(double));
     L.Wtmp = take((size_t)N * p->ng * p->vsize);
@@ -189,19 +236,109 @@ ace_status check_common(ace_plan* p, void* ws, size_t ws_bytes, int op, int nb) 
   return ACE_OK;
 }
 
-bool launch_batch(ace_plan* p, const PairLaunch& L0, const Batch& b, cudaStream_t st) {
-  PairLaunch L = L0;
-  L.ev = nullptr;
-  if (!p->ev.empty()) {
-    if (p->ev_used + 5 <= p->ev.size()) {
-      L.ev = &p->ev[p->ev_used];
-      p->ev_used += 5;
-    } else {
-      ++p->ev_dropped;
-    }
-  }
-  p->launches += pair_batch_launches(L.mode);
+bool launch_one(const ace_plan* p, const PairLaunch& L, const Batch& b, cudaStream_t st) {
   return p->f64 ? launch_pair_batch_f64(L, b, st) : launch_pair_batch_f32(L, b, st);
+}
+
+cudaEvent_t* take_events(ace_plan* p, int count, int kind) {
+  if (p->ev.empty()) return nullptr;
+  if (p->ev_used + (size_t)count > p->ev.size()) {
+    ++p->ev_dropped;
+    return nullptr;
+  }
+  cudaEvent_t* e = &p->ev[p->ev_used];
+  p->prof.push_back(ProfRec{p->ev_used, kind});
+  p->ev_used += (size_t)count;
+  return e;
+}
+
+// Run the pair-solve section: eagerly (each batch in order on `st`, lane 0
+// scratch) when graphs are off or per-pass profiling needs events between
+// kernels, else by replaying (capturing on first use) a graph in which the
+// batches of one round are spread over the plan's lanes.
+ace_status run_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, char* S0, double* E0,
+                     cudaStream_t st, const uintptr_t key_in[6]) {
+  const bool eager = !p->graphs;
+  if (eager) {
+    for (const Batch& b : sc.batches) {
+      PairLaunch L = base;
+      L.S = S0;
+      L.Epart = E0;
+      L.ev = take_events(p, 5, 0);
+      p->launches += pair_batch_launches(L.mode);
+      if (!launch_one(p, L, b, st)) return fail(ACE_ERR_UNSUPPORTED, "edge not built");
+    }
+    return cuda_check("pair section");
+  }
+  uintptr_t key[8] = {key_in[0], key_in[1], key_in[2], key_in[3], key_in[4], key_in[5],
+                      (uintptr_t)base.mode, 0};
+  GraphEntry* hit = nullptr;
+  for (auto& g : p->graph_cache)
+    if (std::memcmp(g.key, key, sizeof(key)) == 0) hit = &g;
+  if (!hit) {
+    if ((int)p->graph_cache.size() >= kMaxGraphs) {
+      size_t victim = 0;
+      for (size_t i = 1; i < p->graph_cache.size(); ++i)
+        if (p->graph_cache[i].last_use < p->graph_cache[victim].last_use) victim = i;
+      cudaGraphExecDestroy(p->graph_cache[victim].exec);
+      p->graph_cache.erase(p->graph_cache.begin() + victim);
+    }
+    GraphEntry g;
+    std::memcpy(g.key, key, sizeof(key));
+    const int nl = p->lanes;
+    cudaStream_t cs = p->cap;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return cuda_check("graph capture begin");
+    auto fork = [&]() {
+      cudaEventRecord(p->fork_ev, cs);
+      for (int i = 0; i < nl; ++i) cudaStreamWaitEvent(p->lane[i], p->fork_ev, 0);
+    };
+    auto join = [&]() {
+      for (int i = 0; i < nl; ++i) {
+        cudaEventRecord(p->join_ev[i], p->lane[i]);
+        cudaStreamWaitEvent(cs, p->join_ev[i], 0);
+      }
+    };
+    fork();
+    int cur = sc.round.empty() ? 0 : sc.round[0], k_in_round = 0;
+    bool ok = true;
+    for (size_t k = 0; k < sc.batches.size(); ++k) {
+      if (sc.round[k] != cur) {
+        join();
+        fork();
+        cur = sc.round[k];
+        k_in_round = 0;
+      }
+      const int ln = k_in_round++ % nl;
+      PairLaunch L = base;
+      L.S = S0 + (size_t)ln * lane_bytes(p);
+      L.Epart = E0 ? E0 + (size_t)ln * epart_per_lane(p) : nullptr;
+      L.ev = nullptr;
+      g.kernels += pair_batch_launches(L.mode);
+      ok = ok && launch_one(p, L, sc.batches[k], p->lane[ln]);
+    }
+    join();
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e1 = cudaStreamEndCapture(cs, &graph);
+    if (!ok || e1 != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return ok ? fail(ACE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e1))
+                : fail(ACE_ERR_UNSUPPORTED, "edge not built");
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) return fail(ACE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e2));
+    p->graph_cache.push_back(g);
+    hit = &p->graph_cache.back();
+  }
+  hit->last_use = ++p->use_clock;
+  cudaEvent_t* ev = take_events(p, 2, 1);
+  if (ev) cudaEventRecord(ev[0], st);
+  if (cudaGraphLaunch(hit->exec, st) != cudaSuccess) return cuda_check("graph launch");
+  if (ev) cudaEventRecord(ev[1], st);
+  p->launches += hit->kernels;
+  return cuda_check("pair section");
 }
 
 PairLaunch base_launch(const ace_plan* p) {
@@ -212,7 +349,13 @@ PairLaunch base_launch(const ace_plan* p) {
   L.tw = p->tw.data();
   L.real_io = p->real;
   L.scale = 1.0;
+  L.prepare_only = false;
   return L;
+}
+
+void drop_graphs(ace_plan* p) {
+  for (auto& g : p->graph_cache) cudaGraphExecDestroy(g.exec);
+  p->graph_cache.clear();
 }
 
 }  // namespace
@@ -247,6 +390,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   if (d->dtype < ACE_DTYPE_R64 || d->dtype > ACE_DTYPE_C64) return fail(ACE_ERR_ARG, "bad dtype");
   if (d->kernel != ACE_KERNEL_BARE && d->kernel != ACE_KERNEL_ERFC) return fail(ACE_ERR_ARG, "bad kernel");
   if (d->n_occ < 1) return fail(ACE_ERR_ARG, "n_occ must be >= 1");
+  if (d->n_occ > 1024) return fail(ACE_ERR_UNSUPPORTED, "n_occ > 1024 not supported");
   if (!(d->L[0] > 0 && d->L[1] > 0 && d->L[2] > 0)) return fail(ACE_ERR_ARG, "cell edges must be > 0");
   if (d->kernel == ACE_KERNEL_ERFC && !(d->omega > 0)) return fail(ACE_ERR_ARG, "omega must be > 0");
   if (!std::isfinite(d->alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
@@ -254,6 +398,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     return fail(ACE_ERR_UNSUPPORTED, "grid edge " + std::to_string(d->n) + " not built for this dtype");
   if (d->tile < 0 || d->tile > kTileMax) return fail(ACE_ERR_ARG, "tile must be 0..8");
   if (d->max_pairs < 0) return fail(ACE_ERR_ARG, "max_pairs must be >= 0");
+  if (d->lanes < 0 || d->lanes > kMaxLanes) return fail(ACE_ERR_ARG, "lanes must be 0..8");
 
   ace_plan* p = new ace_plan();
   p->d = *d;
@@ -267,16 +412,21 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->csize = p->f64 ? 16 : 8;
   p->vsize = p->real ? 8 : p->csize;
   p->tile = d->tile ? d->tile : kTileMax;
+  p->lanes = d->lanes ? d->lanes : 2;
+  p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
   const size_t slot = (size_t)p->ng * p->csize;
+  const int tt = p->tile * p->tile;
   if (d->max_pairs) {
     p->max_pairs = d->max_pairs;
   } else {
-    const long long budget = (512ll << 20) / (long long)slot;
-    p->max_pairs = (int)(budget > 1 ? budget : 1);
-    const long long total = (long long)d->n_occ * (d->n_occ + 1) / 2;
-    if (p->max_pairs > total) p->max_pairs = (int)total;
+    // a batch of whole tiles whose scratch (~64 MB per lane) stays in L2
+    // between the passes
+    long long tiles = (64ll << 20) / ((long long)tt * (long long)slot);
+    if (tiles < 1) tiles = 1;
+    if (tiles > kMaxTiles) tiles = kMaxTiles;
+    p->max_pairs = (int)(tiles * tt);
   }
-  if (p->max_pairs < p->tile * p->tile) p->max_pairs = p->tile * p->tile;
+  if (p->max_pairs < tt) p->max_pairs = tt;
 
   // twiddles exp(-2 pi i k/n) in FP64
   const int n = p->n;
@@ -319,12 +469,24 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   if (e == cudaSuccess) e = cudaMalloc(&p->LinvH, (size_t)2 * N * N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->status, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->status, 0, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
+  for (int i = 0; i < p->lanes && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&p->lane[i], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
+  for (int i = 0; i < p->lanes && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    PairLaunch prep = base_launch(p);
+    prep.prepare_only = true;
+    Batch none{};
+    launch_one(p, prep, none, nullptr);
+    prepare_cholesky(N);
+    e = cudaGetLastError();
+  }
   if (e != cudaSuccess) {
-    std::string m = std::string("plan allocation: ") + cudaGetErrorString(e);
+    std::string m = std::string("plan set-up: ") + cudaGetErrorString(e);
     ace_plan_destroy(p);
     return fail(ACE_ERR_CUDA, m);
   }
-  p->build_batches = make_sym_schedule(N, p->tile, p->max_pairs);
+  p->build = make_sym_schedule(N, p->tile, p->max_pairs);
   *out = p;
   return ACE_OK;
 }
@@ -332,7 +494,14 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
 ace_status ace_plan_destroy(ace_plan* p) {
   if (!p) return ACE_OK;
   cudaDeviceSynchronize();
+  drop_graphs(p);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+  for (int i = 0; i < kMaxLanes; ++i) {
+    if (p->lane[i]) cudaStreamDestroy(p->lane[i]);
+    if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
+  }
+  if (p->cap) cudaStreamDestroy(p->cap);
+  if (p->fork_ev) cudaEventDestroy(p->fork_ev);
   cudaFree(p->Kt);
   cudaFree(p->Mc);
   cudaFree(p->work);
@@ -365,10 +534,18 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
   L.Y = Psi;
   L.OutX = nullptr;
   L.OutY = Y;
-  L.S = W.S;
   L.mode = 0;
-  for (const Batch& b : make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs))
-    if (!launch_batch(p, L, b, st)) return fail(ACE_ERR_UNSUPPORTED, "edge not built");
+  // the one-sided schedule depends on n_b; the plan keeps one per n_b seen
+  const Schedule* sc = nullptr;
+  for (auto& c : p->rect)
+    if (c.first == nb) sc = &c.second;
+  if (!sc) {
+    p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
+    sc = &p->rect.back().second;
+  }
+  const uintptr_t key[6] = {(uintptr_t)Phi, (uintptr_t)Psi, (uintptr_t)Y, (uintptr_t)ws, (uintptr_t)nb, 1};
+  s = run_pairs(p, L, *sc, W.S, nullptr, st, key);
+  if (s != ACE_OK) return s;
   return cuda_check("ace_exchange_apply");
 }
 
@@ -393,10 +570,10 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   L.Y = Phi;
   L.OutX = W;
   L.OutY = W;
-  L.S = Wl.S;
   L.mode = 0;
-  for (const Batch& b : p->build_batches)
-    if (!launch_batch(p, L, b, st)) return fail(ACE_ERR_UNSUPPORTED, "edge not built");
+  const uintptr_t key[6] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, 0, 0, 2};
+  s = run_pairs(p, L, p->build, Wl.S, nullptr, st, key);
+  if (s != ACE_OK) return s;
   // M = dV Phi^* W, Hermitian part (Eq. ACEconstruct2); E_x = 1/2 Re tr M
   const int splits = gram_splits(p->ng);
   launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, st);
@@ -405,7 +582,7 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   // -M = L L^* and L^{-*} in FP64; Xi = W L^{-*} (Eq. Wtilde)
   launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, st);
   launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, st);
-  p->launches += 2 + (Ex_out ? 1 : 0) + (M_out ? 1 : 0) + 2 + 1;
+  p->launches += 2 + (Ex_out ? 1 : 0) + (M_out ? 1 : 0) + 1 + 1;
   return cuda_check("ace_build");
 }
 
@@ -441,7 +618,7 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   cudaStream_t st = (cudaStream_t)stream;
   const int N = p->d.n_occ;
   const WsLayout Wl = layout(p, ACE_OP_ENERGY_GRAD, 0, (char*)ws);
-  const int ecount = epart_count(p);
+  const int ecount = p->lanes * epart_per_lane(p);
   cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), st);
   if (grad_out) cudaMemsetAsync(grad_out, 0, (size_t)N * p->ng * p->vsize, st);
   PairLaunch L = base_launch(p);
@@ -449,12 +626,15 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   L.Y = Phi;
   L.OutX = grad_out;
   L.OutY = grad_out;
-  L.S = Wl.S;
-  L.Epart = Wl.Epart;
   L.mode = grad_out ? 2 : 1;
-  L.scale = 2.0 * p->dv * grad_scale;     // grad = grad_scale * 2 dV W
-  for (const Batch& b : p->build_batches)
-    if (!launch_batch(p, L, b, st)) return fail(ACE_ERR_UNSUPPORTED, "edge not built");
+  L.scale = 2.0 * p->dv;                   // grad = 2 dV W, then * grad_scale
+  const uintptr_t key[6] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)ws, 0, 0, 3};
+  s = run_pairs(p, L, p->build, Wl.S, Wl.Epart, st, key);
+  if (s != ACE_OK) return s;
+  if (grad_out && grad_scale != 1.0) {
+    launch_scale(p->f64, p->real, grad_out, (long long)N * p->ng, grad_scale, st);
+    p->launches += 1;
+  }
   // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2  (Kt = alpha K / N_g)
   launch_energy_reduce(Wl.Epart, ecount, -0.5 * p->vol / (double)p->ng, Ex_out, st);
   p->launches += 1;
@@ -473,6 +653,7 @@ ace_status ace_profile_begin(ace_plan* p, int max_events) {
     }
   p->ev_used = 0;
   p->ev_dropped = 0;
+  p->prof.clear();
   p->launches = 0;
   return ACE_OK;
 }
@@ -481,23 +662,33 @@ ace_status ace_profile_end(ace_plan* p, double* ms_out, long long* counts_out) {
   if (!p) return fail(ACE_ERR_ARG, "plan is NULL");
   if (cudaDeviceSynchronize() != cudaSuccess) return cuda_check("ace_profile_end");
   double ms[5] = {0, 0, 0, 0, 0};
-  const size_t batches = p->ev_used / 5;
-  for (size_t b = 0; b < batches; ++b) {
-    for (int k = 0; k < 4; ++k) {
+  bool per_pass = false;
+  long long recs = 0;
+  for (const ProfRec& r : p->prof) {
+    ++recs;
+    if (r.kind == 0) {
+      per_pass = true;
+      for (int k = 0; k < 4; ++k) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, p->ev[r.first + k], p->ev[r.first + k + 1]) == cudaSuccess) ms[k] += t;
+      }
+    } else {
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, p->ev[5 * b + k], p->ev[5 * b + k + 1]) == cudaSuccess) ms[k] += t;
+      if (cudaEventElapsedTime(&t, p->ev[r.first], p->ev[r.first + 1]) == cudaSuccess) ms[4] += t;
     }
   }
-  ms[4] = ms[0] + ms[1] + ms[2] + ms[3];
+  if (per_pass) ms[4] += ms[0] + ms[1] + ms[2] + ms[3];
+  else ms[0] = ms[1] = ms[2] = ms[3] = std::numeric_limits<double>::quiet_NaN();
   if (ms_out)
     for (int k = 0; k < 5; ++k) ms_out[k] = ms[k];
   if (counts_out) {
-    counts_out[0] = (long long)batches;
+    counts_out[0] = recs;
     counts_out[1] = p->launches;
     counts_out[2] = p->ev_dropped;
   }
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   p->ev.clear();
+  p->prof.clear();
   p->ev_used = 0;
   return cuda_check("ace_profile_end");
 }

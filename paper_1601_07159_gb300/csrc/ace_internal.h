@@ -45,6 +45,7 @@ struct PairLaunch {
   bool real_io;          // R64 vectors
   int mode;              // 0: W / Y accumulate; 1: energy only; 2: energy + accumulate
   cudaEvent_t* ev;       // nullable: 5 events recorded around passes A, B, C, D
+  bool prepare_only;     // set kernel attributes for edge n, launch nothing
 };
 // Kernel launches issued by one pair batch for a mode (4, or 2 for energy only).
 inline int pair_batch_launches(int mode) { return mode == 1 ? 2 : 4; }
@@ -64,6 +65,8 @@ void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C
                   long long ld, long long ng, double alpha, void* Out, cudaStream_t st);
 void launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
                          cudaStream_t st);
+void prepare_cholesky(int n);
+void launch_scale(bool f64, bool real, void* X, long long count, double s, cudaStream_t st);
 void launch_energy_reduce(const double* part, int count, double factor, double* out, cudaStream_t st);
 void launch_zero(void* p, size_t bytes, cudaStream_t st);
 

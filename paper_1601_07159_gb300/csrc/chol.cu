@@ -109,11 +109,33 @@ chol_inv_kernel(const double* __restrict__ M, int n, Cpx* __restrict__ gA, doubl
 
 }  // namespace
 
+void prepare_cholesky(int n) {
+  const size_t packed = (size_t)n * (n + 1) / 2 * sizeof(Cpx);
+  if (packed <= 200 * 1024)
+    cudaFuncSetAttribute(chol_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)packed);
+}
+
+__global__ void scale_kernel_f(float* x, long long count, float s) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+__global__ void scale_kernel_d(double* x, long long count, double s) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
+// X *= s over `count` stored vector elements (real and imaginary parts alike).
+void launch_scale(bool f64, bool real, void* X, long long count, double s, cudaStream_t st) {
+  const long long nreal = real ? count : 2 * count;
+  const unsigned grid = (unsigned)((nreal + 255) / 256 < 152 * 16 ? (nreal + 255) / 256 : 152 * 16);
+  if (f64) scale_kernel_d<<<grid, 256, 0, st>>>(static_cast<double*>(X), nreal, s);
+  else scale_kernel_f<<<grid, 256, 0, st>>>(static_cast<float*>(X), nreal, (float)s);
+}
+
 void launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
                          cudaStream_t st) {
   const size_t packed = (size_t)n * (n + 1) / 2 * sizeof(Cpx);
   if (n <= 1024 && packed <= 200 * 1024) {
-    cudaFuncSetAttribute(chol_inv_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)packed);
     chol_inv_kernel<true><<<1, 1024, packed, st>>>(M, n, nullptr, LinvH, status);
   } else {
     chol_inv_kernel<false><<<1, 1024, 0, st>>>(M, n, reinterpret_cast<Cpx*>(work), LinvH, status);

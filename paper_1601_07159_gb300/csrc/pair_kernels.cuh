@@ -375,14 +375,16 @@ template <typename R, int N>
 bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   constexpr int IPB = plane_items<R, N>();
   constexpr size_t smem = (size_t)IPB * N * (N + 1) * sizeof(cplx<R>);
-  if (smem > 48 * 1024) {
-    // opt in to > 48 KB of dynamic shared memory (cheap host call, device-agnostic)
+  if (L.prepare_only) {
+    // opt in to > 48 KB of dynamic shared memory and the largest carveout; done
+    // once at plan creation on the plan's device, never during stream capture
     cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    return true;
   }
   PairParams<R, N> P;
   fill_params<R, N>(P, L, b);
