@@ -42,6 +42,29 @@ template <typename R, int N> struct PairParams {
   TwTable<R, N> tw;
 };
 
+// Programmatic dependent launch: every pass is launched with programmatic
+// stream serialisation, so its blocks can be scheduled while the previous pass
+// drains; griddep_wait() blocks until the previous grid has completed and its
+// writes are visible, and is called before the first access to data that grid
+// produced (or will still read). Without the launch attribute both are no-ops.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename Kern, typename Arg>
+inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Arg& arg) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 // Slot p of the batch -> tile index and (l, r) orbital indices.
 __device__ __forceinline__ int decode_pair(const Batch& b, int p, int& l, int& r) {
   int t = 0;
@@ -87,6 +110,7 @@ pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
   const int tx = threadIdx.x;
   const long long item = (long long)blockIdx.x * IPB + threadIdx.y;
   const bool active = item < (long long)P.npairs * N;
+  griddep_launch();
   int p = 0, z = 0, l = 0, r = 0;
   if (active) {
     p = (int)(item / N);
@@ -111,6 +135,7 @@ pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
 #pragma unroll
     for (int x = 0; x < N; ++x) b[x] = buf[tx * (N + 1) + x];
     dft<N, N, false, R>(b, P.tw);             // along x, row ky = tx
+    griddep_wait();                           // the previous batch's pass D still reads S
     cplx<R>* out = P.S + ((long long)p * N + z) * N * N + tx;
 #pragma unroll
     for (int kx = 0; kx < N; ++kx) out[kx * N] = b[kx];
@@ -126,6 +151,8 @@ pass_b_kernel(const __grid_constant__ PairParams<R, N> P) {
   const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = gid < (long long)P.npairs * N2;
   double e = 0.0;
+  griddep_launch();
+  griddep_wait();
   if (active) {
     const int p = (int)(gid / N2);
     const int f = (int)(gid % N2);
@@ -179,6 +206,8 @@ pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
   const long long item = (long long)blockIdx.x * IPB + threadIdx.y;
   const bool active = item < (long long)P.npairs * N;
   cplx<R>* plane = nullptr;
+  griddep_launch();
+  griddep_wait();
   if (active) {
     const int p = (int)(item / N);
     const int z = (int)(item % N);
@@ -276,7 +305,9 @@ __global__ void __launch_bounds__(256)
 pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
   constexpr long long NG = (long long)N * N * N;
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  griddep_launch();
   if (g >= NG) return;
+  griddep_wait();
   const TileDesc d = P.batch.t[blockIdx.y];
   const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
   if (d.kind == 1 && d.nl == kTileMax) {
@@ -392,25 +423,25 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   const long long items = (long long)b.npairs * N;
   const dim3 pblk(N, IPB);
   const unsigned pgrid = (unsigned)((items + IPB - 1) / IPB);
-  mark(0);
-  if (L.real_io) pass_a_kernel<R, N, true><<<pgrid, pblk, smem, st>>>(P);
-  else pass_a_kernel<R, N, false><<<pgrid, pblk, smem, st>>>(P);
-  mark(1);
   const unsigned bgrid = (unsigned)(((long long)b.npairs * N * N + 255) / 256);
-  if (L.mode == 0) pass_b_kernel<R, N, 0><<<bgrid, 256, 0, st>>>(P);
-  else if (L.mode == 1) pass_b_kernel<R, N, 1><<<bgrid, 256, 0, st>>>(P);
-  else pass_b_kernel<R, N, 2><<<bgrid, 256, 0, st>>>(P);
+  const dim3 dgrid((unsigned)(((long long)N * N * N + 255) / 256), (unsigned)b.ntiles);
+  mark(0);
+  if (L.real_io) launch_pdl(pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
+  else launch_pdl(pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+  mark(1);
+  if (L.mode == 0) launch_pdl(pass_b_kernel<R, N, 0>, dim3(bgrid), dim3(256), 0, st, P);
+  else if (L.mode == 1) launch_pdl(pass_b_kernel<R, N, 1>, dim3(bgrid), dim3(256), 0, st, P);
+  else launch_pdl(pass_b_kernel<R, N, 2>, dim3(bgrid), dim3(256), 0, st, P);
   mark(2);
   if (L.mode == 1) {
     mark(3);
     mark(4);
     return true;
   }
-  pass_c_kernel<R, N><<<pgrid, pblk, smem, st>>>(P);
+  launch_pdl(pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
   mark(3);
-  const dim3 dgrid((unsigned)(((long long)N * N * N + 255) / 256), (unsigned)b.ntiles);
-  if (L.real_io) pass_d_kernel<R, N, true><<<dgrid, 256, 0, st>>>(P);
-  else pass_d_kernel<R, N, false><<<dgrid, 256, 0, st>>>(P);
+  if (L.real_io) launch_pdl(pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
+  else launch_pdl(pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
   mark(4);
   return true;
 }
