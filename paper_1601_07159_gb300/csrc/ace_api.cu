@@ -252,29 +252,73 @@ cudaEvent_t* take_events(ace_plan* p, int count, int kind) {
   return e;
 }
 
-// Run the pair-solve section: eagerly (each batch in order on `st`, lane 0
-// scratch) when graphs are off or per-pass profiling needs events between
-// kernels, else by replaying (capturing on first use) a graph in which the
-// batches of one round are spread over the plan's lanes.
-ace_status run_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, char* S0, double* E0,
-                     cudaStream_t st, const uintptr_t key_in[6]) {
-  const bool eager = !p->graphs;
-  if (eager) {
+// Enqueue the pair-solve section on `cs`. Eager mode (graphs off): batches in
+// order on `cs` with lane-0 scratch and, when profiling, events around every
+// pass. Graph mode (called while capturing `cs`): the batches of one round
+// are spread over the plan's lanes (fork/join through events), consecutive
+// rounds are joined. Returns the kernel count, or -1 if the edge is not built.
+long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, char* S0, double* E0,
+                      cudaStream_t cs) {
+  long long kernels = 0;
+  if (!p->graphs) {
     for (const Batch& b : sc.batches) {
       PairLaunch L = base;
       L.S = S0;
       L.Epart = E0;
       L.ev = take_events(p, 5, 0);
-      p->launches += pair_batch_launches(L.mode);
-      if (!launch_one(p, L, b, st)) return fail(ACE_ERR_UNSUPPORTED, "edge not built");
+      kernels += pair_batch_launches(L.mode);
+      if (!launch_one(p, L, b, cs)) return -1;
     }
-    return cuda_check("pair section");
+    return kernels;
   }
-  uintptr_t key[8] = {key_in[0], key_in[1], key_in[2], key_in[3], key_in[4], key_in[5],
-                      (uintptr_t)base.mode, 0};
+  const int nl = p->lanes;
+  auto fork = [&]() {
+    cudaEventRecord(p->fork_ev, cs);
+    for (int i = 0; i < nl; ++i) cudaStreamWaitEvent(p->lane[i], p->fork_ev, 0);
+  };
+  auto join = [&]() {
+    for (int i = 0; i < nl; ++i) {
+      cudaEventRecord(p->join_ev[i], p->lane[i]);
+      cudaStreamWaitEvent(cs, p->join_ev[i], 0);
+    }
+  };
+  fork();
+  int cur = sc.round.empty() ? 0 : sc.round[0], k_in_round = 0;
+  bool ok = true;
+  for (size_t k = 0; k < sc.batches.size(); ++k) {
+    if (sc.round[k] != cur) {
+      join();
+      fork();
+      cur = sc.round[k];
+      k_in_round = 0;
+    }
+    const int ln = k_in_round++ % nl;
+    PairLaunch L = base;
+    L.S = S0 + (size_t)ln * lane_bytes(p);
+    L.Epart = E0 ? E0 + (size_t)ln * epart_per_lane(p) : nullptr;
+    L.ev = nullptr;
+    kernels += pair_batch_launches(L.mode);
+    ok = ok && launch_one(p, L, sc.batches[k], p->lane[ln]);
+  }
+  join();
+  return ok ? kernels : -1;
+}
+
+// Run `issue(stream)` (which enqueues work and returns its kernel count, or
+// -1): eagerly on `st` when graphs are off, else by replaying the graph cached
+// under `key`, capturing it on the plan's capture stream on first use. With
+// `timed`, profiling events bracket the graph launch.
+template <typename F>
+ace_status run_graph(ace_plan* p, const uintptr_t key[8], cudaStream_t st, bool timed, F&& issue) {
+  if (!p->graphs) {
+    const long long k = issue(st);
+    if (k < 0) return fail(ACE_ERR_UNSUPPORTED, "edge not built");
+    p->launches += k;
+    return cuda_check("eager section");
+  }
   GraphEntry* hit = nullptr;
   for (auto& g : p->graph_cache)
-    if (std::memcmp(g.key, key, sizeof(key)) == 0) hit = &g;
+    if (std::memcmp(g.key, key, sizeof(g.key)) == 0) hit = &g;
   if (!hit) {
     if ((int)p->graph_cache.size() >= kMaxGraphs) {
       size_t victim = 0;
@@ -284,40 +328,12 @@ ace_status run_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, ch
       p->graph_cache.erase(p->graph_cache.begin() + victim);
     }
     GraphEntry g;
-    std::memcpy(g.key, key, sizeof(key));
-    const int nl = p->lanes;
+    std::memcpy(g.key, key, sizeof(g.key));
     cudaStream_t cs = p->cap;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return cuda_check("graph capture begin");
-    auto fork = [&]() {
-      cudaEventRecord(p->fork_ev, cs);
-      for (int i = 0; i < nl; ++i) cudaStreamWaitEvent(p->lane[i], p->fork_ev, 0);
-    };
-    auto join = [&]() {
-      for (int i = 0; i < nl; ++i) {
-        cudaEventRecord(p->join_ev[i], p->lane[i]);
-        cudaStreamWaitEvent(cs, p->join_ev[i], 0);
-      }
-    };
-    fork();
-    int cur = sc.round.empty() ? 0 : sc.round[0], k_in_round = 0;
-    bool ok = true;
-    for (size_t k = 0; k < sc.batches.size(); ++k) {
-      if (sc.round[k] != cur) {
-        join();
-        fork();
-        cur = sc.round[k];
-        k_in_round = 0;
-      }
-      const int ln = k_in_round++ % nl;
-      PairLaunch L = base;
-      L.S = S0 + (size_t)ln * lane_bytes(p);
-      L.Epart = E0 ? E0 + (size_t)ln * epart_per_lane(p) : nullptr;
-      L.ev = nullptr;
-      g.kernels += pair_batch_launches(L.mode);
-      ok = ok && launch_one(p, L, sc.batches[k], p->lane[ln]);
-    }
-    join();
+    g.kernels = issue(cs);
+    const bool ok = g.kernels >= 0;
     cudaGraph_t graph = nullptr;
     const cudaError_t e1 = cudaStreamEndCapture(cs, &graph);
     if (!ok || e1 != cudaSuccess || !graph) {
@@ -333,12 +349,12 @@ ace_status run_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, ch
     hit = &p->graph_cache.back();
   }
   hit->last_use = ++p->use_clock;
-  cudaEvent_t* ev = take_events(p, 2, 1);
+  cudaEvent_t* ev = timed ? take_events(p, 2, 1) : nullptr;
   if (ev) cudaEventRecord(ev[0], st);
   if (cudaGraphLaunch(hit->exec, st) != cudaSuccess) return cuda_check("graph launch");
   if (ev) cudaEventRecord(ev[1], st);
   p->launches += hit->kernels;
-  return cuda_check("pair section");
+  return cuda_check("graph section");
 }
 
 PairLaunch base_launch(const ace_plan* p) {
@@ -465,7 +481,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     if (e == cudaSuccess) e = cudaMemcpy(p->Kt, kf.data(), kf.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->Mc, (size_t)2 * N * N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->work, (size_t)4 * N * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&p->work, cholesky_work_doubles(N) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->LinvH, (size_t)2 * N * N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->status, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->status, 0, 2 * sizeof(int));
@@ -528,7 +544,6 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
   if (Y == Phi || Y == Psi) return fail(ACE_ERR_ARG, "Y must not alias Phi or Psi");
   cudaStream_t st = (cudaStream_t)stream;
   const WsLayout W = layout(p, ACE_OP_EXCHANGE_APPLY, nb, (char*)ws);
-  cudaMemsetAsync(Y, 0, (size_t)nb * p->ng * p->vsize, st);
   PairLaunch L = base_launch(p);
   L.X = Phi;
   L.Y = Psi;
@@ -543,10 +558,12 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
     p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
     sc = &p->rect.back().second;
   }
-  const uintptr_t key[6] = {(uintptr_t)Phi, (uintptr_t)Psi, (uintptr_t)Y, (uintptr_t)ws, (uintptr_t)nb, 1};
-  s = run_pairs(p, L, *sc, W.S, nullptr, st, key);
-  if (s != ACE_OK) return s;
-  return cuda_check("ace_exchange_apply");
+  const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)Psi, (uintptr_t)Y, (uintptr_t)ws, (uintptr_t)nb, 1, 0, 0};
+  const size_t ybytes = (size_t)nb * p->ng * p->vsize;
+  return run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
+    cudaMemsetAsync(Y, 0, ybytes, cs);
+    return issue_pairs(p, L, *sc, W.S, nullptr, cs);
+  });
 }
 
 ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, double* M_out,
@@ -562,8 +579,7 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   const int N = p->d.n_occ;
   const WsLayout Wl = layout(p, ACE_OP_BUILD, 0, (char*)ws);
   void* W = W_out ? W_out : (void*)Wl.Wtmp;
-  cudaMemsetAsync(W, 0, (size_t)N * p->ng * p->vsize, st);
-  cudaMemsetAsync(p->status, 0, 2 * sizeof(int), st);
+  const size_t wbytes = (size_t)N * p->ng * p->vsize;
   // W = V_X[Phi] Phi over the unique pairs (Eq. W)
   PairLaunch L = base_launch(p);
   L.X = Phi;
@@ -571,18 +587,27 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   L.OutX = W;
   L.OutY = W;
   L.mode = 0;
-  const uintptr_t key[6] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, 0, 0, 2};
-  s = run_pairs(p, L, p->build, Wl.S, nullptr, st, key);
+  const uintptr_t kp[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, 0, 0, 2, 0, 0};
+  s = run_graph(p, kp, st, true, [&](cudaStream_t cs) -> long long {
+    cudaMemsetAsync(W, 0, wbytes, cs);
+    return issue_pairs(p, L, p->build, Wl.S, nullptr, cs);
+  });
   if (s != ACE_OK) return s;
-  // M = dV Phi^* W, Hermitian part (Eq. ACEconstruct2); E_x = 1/2 Re tr M
-  const int splits = gram_splits(p->ng);
-  launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, st);
-  launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, Ex_out, st);
-  if (M_out) launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, p->real, M_out, nullptr, st);
+  // M = dV Phi^* W, Hermitian part (Eq. ACEconstruct2); E_x = 1/2 Re tr M;
   // -M = L L^* and L^{-*} in FP64; Xi = W L^{-*} (Eq. Wtilde)
-  launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, st);
-  launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, st);
-  p->launches += 2 + (Ex_out ? 1 : 0) + (M_out ? 1 : 0) + 1 + 1;
+  const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, 4, 0, 0, 0};
+  s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
+    const int splits = gram_splits(p->ng);
+    cudaMemsetAsync(p->status, 0, 2 * sizeof(int), cs);
+    launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
+    launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
+    const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
+    launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, cs);
+    return 2 + kc + 1;
+  });
+  if (s != ACE_OK) return s;
+  // caller-owned small outputs, outside the graph (their pointers vary per call)
+  p->launches += launch_m_outputs(p->Mc, N, p->real, M_out, Ex_out, st);
   return cuda_check("ace_build");
 }
 
@@ -619,8 +644,6 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   const int N = p->d.n_occ;
   const WsLayout Wl = layout(p, ACE_OP_ENERGY_GRAD, 0, (char*)ws);
   const int ecount = p->lanes * epart_per_lane(p);
-  cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), st);
-  if (grad_out) cudaMemsetAsync(grad_out, 0, (size_t)N * p->ng * p->vsize, st);
   PairLaunch L = base_launch(p);
   L.X = Phi;
   L.Y = Phi;
@@ -628,16 +651,20 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   L.OutY = grad_out;
   L.mode = grad_out ? 2 : 1;
   L.scale = 2.0 * p->dv;                   // grad = 2 dV W, then * grad_scale
-  const uintptr_t key[6] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)ws, 0, 0, 3};
-  s = run_pairs(p, L, p->build, Wl.S, Wl.Epart, st, key);
+  const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)Ex_out, (uintptr_t)ws, 0, 3, 0, 0};
+  s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
+    cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), cs);
+    if (grad_out) cudaMemsetAsync(grad_out, 0, (size_t)N * p->ng * p->vsize, cs);
+    const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, cs);
+    // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2  (Kt = alpha K / N_g)
+    launch_energy_reduce(Wl.Epart, ecount, -0.5 * p->vol / (double)p->ng, Ex_out, cs);
+    return k < 0 ? k : k + 1;
+  });
   if (s != ACE_OK) return s;
-  if (grad_out && grad_scale != 1.0) {
+  if (grad_out && grad_scale != 1.0) {   // outside the graph: the scale varies per call
     launch_scale(p->f64, p->real, grad_out, (long long)N * p->ng, grad_scale, st);
     p->launches += 1;
   }
-  // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2  (Kt = alpha K / N_g)
-  launch_energy_reduce(Wl.Epart, ecount, -0.5 * p->vol / (double)p->ng, Ex_out, st);
-  p->launches += 1;
   return cuda_check("ace_exchange_energy_grad");
 }
 

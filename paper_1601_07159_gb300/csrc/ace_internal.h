@@ -63,8 +63,11 @@ void launch_gram_reduce(const double* part, int splits, int na, int nb, double s
                         bool real_out, double* out, double* out_trace_half, cudaStream_t st);
 void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,
                   long long ld, long long ng, double alpha, void* Out, cudaStream_t st);
-void launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
-                         cudaStream_t st);
+int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st);
+// Blocked FP64 Cholesky of -M and L^{-*}; returns the number of kernels launched.
+int launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
+                        cudaStream_t st);
+size_t cholesky_work_doubles(int n);
 void prepare_cholesky(int n);
 void launch_scale(bool f64, bool real, void* X, long long count, double s, cudaStream_t st);
 void launch_energy_reduce(const double* part, int count, double factor, double* out, cudaStream_t st);

@@ -149,6 +149,33 @@ __global__ void trace_half_kernel(const double* __restrict__ m, int n, int real,
   *out = 0.5 * s;
 }
 
+__global__ void m_copy_kernel(const double* __restrict__ mc, int n, int real, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  if (real) {
+    out[e] = mc[2 * e];
+  } else {
+    out[2 * e] = mc[2 * e];
+    out[2 * e + 1] = mc[2 * e + 1];
+  }
+}
+
+// M_out <- M (real part only for real orbitals), Ex_out <- 1/2 Re tr M; both
+// nullable. Returns the number of kernels launched.
+int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st) {
+  int k = 0;
+  if (M_out) {
+    const long long nn = (long long)n * n;
+    m_copy_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(Mc, n, real ? 1 : 0, M_out);
+    ++k;
+  }
+  if (Ex_out) {
+    trace_half_kernel<<<1, 32, 0, st>>>(Mc, n, 0, Ex_out);
+    ++k;
+  }
+  return k;
+}
+
 void launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
                         bool real_out, double* out, double* out_trace_half, cudaStream_t st) {
   const long long total = (long long)na * nb;
