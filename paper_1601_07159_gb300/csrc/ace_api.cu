@@ -39,7 +39,23 @@ constexpr int kMaxGraphs = 8;
 struct Schedule {
   std::vector<Batch> batches;
   std::vector<int> round;
+  std::vector<int> toff;        // offset of each batch's tiles in dtiles
+  TileDesc* dtiles = nullptr;   // device copy of all tile descriptors
 };
+
+// Copy the tile descriptors of every batch to one device array (kernels read
+// them from there, which keeps the launch parameter block small).
+cudaError_t upload(Schedule& sc) {
+  std::vector<TileDesc> all;
+  for (const Batch& b : sc.batches) {
+    sc.toff.push_back((int)all.size());
+    for (int t = 0; t < b.ntiles; ++t) all.push_back(b.t[t]);
+  }
+  if (all.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&sc.dtiles, all.size() * sizeof(TileDesc));
+  if (e == cudaSuccess) e = cudaMemcpy(sc.dtiles, all.data(), all.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+  return e;
+}
 
 struct GraphEntry {
   uintptr_t key[8] = {};
@@ -266,6 +282,7 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
       L.S = S0;
       L.Epart = E0;
       L.ev = take_events(p, 5, 0);
+      L.dtiles = sc.dtiles + sc.toff[&b - sc.batches.data()];
       kernels += pair_batch_launches(L.mode);
       if (!launch_one(p, L, b, cs)) return -1;
     }
@@ -297,6 +314,7 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
     L.S = S0 + (size_t)ln * lane_bytes(p);
     L.Epart = E0 ? E0 + (size_t)ln * epart_per_lane(p) : nullptr;
     L.ev = nullptr;
+    L.dtiles = sc.dtiles + sc.toff[k];
     kernels += pair_batch_launches(L.mode);
     ok = ok && launch_one(p, L, sc.batches[k], p->lane[ln]);
   }
@@ -503,6 +521,12 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     return fail(ACE_ERR_CUDA, m);
   }
   p->build = make_sym_schedule(N, p->tile, p->max_pairs);
+  e = upload(p->build);
+  if (e != cudaSuccess) {
+    std::string m = std::string("schedule upload: ") + cudaGetErrorString(e);
+    ace_plan_destroy(p);
+    return fail(ACE_ERR_CUDA, m);
+  }
   *out = p;
   return ACE_OK;
 }
@@ -518,6 +542,8 @@ ace_status ace_plan_destroy(ace_plan* p) {
   }
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  cudaFree(p->build.dtiles);
+  for (auto& r : p->rect) cudaFree(r.second.dtiles);
   cudaFree(p->Kt);
   cudaFree(p->Mc);
   cudaFree(p->work);
@@ -554,8 +580,13 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
   const Schedule* sc = nullptr;
   for (auto& c : p->rect)
     if (c.first == nb) sc = &c.second;
-  if (!sc) {
+  if (!sc) {   // first call with this n_b: build and upload its schedule (small allocation)
     p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
+    if (upload(p->rect.back().second) != cudaSuccess) {
+      cudaFree(p->rect.back().second.dtiles);
+      p->rect.pop_back();
+      return cuda_check("schedule upload");
+    }
     sc = &p->rect.back().second;
   }
   const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)Psi, (uintptr_t)Y, (uintptr_t)ws, (uintptr_t)nb, 1, 0, 0};

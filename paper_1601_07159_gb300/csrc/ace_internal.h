@@ -46,6 +46,7 @@ struct PairLaunch {
   int mode;              // 0: W / Y accumulate; 1: energy only; 2: energy + accumulate
   cudaEvent_t* ev;       // nullable: 5 events recorded around passes A, B, C, D
   bool prepare_only;     // set kernel attributes for edge n, launch nothing
+  const TileDesc* dtiles;  // device copy of the batch's tile descriptors
 };
 // Kernel launches issued by one pair batch for a mode (4, or 2 for energy only).
 inline int pair_batch_launches(int mode) { return mode == 1 ? 2 : 4; }

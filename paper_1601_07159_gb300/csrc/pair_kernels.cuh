@@ -38,7 +38,8 @@ template <typename R, int N> struct PairParams {
   long long ld;
   R scale;
   int npairs;
-  Batch batch;
+  const TileDesc* tiles;   // device table of the batch's tiles
+  int ntiles;
   TwTable<R, N> tw;
 };
 
@@ -66,10 +67,10 @@ inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream
 }
 
 // Slot p of the batch -> tile index and (l, r) orbital indices.
-__device__ __forceinline__ int decode_pair(const Batch& b, int p, int& l, int& r) {
+__device__ __forceinline__ int decode_pair(const TileDesc* __restrict__ tiles, int ntiles, int p, int& l, int& r) {
   int t = 0;
-  while (t + 1 < b.ntiles && b.t[t + 1].slot0 <= p) ++t;
-  const TileDesc& d = b.t[t];
+  while (t + 1 < ntiles && tiles[t + 1].slot0 <= p) ++t;
+  const TileDesc d = tiles[t];
   int q = p - d.slot0;
   if (d.kind == 1) {
     int li = 0, len = d.nl;
@@ -115,7 +116,7 @@ pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
   if (active) {
     p = (int)(item / N);
     z = (int)(item % N);
-    decode_pair(P.batch, p, l, r);
+    decode_pair(P.tiles, P.ntiles, p, l, r);
     cplx<R> a[N];
     const long long xo = (long long)l * P.ld + (long long)z * N * N + tx;
     const long long yo = (long long)r * P.ld + (long long)z * N * N + tx;
@@ -163,7 +164,7 @@ pass_b_kernel(const __grid_constant__ PairParams<R, N> P) {
     dft<N, N, false, R>(a, P.tw);
     if constexpr (MODE != 0) {
       int l, r;
-      decode_pair(P.batch, p, l, r);
+      decode_pair(P.tiles, P.ntiles, p, l, r);
       R acc = R(0);
 #pragma unroll
       for (int kz = 0; kz < N; ++kz) {
@@ -308,7 +309,7 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
   griddep_launch();
   if (g >= NG) return;
   griddep_wait();
-  const TileDesc d = P.batch.t[blockIdx.y];
+  const TileDesc d = P.tiles[blockIdx.y];
   const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
   if (d.kind == 1 && d.nl == kTileMax) {
     pass_d_full_diag<R, N, REAL>(P, d, V, g);
@@ -395,7 +396,8 @@ void fill_params(PairParams<R, N>& P, const PairLaunch& L, const Batch& b) {
   P.ld = L.ld;
   P.scale = (R)L.scale;
   P.npairs = b.npairs;
-  P.batch = b;
+  P.tiles = L.dtiles;
+  P.ntiles = b.ntiles;
   for (int k = 0; k < N; ++k) {
     P.tw.w[k].x = (R)L.tw[2 * k];
     P.tw.w[k].y = (R)L.tw[2 * k + 1];
