@@ -50,7 +50,8 @@ def parse():
     p.add_argument("--max-pairs", type=int, default=0, help="pair solves per batch (0 = plan default)")
     p.add_argument("--tile", type=int, default=0, help="orbitals per tile side (0 = plan default)")
     p.add_argument("--lanes", type=int, default=0, help="concurrent batch streams (0 = plan default)")
-    p.add_argument("--eager", action="store_true", help="launch batches eagerly (per-pass timings)")
+    p.add_argument("--eager", action="store_true",
+                   help="four kernels per batch, launched eagerly (per-pass timings)")
     return p.parse_args()
 
 
@@ -221,7 +222,7 @@ def run_ours(args):
     phi, psi = make_inputs(s, rank)
     plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega,
                     max_pairs=args.max_pairs, tile=args.tile, lanes=args.lanes,
-                    graphs=not args.eager)
+                    graphs=not args.eager, passes=args.eager)
     td = torch.complex64
     phi_h = torch.from_numpy(phi).to(td).pin_memory()
     psi_h = torch.from_numpy(psi).to(td).pin_memory()

@@ -84,6 +84,10 @@ typedef struct {
 /* Launch each pair batch eagerly instead of replaying a captured CUDA graph
  * (graphs are keyed by the call's pointers; see ace_build). */
 #define ACE_FLAG_NO_GRAPH 1
+/* Run the pair solves as four kernels per batch (passes A-D, chained by
+ * programmatic dependent launch) instead of one persistent launch per call;
+ * with ACE_FLAG_NO_GRAPH this gives per-pass times in ace_profile_end. */
+#define ACE_FLAG_PASSES 2
 
 typedef struct ace_plan ace_plan;
 

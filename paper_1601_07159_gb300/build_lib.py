@@ -1,7 +1,8 @@
-"""Build libace.so in-tree: one nvcc process per translation unit, in parallel,
-then a shared link. sm_103a only (GB300).
+"""Build libace.so in-tree: one nvcc process per translation unit (the pair
+kernels once per precision and grid edge), run in parallel, then a shared
+link. sm_103a only (GB300).
 
-    python -m paper_1601_07159_gb300.build_lib
+    python -m paper_1601_07159_gb300.build_lib [--force]
 """
 from __future__ import annotations
 
@@ -9,15 +10,30 @@ import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libace.so")
-SOURCES = ["pair_f32.cu", "pair_f64.cu", "dense.cu", "chol.cu", "ace_api.cu", "apply_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
+# keep in step with ACE_EDGES_F32 / ACE_EDGES_F64 in csrc/pair_dispatch.cu
+EDGES_F32 = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64)
+EDGES_F64 = (8, 12, 16, 20, 24, 32, 36, 40, 48)
+PLAIN = ["pair_dispatch.cu", "dense.cu", "chol.cu", "ace_api.cu", "apply_static.cu"]
+
+
+def units():
+    """(source, object name, extra flags) for every translation unit."""
+    out = [(s, s.replace(".cu", ".o"), []) for s in PLAIN]
+    for prec, typ, edges in (("f32", "float", EDGES_F32), ("f64", "double", EDGES_F64)):
+        for n in edges:
+            tag = f"{prec}_{n}"
+            out.append(("pair_edge.cu", f"pair_edge_{tag}.o",
+                        [f"-DACE_EDGE_R={typ}", f"-DACE_EDGE_N={n}", f"-DACE_EDGE_TAG={tag}"]))
+    return out
 
 
 def nvcc() -> str:
@@ -32,7 +48,7 @@ def _stamp(path: str) -> float:
 
 
 def _deps_mtime() -> float:
-    t = 0.0
+    t = _stamp(os.path.abspath(__file__))
     for d in (CSRC, os.path.join(os.path.dirname(PKG), "include")):
         for f in os.listdir(d):
             t = max(t, os.path.getmtime(os.path.join(d, f)))
@@ -46,27 +62,30 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and _stamp(LIB) > deps:
         return LIB
     cc = nvcc()
-    procs = []
+    todo = []
     objs = []
-    for src in SOURCES:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        objs.append(obj)
-        if not force and _stamp(obj) > deps:
-            continue
-        cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+    for src, obj, extra in units():
+        path = os.path.join(BUILD, obj)
+        objs.append(path)
+        if force or _stamp(path) <= deps:
+            todo.append([cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", path])
+
+    def run(cmd):
         if verbose:
             print(" ".join(cmd), flush=True)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+        return cmd, r.returncode, r.stdout.decode(errors="replace")
+
+    workers = max(1, min(len(todo), os.cpu_count() or 1))
     failed = []
-    for src, pr in procs:
-        out, _ = pr.communicate()
-        if pr.returncode != 0:
-            failed.append((src, out.decode(errors="replace")))
-        elif verbose and out:
-            print(out.decode(errors="replace"))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        for cmd, rc, out in ex.map(run, todo):
+            if rc != 0:
+                failed.append((cmd[-3], out))
+            elif verbose and out.strip():
+                print(out)
     if failed:
-        msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
-        raise RuntimeError("nvcc failed:\n" + msg)
+        raise RuntimeError("nvcc failed:\n" + "\n".join(f"--- {s}\n{o}" for s, o in failed))
     tmp = LIB + ".tmp"
     cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     if verbose:
@@ -77,4 +96,4 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -41,20 +41,16 @@ struct Schedule {
   std::vector<int> round;
   std::vector<int> toff;        // offset of each batch's tiles in dtiles
   TileDesc* dtiles = nullptr;   // device copy of all tile descriptors
+  EngineBatch* deng[2] = {nullptr, nullptr};   // engine task tables: [0] Poisson, [1] energy only
+  long long ntasks[2] = {0, 0};
 };
 
-// Copy the tile descriptors of every batch to one device array (kernels read
-// them from there, which keeps the launch parameter block small).
-cudaError_t upload(Schedule& sc) {
-  std::vector<TileDesc> all;
-  for (const Batch& b : sc.batches) {
-    sc.toff.push_back((int)all.size());
-    for (int t = 0; t < b.ntiles; ++t) all.push_back(b.t[t]);
-  }
-  if (all.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&sc.dtiles, all.size() * sizeof(TileDesc));
-  if (e == cudaSuccess) e = cudaMemcpy(sc.dtiles, all.data(), all.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
-  return e;
+void free_schedule(Schedule& sc) {
+  cudaFree(sc.dtiles);
+  cudaFree(sc.deng[0]);
+  cudaFree(sc.deng[1]);
+  sc.dtiles = nullptr;
+  sc.deng[0] = sc.deng[1] = nullptr;
 }
 
 struct GraphEntry {
@@ -82,6 +78,8 @@ struct ace_plan {
   size_t vsize = 0;              // bytes per stored vector element
   int max_pairs = 0, tile = 0, lanes = 1;
   bool graphs = true;
+  bool engine = true;            // persistent pair engine (else four kernels per batch)
+  EngineInfo einfo;
   std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
   Schedule build;                // symmetric schedule of the W build
   std::deque<std::pair<int, Schedule>> rect;   // one-sided schedules by n_b
@@ -104,6 +102,43 @@ struct ace_plan {
 };
 
 namespace {
+
+// Copy the tile descriptors of every batch to one device array (kernels read
+// them from there, which keeps the launch parameter block small), and build
+// the persistent engine's task tables (Poisson and energy-only).
+cudaError_t upload(const ace_plan* p, Schedule& sc) {
+  std::vector<TileDesc> all;
+  std::vector<EngineBatch> eng[2];
+  long long t0[2] = {0, 0};
+  for (const Batch& b : sc.batches) {
+    sc.toff.push_back((int)all.size());
+    int nt[4] = {0, 0, 0, 0};
+    if (p->f64) engine_tasks_f64(p->n, b, nt);
+    else engine_tasks_f32(p->n, b, nt);
+    for (int m = 0; m < 2; ++m) {
+      EngineBatch e{};
+      e.toff = (int)all.size();
+      e.ntiles = b.ntiles;
+      e.npairs = b.npairs;
+      e.task0 = t0[m];
+      for (int q = 0; q < 4; ++q) e.n[q] = (m == 1 && q >= 2) ? 0 : nt[q];
+      t0[m] += e.n[0] + e.n[1] + e.n[2] + e.n[3];
+      eng[m].push_back(e);
+    }
+    for (int t = 0; t < b.ntiles; ++t) all.push_back(b.t[t]);
+  }
+  sc.ntasks[0] = t0[0];
+  sc.ntasks[1] = t0[1];
+  if (all.empty()) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&sc.dtiles, all.size() * sizeof(TileDesc));
+  if (e == cudaSuccess) e = cudaMemcpy(sc.dtiles, all.data(), all.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
+  for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
+    e = cudaMalloc(&sc.deng[m], eng[m].size() * sizeof(EngineBatch));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(sc.deng[m], eng[m].data(), eng[m].size() * sizeof(EngineBatch), cudaMemcpyHostToDevice);
+  }
+  return e;
+}
 
 // Tournament ("circle") schedule over orbital blocks: every round pairs each
 // block with exactly one other, so the tiles of a round write disjoint outputs.
@@ -208,8 +243,18 @@ struct WsLayout {
   double* part = nullptr;
   double* Cm = nullptr;
   char* Wtmp = nullptr;
+  char* ctr = nullptr;          // engine queue head + per-batch counters
   size_t total = 0;
 };
+
+// Upper bound on the batches of the one-sided schedule for n_b vectors.
+long long rect_batch_bound(const ace_plan* p, int nb) {
+  const int N = p->d.n_occ, b = p->tile;
+  int lc = p->max_pairs / b;
+  if (lc < 1) lc = 1;
+  if (lc > N) lc = N;
+  return (long long)((N + lc - 1) / lc) * ((nb + b - 1) / b);
+}
 
 int epart_per_lane(const ace_plan* p) { return energy_blocks(p->n, p->max_pairs, p->f64) + 1; }
 size_t slot_bytes(const ace_plan* p) { return (size_t)p->ng * p->csize; }
@@ -221,8 +266,11 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   auto take = [&](size_t bytes) { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
   const int N = p->d.n_occ;
   const int splits = gram_splits(p->ng);
-  if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD)
+  if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD) {
     L.S = take((size_t)p->lanes * lane_bytes(p));
+    const long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
+    L.ctr = take(16 + 16 * (size_t)nbat);
+  }
   if (op == ACE_OP_ENERGY_GRAD)
     L.Epart = (double*)take((size_t)p->lanes * epart_per_lane(p) * sizeof(double));
   if (op == ACE_OP_BUILD) {
@@ -274,8 +322,31 @@ cudaEvent_t* take_events(ace_plan* p, int count, int kind) {
 // are spread over the plan's lanes (fork/join through events), consecutive
 // rounds are joined. Returns the kernel count, or -1 if the edge is not built.
 long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, char* S0, double* E0,
-                      cudaStream_t cs) {
+                      char* ctr, cudaStream_t cs) {
   long long kernels = 0;
+  cudaMemsetAsync(p->status, 0, 2 * sizeof(int), cs);
+  if (sc.batches.empty()) return 0;
+  if (p->engine) {   // one persistent launch for the whole schedule
+    const int m = base.mode == 1 ? 1 : 0;
+    cudaMemsetAsync(ctr, 0, 16 + 16 * sc.batches.size(), cs);
+    PairLaunch L = base;
+    L.S = S0;
+    L.Epart = E0;
+    L.ev = nullptr;
+    L.dtiles = sc.dtiles;
+    EngineLaunch E{};
+    E.dtiles = sc.dtiles;
+    E.batches = sc.deng[m];
+    E.nbatches = (int)sc.batches.size();
+    E.ntasks = sc.ntasks[m];
+    E.head = reinterpret_cast<unsigned long long*>(ctr);
+    E.done = reinterpret_cast<unsigned*>(ctr + 16);
+    E.status = p->status;
+    E.blocks = p->einfo.blocks;
+    E.smem = p->einfo.smem;
+    const bool ok = p->f64 ? launch_engine_f64(L, E, cs) : launch_engine_f32(L, E, cs);
+    return ok ? 1 : -1;
+  }
   if (!p->graphs) {
     for (const Batch& b : sc.batches) {
       PairLaunch L = base;
@@ -448,6 +519,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->tile = d->tile ? d->tile : kTileMax;
   p->lanes = d->lanes ? d->lanes : 2;
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
+  p->engine = !(d->flags & ACE_FLAG_PASSES);
   const size_t slot = (size_t)p->ng * p->csize;
   const int tt = p->tile * p->tile;
   if (d->max_pairs) {
@@ -513,6 +585,11 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     Batch none{};
     launch_one(p, prep, none, nullptr);
     prepare_cholesky(N);
+    if (p->engine) {
+      if (p->f64) engine_prepare_f64(p->n, p->einfo);
+      else engine_prepare_f32(p->n, p->einfo);
+      if (p->einfo.blocks <= 0) p->engine = false;   // does not fit: four kernels per batch
+    }
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
@@ -521,7 +598,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     return fail(ACE_ERR_CUDA, m);
   }
   p->build = make_sym_schedule(N, p->tile, p->max_pairs);
-  e = upload(p->build);
+  e = upload(p, p->build);
   if (e != cudaSuccess) {
     std::string m = std::string("schedule upload: ") + cudaGetErrorString(e);
     ace_plan_destroy(p);
@@ -542,8 +619,8 @@ ace_status ace_plan_destroy(ace_plan* p) {
   }
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
-  cudaFree(p->build.dtiles);
-  for (auto& r : p->rect) cudaFree(r.second.dtiles);
+  free_schedule(p->build);
+  for (auto& r : p->rect) free_schedule(r.second);
   cudaFree(p->Kt);
   cudaFree(p->Mc);
   cudaFree(p->work);
@@ -582,8 +659,8 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
     if (c.first == nb) sc = &c.second;
   if (!sc) {   // first call with this n_b: build and upload its schedule (small allocation)
     p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
-    if (upload(p->rect.back().second) != cudaSuccess) {
-      cudaFree(p->rect.back().second.dtiles);
+    if (upload(p, p->rect.back().second) != cudaSuccess) {
+      free_schedule(p->rect.back().second);
       p->rect.pop_back();
       return cuda_check("schedule upload");
     }
@@ -593,7 +670,7 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
   const size_t ybytes = (size_t)nb * p->ng * p->vsize;
   return run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
     cudaMemsetAsync(Y, 0, ybytes, cs);
-    return issue_pairs(p, L, *sc, W.S, nullptr, cs);
+    return issue_pairs(p, L, *sc, W.S, nullptr, W.ctr, cs);
   });
 }
 
@@ -621,7 +698,7 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   const uintptr_t kp[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, 0, 0, 2, 0, 0};
   s = run_graph(p, kp, st, true, [&](cudaStream_t cs) -> long long {
     cudaMemsetAsync(W, 0, wbytes, cs);
-    return issue_pairs(p, L, p->build, Wl.S, nullptr, cs);
+    return issue_pairs(p, L, p->build, Wl.S, nullptr, Wl.ctr, cs);
   });
   if (s != ACE_OK) return s;
   // M = dV Phi^* W, Hermitian part (Eq. ACEconstruct2); E_x = 1/2 Re tr M;
@@ -629,7 +706,6 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, 4, 0, 0, 0};
   s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
     const int splits = gram_splits(p->ng);
-    cudaMemsetAsync(p->status, 0, 2 * sizeof(int), cs);
     launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
     launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
     const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
@@ -686,7 +762,7 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
     cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), cs);
     if (grad_out) cudaMemsetAsync(grad_out, 0, (size_t)N * p->ng * p->vsize, cs);
-    const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, cs);
+    const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, Wl.ctr, cs);
     // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2  (Kt = alpha K / N_g)
     launch_energy_reduce(Wl.Epart, ecount, -0.5 * p->vol / (double)p->ng, Ex_out, cs);
     return k < 0 ? k : k + 1;
@@ -762,6 +838,7 @@ ace_status ace_status_sync(ace_plan* p, void* stream, int* info) {
   if (info) *info = h[1];
   if (h[0] == ACE_ERR_NOT_POSDEF) return fail(ACE_ERR_NOT_POSDEF, "-M is not positive definite at pivot " + std::to_string(h[1]));
   if (h[0] == ACE_ERR_NONFINITE) return fail(ACE_ERR_NONFINITE, "non-finite Cholesky pivot " + std::to_string(h[1]));
+  if (h[0] == ACE_ERR_TIMEOUT) return fail(ACE_ERR_TIMEOUT, "pair engine wait ran out at task " + std::to_string(h[1]));
   return ACE_OK;
 }
 

@@ -48,6 +48,35 @@ struct PairLaunch {
   bool prepare_only;     // set kernel attributes for edge n, launch nothing
   const TileDesc* dtiles;  // device copy of the batch's tile descriptors
 };
+// Persistent engine: per-batch task table and launch description.
+struct EngineBatch {
+  int toff, ntiles, npairs, pad;
+  long long task0;   // first global task of the batch
+  int n[4];          // tasks of passes A, B, C, D (C, D zero in energy-only tables)
+};
+struct EngineInfo {
+  size_t smem = 0;
+  int threads = 0;
+  int blocks = 0;    // co-resident blocks on the device (0: the engine does not fit)
+};
+struct EngineLaunch {
+  const TileDesc* dtiles;
+  const EngineBatch* batches;
+  int nbatches;
+  long long ntasks;
+  unsigned long long* head;
+  unsigned* done;
+  int* status;
+  long long blocks;
+  size_t smem;
+};
+bool engine_prepare_f32(int n, EngineInfo& info);
+bool engine_prepare_f64(int n, EngineInfo& info);
+bool engine_tasks_f32(int n, const Batch& b, int nt[4]);
+bool engine_tasks_f64(int n, const Batch& b, int nt[4]);
+bool launch_engine_f32(const PairLaunch& L, const EngineLaunch& E, cudaStream_t st);
+bool launch_engine_f64(const PairLaunch& L, const EngineLaunch& E, cudaStream_t st);
+
 // Kernel launches issued by one pair batch for a mode (4, or 2 for energy only).
 inline int pair_batch_launches(int mode) { return mode == 1 ? 2 : 4; }
 bool launch_pair_batch_f32(const PairLaunch& L, const Batch& b, cudaStream_t st);

@@ -1,8 +1,8 @@
 // Pair FFT-Poisson solves: the hot loop of Eq. applyVX / Eq. W.
 //
 // For a batch of pairs (l, r) the 3-D solve v = F^-1[ K F[conj(x_l) y_r] ] is
-// split into three passes over the batch's spectrum scratch S, each pass a
-// set of register-resident line FFTs (fft_reg.cuh), plus one accumulate pass:
+// split into three passes over the batch's spectrum scratch S, each a set of
+// register-resident line FFTs (fft_reg.cuh), plus one accumulate pass:
 //
 //   pass A  (per z-plane)   rho = conj(x_l) y_r; FFT along y (thread = column x,
 //                           coalesced loads), transpose through shared memory,
@@ -19,8 +19,20 @@
 //                           orbitals and accumulators, one read-modify-write of
 //                           each output per tile, fixed summation order.
 //
-// Tiles within a batch touch disjoint outputs (the schedule guarantees it), so
-// pass D needs no atomics and the result is bitwise reproducible.
+// Two ways to run a schedule of batches:
+//  * four kernels per batch (pass_*_kernel), chained with programmatic
+//    dependent launch; used for per-pass timing;
+//  * one persistent launch (pair_engine_kernel): co-resident blocks take
+//    tasks (one pass-A/C block of planes, one pass-B block of pencils, one
+//    pass-D block of points) in schedule order from an atomic queue and wait,
+//    with a bounded spin, on per-batch completion counters: pass p of batch k
+//    needs all of pass p-1 of batch k, pass A of batch k needs the last pass of
+//    batch k-1 (the scratch is reused). Tasks are taken in increasing order by
+//    resident blocks, so every awaited task is already running: no deadlock.
+//
+// Tiles within a batch touch disjoint outputs (the schedule guarantees it) and
+// batches run in order, so the accumulation needs no atomics and the result is
+// bitwise reproducible and identical in both modes.
 #pragma once
 #include "ace_internal.h"
 #include "fft_reg.cuh"
@@ -43,16 +55,15 @@ template <typename R, int N> struct PairParams {
   TwTable<R, N> tw;
 };
 
-// Programmatic dependent launch: every pass is launched with programmatic
-// stream serialisation, so its blocks can be scheduled while the previous pass
-// drains; griddep_wait() blocks until the previous grid has completed and its
-// writes are visible, and is called before the first access to data that grid
-// produced (or will still read). Without the launch attribute both are no-ops.
+// Programmatic dependent launch (four-kernel mode): every pass is launched with
+// programmatic stream serialisation, so its blocks can be scheduled while the
+// previous pass drains; griddep_wait() blocks until the previous grid has
+// completed and its writes are visible. Without the attribute both are no-ops.
 __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <typename Kern, typename Arg>
-inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Arg& arg) {
+template <typename Kern, typename... Args>
+inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Args&... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -63,7 +74,19 @@ inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, kern, arg);
+  cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Loads and stores of data that other blocks of the same launch produce or
+// consume (the pair scratch and the outputs, in the persistent engine) go
+// through L2 (.cg): L1 is not coherent across SMs.
+template <bool COH, typename T> __device__ __forceinline__ T ldx(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+template <bool COH, typename T> __device__ __forceinline__ void stx(T* p, T v) {
+  if constexpr (COH) __stcg(p, v);
+  else *p = v;
 }
 
 // Slot p of the batch -> tile index and (l, r) orbital indices.
@@ -94,29 +117,35 @@ __device__ __forceinline__ cplx<R> load_vec(const void* base, long long idx) {
 }
 
 template <typename R, int N> __host__ __device__ constexpr int plane_items() {
-  // items (pair, z-plane) per CTA: ~256 threads, <= 96 KB of padded planes
+  // items (pair, z-plane) per CTA of the plane kernels: ~256 threads, <= 96 KB
   constexpr int by_threads = (256 / N) > 0 ? (256 / N) : 1;
   constexpr int by_smem = (96 * 1024) / (N * (N + 1) * (int)sizeof(cplx<R>));
   constexpr int v = by_threads < by_smem ? by_threads : by_smem;
   return v > 0 ? v : 1;
 }
+constexpr int kEngineThreads = 256;
+template <typename R, int N> __host__ __device__ constexpr int engine_items() {
+  // items per plane task of the engine: all 256 threads, <= 200 KB of planes
+  constexpr int by_threads = (kEngineThreads / N) > 0 ? (kEngineThreads / N) : 1;
+  constexpr int by_smem = (200 * 1024) / (N * (N + 1) * (int)sizeof(cplx<R>));
+  constexpr int v = by_threads < by_smem ? by_threads : by_smem;
+  return v > 0 ? v : 1;
+}
 
-// ---------------------------------------------------------------- pass A
-template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
-pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
-  constexpr int IPB = plane_items<R, N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw) + threadIdx.y * N * (N + 1);
-  const int tx = threadIdx.x;
-  const long long item = (long long)blockIdx.x * IPB + threadIdx.y;
-  const bool active = item < (long long)P.npairs * N;
-  griddep_launch();
+// ---------------------------------------------------------------- pass bodies
+// Pass A on virtual block `vb` (IPB plane items, thread tid = ty * N + tx).
+template <typename R, int N, bool REAL, bool COH, int IPB, bool PDL>
+__device__ __forceinline__ void body_a(const PairParams<R, N>& P, const TileDesc* tiles, int ntiles, int npairs,
+                                       cplx<R>* smem, long long vb, int tid) {
+  const int tx = tid % N, ty = tid / N;
+  cplx<R>* buf = smem + ty * N * (N + 1);
+  const long long item = vb * IPB + ty;
+  const bool active = ty < IPB && item < (long long)npairs * N;
   int p = 0, z = 0, l = 0, r = 0;
   if (active) {
     p = (int)(item / N);
     z = (int)(item % N);
-    decode_pair(P.tiles, P.ntiles, p, l, r);
+    decode_pair(tiles, ntiles, p, l, r);
     cplx<R> a[N];
     const long long xo = (long long)l * P.ld + (long long)z * N * N + tx;
     const long long yo = (long long)r * P.ld + (long long)z * N * N + tx;
@@ -136,87 +165,78 @@ pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
 #pragma unroll
     for (int x = 0; x < N; ++x) b[x] = buf[tx * (N + 1) + x];
     dft<N, N, false, R>(b, P.tw);             // along x, row ky = tx
-    griddep_wait();                           // the previous batch's pass D still reads S
+    if constexpr (PDL) griddep_wait();        // the previous batch's pass D still reads S
     cplx<R>* out = P.S + ((long long)p * N + z) * N * N + tx;
 #pragma unroll
-    for (int kx = 0; kx < N; ++kx) out[kx * N] = b[kx];
+    for (int kx = 0; kx < N; ++kx) stx<COH>(out + kx * N, b[kx]);
   }
 }
 
-// ---------------------------------------------------------------- pass B
-// MODE 0: Poisson (forward z, K, inverse z); 1: energy only; 2: both.
-template <typename R, int N, int MODE>
-__global__ void __launch_bounds__(256)
-pass_b_kernel(const __grid_constant__ PairParams<R, N> P) {
+// Pass B on virtual block `vb` of `nthr` pencils. mode 0: Poisson (forward z,
+// K, inverse z); 1: energy only; 2: both. The energy partial of the block
+// (mode != 0) is added to *eslot by thread 0 (one owner per slot).
+template <typename R, int N, bool COH>
+__device__ __forceinline__ void body_b(const PairParams<R, N>& P, const TileDesc* tiles, int ntiles, int npairs,
+                                       int mode, long long vb, int tid, int nthr, double* red, double* eslot) {
   constexpr int N2 = N * N;
-  const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = gid < (long long)P.npairs * N2;
+  const long long gid = vb * nthr + tid;
+  const bool active = gid < (long long)npairs * N2;
   double e = 0.0;
-  griddep_launch();
-  griddep_wait();
   if (active) {
     const int p = (int)(gid / N2);
     const int f = (int)(gid % N2);
     cplx<R>* s = P.S + (long long)p * N * N2 + f;
     cplx<R> a[N];
 #pragma unroll
-    for (int zz = 0; zz < N; ++zz) a[zz] = s[(long long)zz * N2];
+    for (int zz = 0; zz < N; ++zz) a[zz] = ldx<COH>(s + (long long)zz * N2);
     dft<N, N, false, R>(a, P.tw);
-    if constexpr (MODE != 0) {
-      int l, r;
-      decode_pair(P.tiles, P.ntiles, p, l, r);
-      R acc = R(0);
+    R acc = R(0);
 #pragma unroll
-      for (int kz = 0; kz < N; ++kz) {
-        const R k = P.Kt[kz * N2 + f];
-        acc += k * (a[kz].x * a[kz].x + a[kz].y * a[kz].y);
-      }
+    for (int kz = 0; kz < N; ++kz) {
+      const R k = P.Kt[kz * N2 + f];
+      if (mode != 0) acc += k * (a[kz].x * a[kz].x + a[kz].y * a[kz].y);
+      a[kz] = cscale(a[kz], k);
+    }
+    if (mode != 0) {
+      int l, r;
+      decode_pair(tiles, ntiles, p, l, r);
       e = (l == r ? 1.0 : 2.0) * (double)acc;
     }
-    if constexpr (MODE != 1) {
-#pragma unroll
-      for (int kz = 0; kz < N; ++kz) a[kz] = cscale(a[kz], P.Kt[kz * N2 + f]);
+    if (mode != 1) {
       dft<N, N, true, R>(a, P.tw);
 #pragma unroll
-      for (int zz = 0; zz < N; ++zz) s[(long long)zz * N2] = a[zz];
+      for (int zz = 0; zz < N; ++zz) stx<COH>(s + (long long)zz * N2, a[zz]);
     }
   }
-  if constexpr (MODE != 0) {
-    // deterministic block sum -> Epart[blockIdx.x] += sum (one owner per slot)
-    __shared__ double red[32];
+  if (mode != 0) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+    if ((tid & 31) == 0) red[tid >> 5] = e;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      P.Epart[blockIdx.x] += s;
+      for (int w = 0; w < nthr / 32; ++w) s += red[w];
+      *eslot += s;
     }
   }
 }
 
-// ---------------------------------------------------------------- pass C
-template <typename R, int N>
-__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
-pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
-  constexpr int IPB = plane_items<R, N>();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<R>* buf = reinterpret_cast<cplx<R>*>(smem_raw) + threadIdx.y * N * (N + 1);
-  const int tx = threadIdx.x;
-  const long long item = (long long)blockIdx.x * IPB + threadIdx.y;
-  const bool active = item < (long long)P.npairs * N;
+// Pass C on virtual block `vb` (IPB plane items).
+template <typename R, int N, bool COH, int IPB>
+__device__ __forceinline__ void body_c(const PairParams<R, N>& P, int npairs, cplx<R>* smem, long long vb, int tid) {
+  const int tx = tid % N, ty = tid / N;
+  cplx<R>* buf = smem + ty * N * (N + 1);
+  const long long item = vb * IPB + ty;
+  const bool active = ty < IPB && item < (long long)npairs * N;
   cplx<R>* plane = nullptr;
-  griddep_launch();
-  griddep_wait();
   if (active) {
     const int p = (int)(item / N);
     const int z = (int)(item % N);
     plane = P.S + ((long long)p * N + z) * N * N;
     cplx<R> b[N];
 #pragma unroll
-    for (int kx = 0; kx < N; ++kx) b[kx] = plane[kx * N + tx];   // row ky = tx
-    dft<N, N, true, R>(b, P.tw);                                   // inverse along x
+    for (int kx = 0; kx < N; ++kx) b[kx] = ldx<COH>(plane + kx * N + tx);   // row ky = tx
+    dft<N, N, true, R>(b, P.tw);                                            // inverse along x
 #pragma unroll
     for (int x = 0; x < N; ++x) buf[tx * (N + 1) + x] = b[x];
   }
@@ -227,29 +247,28 @@ pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
     for (int ky = 0; ky < N; ++ky) a[ky] = buf[ky * (N + 1) + tx];  // column x = tx
     dft<N, N, true, R>(a, P.tw);                                    // inverse along y
 #pragma unroll
-    for (int y = 0; y < N; ++y) plane[y * N + tx] = a[y];
+    for (int y = 0; y < N; ++y) stx<COH>(plane + y * N + tx, a[y]);
   }
 }
 
-// ---------------------------------------------------------------- pass D
-template <typename R, bool REAL>
+template <typename R, bool REAL, bool COH>
 __device__ __forceinline__ void rmw_out(void* base, long long idx, cplx<R> acc, R scale) {
   if constexpr (REAL) {
     R* o = static_cast<R*>(base) + idx;
-    *o = *o - scale * acc.x;
+    stx<COH>(o, ldx<COH>(o) - scale * acc.x);
   } else {
     cplx<R>* o = static_cast<cplx<R>*>(base) + idx;
-    const cplx<R> c = *o;
-    *o = cmk<cplx<R>>(c.x - scale * acc.x, c.y - scale * acc.y);
+    const cplx<R> c = ldx<COH>(o);
+    stx<COH>(o, cmk<cplx<R>>(c.x - scale * acc.x, c.y - scale * acc.y));
   }
 }
 
 // Full tiles (kTileMax orbitals per side): no runtime guards, so all loads of
 // the tile's pair potentials can be issued back to back. v is read once, so it
 // is loaded with the streaming (evict-first) hint.
-template <typename R, int N, bool REAL>
-__device__ __forceinline__ void pass_d_full_diag(const PairParams<R, N>& P, const TileDesc& d,
-                                                 const cplx<R>* __restrict__ V, long long g) {
+template <typename R, int N, bool REAL, bool COH>
+__device__ __forceinline__ void d_full_diag(const PairParams<R, N>& P, const TileDesc& d,
+                                            const cplx<R>* __restrict__ V, long long g) {
   constexpr long long NG = (long long)N * N * N;
   constexpr int B = kTileMax;
   cplx<R> x[B], acc[B];
@@ -269,12 +288,12 @@ __device__ __forceinline__ void pass_d_full_diag(const PairParams<R, N>& P, cons
     }
   }
 #pragma unroll
-  for (int o = 0; o < B; ++o) rmw_out<R, REAL>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
+  for (int o = 0; o < B; ++o) rmw_out<R, REAL, COH>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
 }
 
-template <typename R, int N, bool REAL>
-__device__ __forceinline__ void pass_d_full_off(const PairParams<R, N>& P, const TileDesc& d,
-                                                const cplx<R>* __restrict__ V, long long g) {
+template <typename R, int N, bool REAL, bool COH>
+__device__ __forceinline__ void d_full_off(const PairParams<R, N>& P, const TileDesc& d,
+                                           const cplx<R>* __restrict__ V, long long g) {
   constexpr long long NG = (long long)N * N * N;
   constexpr int B = kTileMax;
   cplx<R> xl[B], yr[B], al[B], ar[B];
@@ -296,25 +315,23 @@ __device__ __forceinline__ void pass_d_full_off(const PairParams<R, N>& P, const
   }
 #pragma unroll
   for (int o = 0; o < B; ++o) {
-    rmw_out<R, REAL>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
-    rmw_out<R, REAL>(P.OutX, (long long)(d.l0 + o) * P.ld + g, al[o], P.scale);
+    rmw_out<R, REAL, COH>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+    rmw_out<R, REAL, COH>(P.OutX, (long long)(d.l0 + o) * P.ld + g, al[o], P.scale);
   }
 }
 
-template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(256)
-pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
+// Pass D for point block `vbx` (nthr points) of tile `d`.
+template <typename R, int N, bool REAL, bool COH>
+__device__ __forceinline__ void body_d(const PairParams<R, N>& P, const TileDesc& d, long long vbx, int tid,
+                                       int nthr) {
   constexpr long long NG = (long long)N * N * N;
-  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  griddep_launch();
+  const long long g = vbx * nthr + tid;
   if (g >= NG) return;
-  griddep_wait();
-  const TileDesc d = P.tiles[blockIdx.y];
   const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
   if (d.kind == 1 && d.nl == kTileMax) {
-    pass_d_full_diag<R, N, REAL>(P, d, V, g);
+    d_full_diag<R, N, REAL, COH>(P, d, V, g);
   } else if (d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
-    pass_d_full_off<R, N, REAL>(P, d, V, g);
+    d_full_off<R, N, REAL, COH>(P, d, V, g);
   } else if (d.kind == 1) {
     cplx<R> x[kTileMax], acc[kTileMax];
 #pragma unroll
@@ -328,7 +345,7 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
 #pragma unroll
       for (int ri = li; ri < kTileMax; ++ri) {
         if (li < d.nl && ri < d.nl) {
-          const cplx<R> v = V[(long long)q * NG];
+          const cplx<R> v = ldx<COH>(V + (long long)q * NG);
           ++q;
           acc[ri] = cadd(acc[ri], cmul(x[li], v));
           if (ri != li) acc[li] = cadd(acc[li], cmulc(v, x[ri]));   // x_r conj(v)
@@ -337,7 +354,7 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
     }
 #pragma unroll
     for (int o = 0; o < kTileMax; ++o)
-      if (o < d.nl) rmw_out<R, REAL>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
+      if (o < d.nl) rmw_out<R, REAL, COH>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
   } else if (d.kind == 0) {
     cplx<R> xl[kTileMax], yr[kTileMax], al[kTileMax], ar[kTileMax];
 #pragma unroll
@@ -352,7 +369,7 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
 #pragma unroll
       for (int ri = 0; ri < kTileMax; ++ri) {
         if (li < d.nl && ri < d.nr) {
-          const cplx<R> v = V[(long long)(li * d.nr + ri) * NG];
+          const cplx<R> v = ldx<COH>(V + (long long)(li * d.nr + ri) * NG);
           ar[ri] = cadd(ar[ri], cmul(xl[li], v));
           al[li] = cadd(al[li], cmulc(v, yr[ri]));
         }
@@ -360,8 +377,8 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
     }
 #pragma unroll
     for (int o = 0; o < kTileMax; ++o) {
-      if (o < d.nr) rmw_out<R, REAL>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
-      if (o < d.nl) rmw_out<R, REAL>(P.OutX, (long long)(d.l0 + o) * P.ld + g, al[o], P.scale);
+      if (o < d.nr) rmw_out<R, REAL, COH>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+      if (o < d.nl) rmw_out<R, REAL, COH>(P.OutX, (long long)(d.l0 + o) * P.ld + g, al[o], P.scale);
     }
   } else {
     cplx<R> ar[kTileMax];
@@ -372,14 +389,157 @@ pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
 #pragma unroll
       for (int ri = 0; ri < kTileMax; ++ri) {
         if (ri < d.nr) {
-          const cplx<R> v = V[(long long)(li * d.nr + ri) * NG];
+          const cplx<R> v = ldx<COH>(V + (long long)(li * d.nr + ri) * NG);
           ar[ri] = cadd(ar[ri], cmul(xv, v));
         }
       }
     }
 #pragma unroll
     for (int o = 0; o < kTileMax; ++o)
-      if (o < d.nr) rmw_out<R, REAL>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+      if (o < d.nr) rmw_out<R, REAL, COH>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+  }
+}
+
+// ---------------------------------------------------------------- four-kernel mode
+template <typename R, int N, bool REAL>
+__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
+pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  griddep_launch();
+  body_a<R, N, REAL, false, plane_items<R, N>(), true>(P, P.tiles, P.ntiles, P.npairs,
+                                                       reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(256, 2)
+pass_b_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
+  __shared__ double red[32];
+  griddep_launch();
+  griddep_wait();
+  body_b<R, N, false>(P, P.tiles, P.ntiles, P.npairs, mode, blockIdx.x, threadIdx.x, blockDim.x, red,
+                      mode != 0 ? P.Epart + blockIdx.x : nullptr);
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
+pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  griddep_launch();
+  griddep_wait();
+  body_c<R, N, false, plane_items<R, N>()>(P, P.npairs, reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
+}
+
+template <typename R, int N, bool REAL>
+__global__ void __launch_bounds__(256)
+pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
+  griddep_launch();
+  griddep_wait();
+  const TileDesc d = P.tiles[blockIdx.y];
+  body_d<R, N, REAL, false>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
+// ---------------------------------------------------------------- persistent engine
+template <typename R, int N> struct EngineParams {
+  PairParams<R, N> P;           // npairs / ntiles unused: per batch from the table
+  const EngineBatch* batches;   // per batch: tiles, pairs, first task, tasks per pass
+  int nbatches;
+  int npasses;                  // 4 (Poisson) or 2 (energy only: A, B)
+  long long ntasks;
+  unsigned long long* head;     // task queue head
+  unsigned* done;               // done[4 k + p]: finished tasks of pass p of batch k
+  int* status;                  // plan status word: timeout -> ACE_ERR_TIMEOUT
+  int mode;                     // 0: Poisson + accumulate; 1: energy only; 2: both
+};
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// A wait gives up after ~2^22 sleeps of >= 256 ns (about a second or more);
+// the block then records ACE_ERR_TIMEOUT and leaves, and so do the blocks that
+// wait on it, so the launch always ends.
+constexpr unsigned kSpinLimit = 1u << 22;
+
+template <typename R, int N, bool REAL>
+__global__ void __launch_bounds__(kEngineThreads, 2)
+pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
+  constexpr int IPB = engine_items<R, N>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  __shared__ long long s_loc;
+  __shared__ int s_batch, s_pass, s_stop;
+  const int tid = threadIdx.x;
+  cplx<R>* smem = reinterpret_cast<cplx<R>*>(smem_raw);
+  for (;;) {
+    if (tid == 0) {
+      const long long t = (long long)atomicAdd(E.head, 1ull);
+      int stop = 0, k = 0, pass = 0;
+      long long loc = 0;
+      if (t >= E.ntasks) {
+        stop = 1;
+      } else {
+        int lo = 0, hi = E.nbatches - 1;   // last batch whose first task <= t
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (E.batches[mid].task0 <= t) lo = mid;
+          else hi = mid - 1;
+        }
+        k = lo;
+        const EngineBatch b = E.batches[k];
+        loc = t - b.task0;
+        while (loc >= b.n[pass]) { loc -= b.n[pass]; ++pass; }
+        const unsigned* want = nullptr;
+        unsigned target = 0;
+        if (pass > 0) {
+          want = E.done + 4 * k + pass - 1;
+          target = (unsigned)b.n[pass - 1];
+        } else if (k > 0) {
+          want = E.done + 4 * (k - 1) + E.npasses - 1;
+          target = (unsigned)E.batches[k - 1].n[E.npasses - 1];
+        }
+        if (want) {
+          unsigned it = 0;
+          while (ld_acquire(want) < target) {
+            __nanosleep(256);
+            if (++it > kSpinLimit) {
+              E.status[0] = -6;   // ACE_ERR_TIMEOUT
+              E.status[1] = (int)(t & 0x7fffffff);
+              stop = 1;
+              break;
+            }
+          }
+        }
+      }
+      s_stop = stop;
+      s_batch = k;
+      s_pass = pass;
+      s_loc = loc;
+    }
+    __syncthreads();
+    if (s_stop) return;
+    const int k = s_batch, pass = s_pass;
+    const long long loc = s_loc;
+    const EngineBatch& b = E.batches[k];
+    const TileDesc* tiles = E.P.tiles + b.toff;
+    if (pass == 0) {
+      body_a<R, N, REAL, true, IPB, false>(E.P, tiles, b.ntiles, b.npairs, smem, loc, tid);
+    } else if (pass == 1) {
+      body_b<R, N, true>(E.P, tiles, b.ntiles, b.npairs, E.mode, loc, tid, kEngineThreads, red,
+                         E.mode != 0 ? E.P.Epart + loc : nullptr);
+    } else if (pass == 2) {
+      body_c<R, N, true, IPB>(E.P, b.npairs, smem, loc, tid);
+    } else {
+      const long long nvb = ((long long)N * N * N + kEngineThreads - 1) / kEngineThreads;
+      const TileDesc d = tiles[loc / nvb];
+      body_d<R, N, REAL, true>(E.P, d, loc % nvb, tid, kEngineThreads);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      atomicAdd(E.done + 4 * k + pass, 1u);
+    }
   }
 }
 
@@ -404,6 +564,75 @@ void fill_params(PairParams<R, N>& P, const PairLaunch& L, const Batch& b) {
   }
 }
 
+// Tasks per pass of a batch in the engine (A, B, C, D).
+template <typename R, int N>
+void engine_tasks(const Batch& b, int n[4]) {
+  constexpr int IPB = engine_items<R, N>();
+  n[0] = (int)(((long long)b.npairs * N + IPB - 1) / IPB);
+  n[1] = (int)(((long long)b.npairs * N * N + kEngineThreads - 1) / kEngineThreads);
+  n[2] = n[0];
+  n[3] = (int)((((long long)N * N * N + kEngineThreads - 1) / kEngineThreads) * b.ntiles);
+}
+
+template <typename R, int N>
+void engine_prepare(EngineInfo& info) {
+  constexpr int IPB = engine_items<R, N>();
+  constexpr size_t smem = (size_t)IPB * N * (N + 1) * sizeof(cplx<R>);
+  info.smem = smem;
+  info.threads = kEngineThreads;
+  int dev = 0, sms = 0, per = 0, occ = 1 << 30;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto one = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kEngineThreads, smem);
+    if (per < occ) occ = per;
+  };
+  one(pair_engine_kernel<R, N, false>);
+  if constexpr (sizeof(R) == 8) one(pair_engine_kernel<R, N, true>);
+  info.blocks = occ > 0 ? occ * sms : 0;
+}
+
+template <typename R, int N>
+bool launch_engine(const PairLaunch& L, const EngineLaunch& EL, cudaStream_t st) {
+  EngineParams<R, N> E;
+  Batch none{};
+  fill_params<R, N>(E.P, L, none);
+  E.P.tiles = EL.dtiles;
+  E.batches = EL.batches;
+  E.nbatches = EL.nbatches;
+  E.npasses = L.mode == 1 ? 2 : 4;
+  E.ntasks = EL.ntasks;
+  E.head = EL.head;
+  E.done = EL.done;
+  E.status = EL.status;
+  E.mode = L.mode;
+  cudaLaunchConfig_t cfg{};
+  long long blocks = EL.blocks;
+  if (blocks > EL.ntasks) blocks = EL.ntasks;
+  if (blocks < 1) return true;
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kEngineThreads);
+  cfg.dynamicSmemBytes = EL.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident (required by the waits)
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  if constexpr (sizeof(R) == 8) {
+    if (L.real_io) {
+      cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, true>, E);
+      return true;
+    }
+  }
+  if (L.real_io) return false;
+  cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, false>, E);
+  return true;
+}
+
 template <typename R, int N>
 bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   constexpr int IPB = plane_items<R, N>();
@@ -411,10 +640,12 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   if (L.prepare_only) {
     // opt in to > 48 KB of dynamic shared memory and the largest carveout; done
     // once at plan creation on the plan's device, never during stream capture
-    cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if constexpr (sizeof(R) == 8) {
+      cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     return true;
@@ -423,17 +654,22 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   fill_params<R, N>(P, L, b);
   auto mark = [&](int k) { if (L.ev) cudaEventRecord(L.ev[k], st); };
   const long long items = (long long)b.npairs * N;
-  const dim3 pblk(N, IPB);
+  const dim3 pblk(N * IPB);
   const unsigned pgrid = (unsigned)((items + IPB - 1) / IPB);
   const unsigned bgrid = (unsigned)(((long long)b.npairs * N * N + 255) / 256);
   const dim3 dgrid((unsigned)(((long long)N * N * N + 255) / 256), (unsigned)b.ntiles);
+  if constexpr (sizeof(R) != 8) {
+    if (L.real_io) return false;
+  }
   mark(0);
-  if (L.real_io) launch_pdl(pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
-  else launch_pdl(pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+  if constexpr (sizeof(R) == 8) {
+    if (L.real_io) launch_pdl(pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
+    else launch_pdl(pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+  } else {
+    launch_pdl(pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+  }
   mark(1);
-  if (L.mode == 0) launch_pdl(pass_b_kernel<R, N, 0>, dim3(bgrid), dim3(256), 0, st, P);
-  else if (L.mode == 1) launch_pdl(pass_b_kernel<R, N, 1>, dim3(bgrid), dim3(256), 0, st, P);
-  else launch_pdl(pass_b_kernel<R, N, 2>, dim3(bgrid), dim3(256), 0, st, P);
+  launch_pdl(pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
   mark(2);
   if (L.mode == 1) {
     mark(3);
@@ -442,8 +678,12 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   }
   launch_pdl(pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
   mark(3);
-  if (L.real_io) launch_pdl(pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
-  else launch_pdl(pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+  if constexpr (sizeof(R) == 8) {
+    if (L.real_io) launch_pdl(pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
+    else launch_pdl(pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+  } else {
+    launch_pdl(pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+  }
   mark(4);
   return true;
 }

@@ -115,16 +115,18 @@ def test_bitwise_reproducible(ace):
     assert rel(_host(c["W"]), ref) < 1e-6 and rel(_host(a["W"]), ref) < 1e-6
 
 
-@pytest.mark.parametrize("lanes", [1, 3])
-def test_graph_replay_matches_eager(ace, lanes):
-    """The captured-graph path (batches of a round spread over lanes) gives the
-    same bits as eager launches: every output element is written by one tile
-    per round and rounds run in order. New pointers capture a new graph."""
+@pytest.mark.parametrize("engine,lanes,graphs", [(True, 1, True), (True, 1, False), (False, 3, True)])
+def test_schedules_match_bitwise(ace, engine, lanes, graphs):
+    """Every way of running the pair schedule gives the same bits as eager
+    four-kernel launches: the persistent engine (in or out of a graph) and the
+    four-kernel path replayed from a graph with a round's batches spread over
+    lanes. Each output element is written by one tile per round and rounds run
+    in order. New pointers capture a new graph."""
     s, phi, psi, kern = _inputs(24, 10.0, 21, 10, "c64", "erfc", 0.3, seed=8)
     eager = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
-                     graphs=False)
+                     graphs=False, passes=True)
     graph = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
-                     lanes=lanes)
+                     lanes=lanes, graphs=graphs, passes=not engine)
     phi_d = _dev(phi, "c64", ace)
     psi_d = _dev(psi, "c64", ace)
     a = eager.build(phi_d)
@@ -141,6 +143,7 @@ def test_graph_replay_matches_eager(ace, lanes):
     ea, ga = eager.energy_grad(phi_d, grad=True, grad_scale=-1.5)
     eb, gb = graph.energy_grad(phi_d, grad=True, grad_scale=-1.5)
     assert torch.equal(ga, gb) and abs(ea.item() - eb.item()) <= 1e-13 * abs(ea.item())
+    assert graph.status() == (0, 0)
     assert rel(_host(gb), -1.5 * oracle.energy_grad(phi, kern, s.dv)) < 1e-5
 
 
