@@ -88,6 +88,9 @@ typedef struct {
  * programmatic dependent launch) instead of one persistent launch per call;
  * with ACE_FLAG_NO_GRAPH this gives per-pass times in ace_profile_end. */
 #define ACE_FLAG_PASSES 2
+/* With ACE_FLAG_PASSES: launch the passes without programmatic dependent launch
+ * (a tuning and diagnosis switch). */
+#define ACE_FLAG_NO_PDL 4
 
 typedef struct ace_plan ace_plan;
 

@@ -269,7 +269,7 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD) {
     L.S = take((size_t)p->lanes * lane_bytes(p));
     const long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
-    L.ctr = take(16 + 16 * (size_t)nbat);
+    L.ctr = take(engine_ctr_bytes(nbat));
   }
   if (op == ACE_OP_ENERGY_GRAD)
     L.Epart = (double*)take((size_t)p->lanes * epart_per_lane(p) * sizeof(double));
@@ -328,7 +328,7 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
   if (sc.batches.empty()) return 0;
   if (p->engine) {   // one persistent launch for the whole schedule
     const int m = base.mode == 1 ? 1 : 0;
-    cudaMemsetAsync(ctr, 0, 16 + 16 * sc.batches.size(), cs);
+    cudaMemsetAsync(ctr, 0, engine_ctr_bytes((long long)sc.batches.size()), cs);
     PairLaunch L = base;
     L.S = S0;
     L.Epart = E0;
@@ -340,7 +340,7 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
     E.nbatches = (int)sc.batches.size();
     E.ntasks = sc.ntasks[m];
     E.head = reinterpret_cast<unsigned long long*>(ctr);
-    E.done = reinterpret_cast<unsigned*>(ctr + 16);
+    E.done = reinterpret_cast<unsigned*>(ctr + 128);
     E.status = p->status;
     E.blocks = p->einfo.blocks;
     E.smem = p->einfo.smem;
@@ -455,6 +455,7 @@ PairLaunch base_launch(const ace_plan* p) {
   L.real_io = p->real;
   L.scale = 1.0;
   L.prepare_only = false;
+  L.no_pdl = (p->d.flags & ACE_FLAG_NO_PDL) != 0;
   return L;
 }
 

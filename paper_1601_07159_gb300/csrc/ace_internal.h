@@ -47,7 +47,14 @@ struct PairLaunch {
   cudaEvent_t* ev;       // nullable: 5 events recorded around passes A, B, C, D
   bool prepare_only;     // set kernel attributes for edge n, launch nothing
   const TileDesc* dtiles;  // device copy of the batch's tile descriptors
+  bool no_pdl;           // launch the passes without programmatic dependent launch
 };
+// Persistent engine counters: a queue head and one completion counter per
+// (batch, pass), each on its own 128-byte line so that polling blocks do not
+// contend with the atomics of the producers.
+constexpr int kCtrStride = 32;   // unsigned ints between counters
+inline size_t engine_ctr_bytes(long long nbatches) { return 128 + (size_t)512 * (size_t)nbatches; }
+
 // Persistent engine: per-batch task table and launch description.
 struct EngineBatch {
   int toff, ntiles, npairs, pad;

@@ -63,7 +63,8 @@ __device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wa
 __device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename Kern, typename... Args>
-inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Args&... args) {
+inline void launch_pdl(bool pdl, Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       const Args&... args) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -73,7 +74,7 @@ inline void launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream
   at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   at[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = at;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 1 : 0;
   cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
@@ -493,16 +494,16 @@ pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
         const unsigned* want = nullptr;
         unsigned target = 0;
         if (pass > 0) {
-          want = E.done + 4 * k + pass - 1;
+          want = E.done + kCtrStride * (4 * k + pass - 1);
           target = (unsigned)b.n[pass - 1];
         } else if (k > 0) {
-          want = E.done + 4 * (k - 1) + E.npasses - 1;
+          want = E.done + kCtrStride * (4 * (k - 1) + E.npasses - 1);
           target = (unsigned)E.batches[k - 1].n[E.npasses - 1];
         }
         if (want) {
           unsigned it = 0;
           while (ld_acquire(want) < target) {
-            __nanosleep(256);
+            __nanosleep(it < 64 ? 32 : 256);
             if (++it > kSpinLimit) {
               E.status[0] = -6;   // ACE_ERR_TIMEOUT
               E.status[1] = (int)(t & 0x7fffffff);
@@ -538,7 +539,7 @@ pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      atomicAdd(E.done + 4 * k + pass, 1u);
+      atomicAdd(E.done + kCtrStride * (4 * k + pass), 1u);
     }
   }
 }
@@ -663,26 +664,26 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   }
   mark(0);
   if constexpr (sizeof(R) == 8) {
-    if (L.real_io) launch_pdl(pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
-    else launch_pdl(pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+    if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
+    else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
   } else {
-    launch_pdl(pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+    launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
   }
   mark(1);
-  launch_pdl(pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
+  launch_pdl(!L.no_pdl, pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
   mark(2);
   if (L.mode == 1) {
     mark(3);
     mark(4);
     return true;
   }
-  launch_pdl(pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
+  launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
   mark(3);
   if constexpr (sizeof(R) == 8) {
-    if (L.real_io) launch_pdl(pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
-    else launch_pdl(pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+    if (L.real_io) launch_pdl(!L.no_pdl, pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
+    else launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
   } else {
-    launch_pdl(pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+    launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
   }
   mark(4);
   return true;
