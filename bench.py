@@ -52,7 +52,6 @@ def parse():
     p.add_argument("--lanes", type=int, default=0, help="concurrent batch streams (0 = plan default)")
     p.add_argument("--eager", action="store_true",
                    help="four kernels per batch, launched eagerly (per-pass timings)")
-    p.add_argument("--passes", action="store_true", help="four kernels per batch (graph-replayed)")
     p.add_argument("--engine", action="store_true", help="persistent pair engine")
     p.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
     return p.parse_args()
@@ -225,7 +224,7 @@ def run_ours(args):
     phi, psi = make_inputs(s, rank)
     plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega,
                     max_pairs=args.max_pairs, tile=args.tile, lanes=args.lanes,
-                    graphs=not args.eager, passes=(args.eager or args.passes) and not args.engine,
+                    graphs=not args.eager, engine=args.engine and not args.eager,
                     pdl=not args.no_pdl)
     td = torch.complex64
     phi_h = torch.from_numpy(phi).to(td).pin_memory()

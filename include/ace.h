@@ -84,12 +84,15 @@ typedef struct {
 /* Launch each pair batch eagerly instead of replaying a captured CUDA graph
  * (graphs are keyed by the call's pointers; see ace_build). */
 #define ACE_FLAG_NO_GRAPH 1
-/* Run the pair solves as four kernels per batch (passes A-D, chained by
- * programmatic dependent launch) instead of one persistent launch per call;
- * with ACE_FLAG_NO_GRAPH this gives per-pass times in ace_profile_end. */
-#define ACE_FLAG_PASSES 2
-/* With ACE_FLAG_PASSES: launch the passes without programmatic dependent launch
- * (a tuning and diagnosis switch). */
+/* Run the pair solves as one persistent cooperative launch per call (blocks
+ * take pass tasks from an ordered queue and wait, with a bounded spin, on
+ * per-batch completion counters) instead of the default four kernels per
+ * batch (passes A-D chained by programmatic dependent launch). A wait that runs
+ * out (about a second) leaves ACE_ERR_TIMEOUT in the status word. */
+#define ACE_FLAG_ENGINE 2
+/* Launch the four pass kernels without programmatic dependent launch (a
+ * tuning and diagnosis switch). With ACE_FLAG_NO_GRAPH and without
+ * ACE_FLAG_ENGINE, ace_profile_end reports per-pass times. */
 #define ACE_FLAG_NO_PDL 4
 
 typedef struct ace_plan ace_plan;

@@ -520,18 +520,17 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->tile = d->tile ? d->tile : kTileMax;
   p->lanes = d->lanes ? d->lanes : 2;
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
-  p->engine = !(d->flags & ACE_FLAG_PASSES);
+  p->engine = (d->flags & ACE_FLAG_ENGINE) != 0;
   const size_t slot = (size_t)p->ng * p->csize;
   const int tt = p->tile * p->tile;
   if (d->max_pairs) {
     p->max_pairs = d->max_pairs;
   } else {
-    // a batch of whole tiles whose scratch (~64 MB per lane) stays in L2
-    // between the passes
-    long long tiles = (64ll << 20) / ((long long)tt * (long long)slot);
-    if (tiles < 1) tiles = 1;
-    if (tiles > kMaxTiles) tiles = kMaxTiles;
-    p->max_pairs = (int)(tiles * tt);
+    // a batch whose scratch (~72 MB per lane, at least one whole tile) stays
+    // in L2 between the passes; at 48^3 FP32 that is one off-diagonal tile
+    // (64 pairs) or two diagonal ones (2 x 36)
+    const long long budget = (72ll << 20) / (long long)slot;
+    p->max_pairs = (int)(budget > (long long)kMaxTiles * tt ? (long long)kMaxTiles * tt : budget);
   }
   if (p->max_pairs < tt) p->max_pairs = tt;
 

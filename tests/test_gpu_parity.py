@@ -124,9 +124,9 @@ def test_schedules_match_bitwise(ace, engine, lanes, graphs):
     in order. New pointers capture a new graph."""
     s, phi, psi, kern = _inputs(24, 10.0, 21, 10, "c64", "erfc", 0.3, seed=8)
     eager = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
-                     graphs=False, passes=True)
+                     graphs=False)
     graph = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
-                     lanes=lanes, graphs=graphs, passes=not engine)
+                     lanes=lanes, graphs=graphs, engine=engine)
     phi_d = _dev(phi, "c64", ace)
     psi_d = _dev(psi, "c64", ace)
     a = eager.build(phi_d)
