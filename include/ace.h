@@ -94,6 +94,9 @@ typedef struct {
  * tuning and diagnosis switch). With ACE_FLAG_NO_GRAPH and without
  * ACE_FLAG_ENGINE, ace_profile_end reports per-pass times. */
 #define ACE_FLAG_NO_PDL 4
+/* ACE_DTYPE_C64: run M = Phi^* W, Xi = W L^{-*} and the apply on CUDA cores in
+ * FP32 instead of the tensor cores (tcgen05 TF32 with a 3-term split). */
+#define ACE_FLAG_SIMT_GEMM 8
 
 typedef struct ace_plan ace_plan;
 

@@ -79,6 +79,7 @@ struct ace_plan {
   int max_pairs = 0, tile = 0, lanes = 1;
   bool graphs = true;
   bool engine = true;            // persistent pair engine (else four kernels per batch)
+  bool tc = false;               // tensor-core GEMMs (complex FP32 storage)
   EngineInfo einfo;
   std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
   Schedule build;                // symmetric schedule of the W build
@@ -247,6 +248,11 @@ struct WsLayout {
   size_t total = 0;
 };
 
+// Split-K partial matrices of a gram product (the tensor-core or CUDA-core one).
+int gram_parts(const ace_plan* p, int na, int nb) {
+  return p->tc ? gram_tc_splits(p->ng, na, nb) : gram_splits(p->ng);
+}
+
 // Upper bound on the batches of the one-sided schedule for n_b vectors.
 long long rect_batch_bound(const ace_plan* p, int nb) {
   const int N = p->d.n_occ, b = p->tile;
@@ -265,7 +271,7 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   size_t off = 0;
   auto take = [&](size_t bytes) { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
   const int N = p->d.n_occ;
-  const int splits = gram_splits(p->ng);
+  const int splits = gram_parts(p, N, op == ACE_OP_APPLY ? nb : N);
   if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD) {
     L.S = take((size_t)p->lanes * lane_bytes(p));
     const long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
@@ -521,6 +527,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->lanes = d->lanes ? d->lanes : 2;
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
   p->engine = (d->flags & ACE_FLAG_ENGINE) != 0;
+  p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM);
   const size_t slot = (size_t)p->ng * p->csize;
   const int tt = p->tile * p->tile;
   if (d->max_pairs) {
@@ -585,6 +592,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     Batch none{};
     launch_one(p, prep, none, nullptr);
     prepare_cholesky(N);
+    if (p->tc) tc_gemm_prepare();
     if (p->engine) {
       if (p->f64) engine_prepare_f64(p->n, p->einfo);
       else engine_prepare_f32(p->n, p->einfo);
@@ -705,11 +713,13 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   // -M = L L^* and L^{-*} in FP64; Xi = W L^{-*} (Eq. Wtilde)
   const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, 4, 0, 0, 0};
   s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
-    const int splits = gram_splits(p->ng);
-    launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
+    const int splits = gram_parts(p, N, N);
+    if (p->tc) launch_gram_tc(Phi, N, W, N, p->ng, p->ng, Wl.part, splits, p->status, cs);
+    else launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
     launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
     const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
-    launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, cs);
+    if (p->tc) launch_outer_tc(W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, p->status, cs);
+    else launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, cs);
     return 2 + kc + 1;
   });
   if (s != ACE_OK) return s;
@@ -730,11 +740,13 @@ ace_status ace_apply(ace_plan* p, const void* Xi, const void* Psi, int nb, void*
   cudaStream_t st = (cudaStream_t)stream;
   const int N = p->d.n_occ;
   const WsLayout Wl = layout(p, ACE_OP_APPLY, nb, (char*)ws);
-  const int splits = gram_splits(p->ng);
+  const int splits = gram_parts(p, N, nb);
   // C = dV Xi^* Psi, Y = -Xi C (Eq. ACE)
-  launch_gram(p->f64, p->real, Xi, N, Psi, nb, p->ng, p->ng, Wl.part, splits, st);
+  if (p->tc) launch_gram_tc(Xi, N, Psi, nb, p->ng, p->ng, Wl.part, splits, p->status, st);
+  else launch_gram(p->f64, p->real, Xi, N, Psi, nb, p->ng, p->ng, Wl.part, splits, st);
   launch_gram_reduce(Wl.part, splits, N, nb, p->dv, false, false, Wl.Cm, nullptr, st);
-  launch_outer(p->f64, p->real, Xi, N, Wl.Cm, nb, p->ng, p->ng, -1.0, Y, st);
+  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ng, p->ng, -1.0, Y, p->status, st);
+  else launch_outer(p->f64, p->real, Xi, N, Wl.Cm, nb, p->ng, p->ng, -1.0, Y, st);
   p->launches += 3;
   return cuda_check("ace_apply");
 }

@@ -101,6 +101,13 @@ void launch_gram_reduce(const double* part, int splits, int na, int nb, double s
 void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,
                   long long ld, long long ng, double alpha, void* Out, cudaStream_t st);
 int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st);
+// Tensor-core (tcgen05 kind::tf32, 3-term split) GEMMs for complex FP32 (tc_gemm.cu).
+bool tc_gemm_prepare();
+int gram_tc_splits(long long ng, int na, int nb);
+void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, long long ng, double* part,
+                    int splits, int* status, cudaStream_t st);
+void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
+                     void* Out, int* status, cudaStream_t st);
 // Blocked FP64 Cholesky of -M and L^{-*}; returns the number of kernels launched.
 int launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
                         cudaStream_t st);

@@ -153,6 +153,29 @@ def test_schedules_match_bitwise(ace, engine, lanes, graphs):
     assert rel(_host(gb), -1.5 * oracle.energy_grad(phi, kern, s.dv)) < 1e-5
 
 
+@pytest.mark.parametrize("n,L,nocc,nb", [(20, 8.0, 13, 70), (24, 10.0, 130, 9)])
+def test_tensor_core_gemms_match_cuda_cores(ace, n, L, nocc, nb):
+    """tcgen05 TF32 3-term-split GEMMs (M, Xi, apply) against the FP32 CUDA-core
+    ones and the FP64 oracle, on shapes with partial row (N not a multiple of
+    128), column (n_b not a multiple of 64) and grid-point (8000 points) tiles."""
+    s, phi, psi, kern = _inputs(n, L, nocc, nb, "c64", "erfc", 0.3, seed=31)
+    ref = oracle.ace_build(phi, kern, s.dv)
+    phi_d, psi_d = _dev(phi, "c64", ace), _dev(psi, "c64", ace)
+    tc = ace.Plan(n, L, nocc, dtype="c64", kernel="erfc", omega=0.3)
+    simt = ace.Plan(n, L, nocc, dtype="c64", kernel="erfc", omega=0.3, tensor_cores=False)
+    a, b = tc.build(phi_d), simt.build(phi_d)
+    assert tc.status() == (0, 0) and simt.status() == (0, 0)
+    assert torch.equal(a["W"], b["W"])
+    m_ref = ref["M"]
+    assert rel(_host(a["M"]), m_ref) < 1e-5 and rel(_host(b["M"]), m_ref) < 1e-5
+    assert rel(_host(a["Xi"]), ref["Xi"]) < 1e-5
+    ya = tc.apply(a["Xi"], psi_d)
+    yb = simt.apply(b["Xi"], psi_d)
+    y_ref = oracle.ace_apply(ref["Xi"], psi, s.dv)
+    assert rel(_host(ya), y_ref) < 1e-5 and rel(_host(yb), y_ref) < 1e-5
+    assert tc.status() == (0, 0)
+
+
 def test_single_orbital_and_empty(ace):
     s, phi, psi, kern = _inputs(16, 8.0, 1, 2, "c128", "erfc", 0.4, seed=9)
     plan = ace.Plan(16, 8.0, 1, dtype="c128", kernel="erfc", omega=0.4)
