@@ -280,7 +280,8 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   if (op == ACE_OP_ENERGY_GRAD)
     L.Epart = (double*)take((size_t)p->lanes * epart_per_lane(p) * sizeof(double));
   if (op == ACE_OP_BUILD) {
-    L.part = (double*)take((size_t)splits * N * N * 2 * sizeof(double));
+    const size_t pd = (size_t)splits * N * N * 2;
+    L.part = (double*)take((pd > diag_dot_part_doubles(N) ? pd : diag_dot_part_doubles(N)) * sizeof(double));
     L.Wtmp = take((size_t)N * p->ng * p->vsize);
   }
   if (op == ACE_OP_APPLY) {
@@ -717,10 +718,11 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
     if (p->tc) launch_gram_tc(Phi, N, W, N, p->ng, p->ng, Wl.part, splits, p->status, cs);
     else launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
     launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
+    if (p->tc) launch_diag_exact(Phi, W, N, p->ng, p->ng, p->dv, Wl.part, p->Mc, cs);
     const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
     if (p->tc) launch_outer_tc(W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, p->status, cs);
     else launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, cs);
-    return 2 + kc + 1;
+    return 2 + (p->tc ? 2 : 0) + kc + 1;
   });
   if (s != ACE_OK) return s;
   // caller-owned small outputs, outside the graph (their pointers vary per call)

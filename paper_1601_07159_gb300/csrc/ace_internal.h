@@ -108,6 +108,11 @@ void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, 
                     int splits, int* status, cudaStream_t st);
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
                      void* Out, int* status, cudaStream_t st);
+// Diagonal of dV A^* B recomputed with FP64 accumulation into Mc (after the
+// tensor-core gram): keeps 1/2 tr M = E_x at FP32 accuracy. part: scratch.
+size_t diag_dot_part_doubles(int na);
+void launch_diag_exact(const void* A, const void* B, int na, long long ld, long long ng, double scale,
+                       double* part, double* Mc, cudaStream_t st);
 // Blocked FP64 Cholesky of -M and L^{-*}; returns the number of kernels launched.
 int launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int* status,
                         cudaStream_t st);

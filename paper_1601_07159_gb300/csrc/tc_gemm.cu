@@ -187,6 +187,61 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char* 
   mma_commit(bar);
 }
 
+// Main loop shared by both kernels. fill(stage, c) stores K chunk c. The TMEM
+// accumulator restarts every kGroup chunks and is drained into FP32 registers:
+// the tensor core's FP32 accumulation truncates, so a long chain of MMAs into
+// one accumulator drifts toward zero (about 2^-24 per accumulation); groups
+// of kGroup chunks (12 MMAs each) bound that drift to ~3e-6 relative, and the
+// register sums across groups round to nearest. Thread (warp w, lane) ends
+// with acc[j] = D[row 32 (w % 4) + lane][col 64 (w / 4) + j].
+constexpr int kGroup = 4;
+
+template <typename Fill>
+__device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks, float (&acc)[64],
+                                            Fill fill) {
+  const int tid = threadIdx.x, w = tid >> 5;
+  const uint32_t taddr = tmem + ((uint32_t)(32 * (w & 3)) << 16) + 64 * (w >> 2);
+  unsigned phase[2] = {0, 0};
+  int issued[2] = {0, 0};   // commits on a stage not yet waited for (0 or 1)
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int s = c & 1;
+    unsigned char* st = S.stage + s * STAGE_BYTES;
+    if (issued[s]) {   // the MMAs of chunk c-2 read this stage
+      ok = stage_wait(S, s, phase, issued);
+      if (!ok) break;
+    }
+    fill(st, c);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      issue_chunk(tmem, st, &S.bar[s], (c % kGroup) == 0);
+    }
+    issued[s] = 1;
+    if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) {
+      ok = stage_wait(S, s, phase, issued);   // this commit covers every MMA issued so far
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float v[32];
+      tmem_ld32(taddr, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] += v[j];
+      tmem_ld32(taddr + 32, v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[32 + j] += v[j];
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();   // all reads done before the next group's first MMA overwrites
+    }
+  }
+  // commits still in flight (only after a timeout): bounded wait before TMEM is freed
+  for (int s = 0; s < 2; ++s)
+    if (issued[s]) ok = stage_wait(S, s, phase, issued) && ok;
+  return ok;
+}
+
 // ---------------------------------------------------------------- gram
 // Grid: (ceil(na/128), ceil(nb/64), splits). part is FP64 complex [splits][na][nb].
 __global__ void __launch_bounds__(256, 1)
@@ -200,16 +255,7 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
   const long long g_begin = (long long)blockIdx.z * chunk;
   const long long g_end = g_begin + chunk < ng ? g_begin + chunk : ng;
   const int nchunks = g_end > g_begin ? (int)((g_end - g_begin + KC / 2 - 1) / (KC / 2)) : 0;
-  unsigned phase[2] = {0, 0};
-  int issued[2] = {0, 0};   // commits on a stage not yet waited for (0 or 1)
-  bool ok = true;
-  for (int c = 0; c < nchunks && ok; ++c) {
-    const int s = c & 1;
-    unsigned char* st = S.stage + s * STAGE_BYTES;
-    if (issued[s]) {   // the MMAs of chunk c-2 read this stage
-      ok = stage_wait(S, s, phase, issued);
-      if (!ok) break;
-    }
+  auto fill = [&](unsigned char* st, int c) {
     const long long g0 = g_begin + (long long)c * (KC / 2);
     // A: 128 rows x 16 complex; B: 64 rows x 16 complex -> 128 operand rows
     for (int e = tid; e < TM * 8; e += 256) {
@@ -233,52 +279,20 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
                     make_float4(vb.y, -vb.x, vb.w, -vb.z));
       }
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      issue_chunk(tmem, st, &S.bar[s], c == 0);
-    }
-    issued[s] = 1;
-  }
-  // drain: wait (bounded, also after a timeout) for the commits still in flight
-  for (int s = 0; s < 2; ++s)
-    if (issued[s]) ok = stage_wait(S, s, phase, issued) && ok;
+  };
+  float acc[64];
+  const bool ok = tc_mainloop(S, tmem, nchunks, acc, fill);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -1;
   }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && tid < 128 && nchunks > 0) {
-    const int w = tid >> 5, lane = tid & 31;
-    const int a = a0 + 32 * w + lane;
-    float re[32], im[32];
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 32 * h, re);
-      tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 64 + 32 * h, im);
-      if (a < na) {
-        double* out = part + ((long long)blockIdx.z * na + a) * nb * 2;
+  const int w = tid >> 5, lane = tid & 31;
+  const int a = a0 + 32 * (w & 3) + lane, part_ri = w >> 2;   // 0: real columns, 1: imaginary
+  if (ok && a < na) {
+    double* out = part + ((long long)blockIdx.z * na + a) * nb * 2 + part_ri;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int b = b0 + 32 * h + j;
-          if (b < nb) {
-            out[2 * b] = (double)re[j];
-            out[2 * b + 1] = (double)im[j];
-          }
-        }
-      }
-    }
-  } else if (tid < 128 && nchunks == 0) {
-    const int a = a0 + tid;
-    if (a < na)
-      for (int j = 0; j < 64; ++j) {
-        const int b = b0 + j;
-        if (b < nb) {
-          part[((long long)blockIdx.z * na + a) * nb * 2 + 2 * b] = 0.0;
-          part[((long long)blockIdx.z * na + a) * nb * 2 + 2 * b + 1] = 0.0;
-        }
-      }
+    for (int j = 0; j < 64; ++j)
+      if (b0 + j < nb) out[2 * (b0 + j)] = (double)acc[j];
   }
   tc_teardown(S, tmem);
 }
@@ -287,7 +301,7 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
 // Grid: (ceil(nb/64), ceil(ng/128)). C: FP64 complex [nk][nb].
 __global__ void __launch_bounds__(256, 1)
 outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
-                long long ng, double alpha, float2* __restrict__ Out, int* status) {
+                long long ng, double alpha, float* __restrict__ Out, int* status) {
   extern __shared__ unsigned char smem_raw[];
   TcState S = tc_setup(smem_raw);
   const uint32_t tmem = *S.tmem_slot;
@@ -295,16 +309,7 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
   const int b0 = blockIdx.x * 64;
   const long long g0 = (long long)blockIdx.y * TM;
   const int nchunks = (nk + KC / 2 - 1) / (KC / 2);
-  unsigned phase[2] = {0, 0};
-  int issued[2] = {0, 0};   // commits on a stage not yet waited for (0 or 1)
-  bool ok = true;
-  for (int c = 0; c < nchunks && ok; ++c) {
-    const int s = c & 1;
-    unsigned char* st = S.stage + s * STAGE_BYTES;
-    if (issued[s]) {   // the MMAs of chunk c-2 read this stage
-      ok = stage_wait(S, s, phase, issued);
-      if (!ok) break;
-    }
+  auto fill = [&](unsigned char* st, int c) {
     const int k0 = c * (KC / 2);
     // A rows = grid points: element (g, k) of A_k(g); loads run along g (coalesced)
     for (int e = tid; e < TM * (KC / 2); e += 256) {
@@ -326,39 +331,61 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
       split_store2(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j, 2 * kk), cr, -ci);
       split_store2(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j + 64, 2 * kk), ci, cr);
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      issue_chunk(tmem, st, &S.bar[s], c == 0);
-    }
-    issued[s] = 1;
-  }
-  for (int s = 0; s < 2; ++s)
-    if (issued[s]) ok = stage_wait(S, s, phase, issued) && ok;
+  };
+  float acc[64];
+  const bool ok = tc_mainloop(S, tmem, nchunks, acc, fill);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -2;
   }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && tid < 128 && nchunks > 0) {
-    const int w = tid >> 5, lane = tid & 31;
-    const long long g = g0 + 32 * w + lane;
-    float re[32], im[32];
-#pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 32 * h, re);
-      tmem_ld32(tmem + ((uint32_t)(32 * w) << 16) + 64 + 32 * h, im);
-      if (g < ng) {
+  const int w = tid >> 5, lane = tid & 31;
+  const long long g = g0 + 32 * (w & 3) + lane;
+  const int part_ri = w >> 2;
+  if (ok && g < ng) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int b = b0 + 32 * h + j;
-          if (b < nb) Out[(long long)b * ld + g] = make_float2((float)alpha * re[j], (float)alpha * im[j]);
-        }
-      }
-    }
+    for (int j = 0; j < 64; ++j)
+      if (b0 + j < nb) Out[2 * ((long long)(b0 + j) * ld + g) + part_ri] = (float)alpha * acc[j];
   }
   tc_teardown(S, tmem);
+}
+
+// Exact diagonal of the gram product: Mc[a][a] = (scale Re sum_g conj(A_a) B_a, 0),
+// FP32 products summed in FP32 over short runs and in FP64 across them.
+// Grid: (na, kDiagSplits); part: FP64 [na][kDiagSplits].
+constexpr int kDiagSplits = 32;
+__global__ void __launch_bounds__(256)
+diag_dot_kernel(const float2* __restrict__ A, const float2* __restrict__ B, long long ld, long long ng,
+                double* __restrict__ part) {
+  __shared__ double red[8];
+  const int a = blockIdx.x;
+  const long long per = (ng + kDiagSplits - 1) / kDiagSplits;
+  const long long g0 = blockIdx.y * per, g1 = g0 + per < ng ? g0 + per : ng;
+  double s = 0.0;
+  float run = 0.f;
+  int cnt = 0;
+  for (long long g = g0 + threadIdx.x; g < g1; g += blockDim.x) {
+    const float2 x = A[(long long)a * ld + g], y = B[(long long)a * ld + g];
+    run = fmaf(x.x, y.x, fmaf(x.y, y.y, run));
+    if (++cnt == 16) { s += (double)run; run = 0.f; cnt = 0; }
+  }
+  s += (double)run;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    part[(long long)a * kDiagSplits + blockIdx.y] = t;
+  }
+}
+
+__global__ void diag_fix_kernel(const double* __restrict__ part, int na, double scale, double* __restrict__ Mc) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= na) return;
+  double t = 0.0;
+  for (int k = 0; k < kDiagSplits; ++k) t += part[(long long)a * kDiagSplits + k];
+  Mc[2 * ((long long)a * na + a)] = scale * t;
+  Mc[2 * ((long long)a * na + a) + 1] = 0.0;
 }
 
 }  // namespace
@@ -391,7 +418,16 @@ void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long l
                      void* Out, int* status, cudaStream_t st) {
   const dim3 grid((nb + 63) / 64, (unsigned)((ng + TM - 1) / TM));
   outer_tc_kernel<<<grid, 256, SMEM_BYTES, st>>>(static_cast<const float2*>(A), nk, C, nb, ld, ng, alpha,
-                                                 static_cast<float2*>(Out), status);
+                                                 static_cast<float*>(Out), status);
+}
+
+size_t diag_dot_part_doubles(int na) { return (size_t)na * kDiagSplits; }
+
+void launch_diag_exact(const void* A, const void* B, int na, long long ld, long long ng, double scale,
+                       double* part, double* Mc, cudaStream_t st) {
+  diag_dot_kernel<<<dim3(na, kDiagSplits), 256, 0, st>>>(static_cast<const float2*>(A),
+                                                         static_cast<const float2*>(B), ld, ng, part);
+  diag_fix_kernel<<<(na + 127) / 128, 128, 0, st>>>(part, na, scale, Mc);
 }
 
 }  // namespace ace
