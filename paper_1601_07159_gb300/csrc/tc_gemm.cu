@@ -162,10 +162,10 @@ __device__ __forceinline__ void tc_teardown(const TcState& s, uint32_t tmem) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
 }
 
-// Block-uniform wait for the outstanding commit of stage s: every thread polls
-// (bounded), then the block agrees; on success the stage's phase flips.
+// Block-uniform wait for the outstanding commit of stage s: thread 0 polls
+// (bounded) and the block takes its answer; on success the stage's phase flips.
 __device__ __forceinline__ bool stage_wait(const TcState& S, int s, unsigned (&phase)[2], int (&issued)[2]) {
-  const bool mine = mbar_wait(&S.bar[s], phase[s]);
+  const bool mine = threadIdx.x == 0 ? mbar_wait(&S.bar[s], phase[s]) : true;
   const bool all = __syncthreads_and(mine ? 1 : 0) != 0;
   if (all) {
     phase[s] ^= 1;
@@ -196,9 +196,9 @@ __device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char* 
 // with acc[j] = D[row 32 (w % 4) + lane][col 64 (w / 4) + j].
 constexpr int kGroup = 4;
 
-template <typename Fill>
+template <typename Regs, typename Load, typename Store>
 __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks, float (&acc)[64],
-                                            Fill fill) {
+                                            Load load, Store store) {
   const int tid = threadIdx.x, w = tid >> 5;
   const uint32_t taddr = tmem + ((uint32_t)(32 * (w & 3)) << 16) + 64 * (w >> 2);
   unsigned phase[2] = {0, 0};
@@ -206,14 +206,18 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 64; ++j) acc[j] = 0.f;
+  Regs cur, nxt;   // chunk c in registers; chunk c + 1 loads while c is stored and issued
+  if (nchunks > 0) load(0, cur);
   for (int c = 0; c < nchunks && ok; ++c) {
     const int s = c & 1;
     unsigned char* st = S.stage + s * STAGE_BYTES;
+    if (c + 1 < nchunks) load(c + 1, nxt);
     if (issued[s]) {   // the MMAs of chunk c-2 read this stage
       ok = stage_wait(S, s, phase, issued);
       if (!ok) break;
     }
-    fill(st, c);
+    store(st, cur);
+    cur = nxt;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
@@ -255,25 +259,40 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
   const long long g_begin = (long long)blockIdx.z * chunk;
   const long long g_end = g_begin + chunk < ng ? g_begin + chunk : ng;
   const int nchunks = g_end > g_begin ? (int)((g_end - g_begin + KC / 2 - 1) / (KC / 2)) : 0;
-  auto fill = [&](unsigned char* st, int c) {
+  // A: 128 rows x 16 complex; B: 64 rows x 16 complex -> 128 operand rows.
+  // Element e = tid + 256 i (i < 4): row e / 8, complex pair e % 8 (4 real K terms).
+  struct Regs { float4 a[4], b[2]; };
+  auto load = [&](int c, Regs& R) {
     const long long g0 = g_begin + (long long)c * (KC / 2);
-    // A: 128 rows x 16 complex; B: 64 rows x 16 complex -> 128 operand rows
-    for (int e = tid; e < TM * 8; e += 256) {
-      const int r = e >> 3, q = e & 7;   // q: pair of complex values (= 4 real K terms)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + 256 * i, r = e >> 3, q = e & 7;
       const long long g = g0 + 2 * q;
-      float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+      float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
       if (a0 + r < na) {
         const float2* pa = A + (long long)(a0 + r) * ld + g;
-        if (g < g_end) { va.x = pa[0].x; va.y = pa[0].y; }
-        if (g + 1 < g_end) { va.z = pa[1].x; va.w = pa[1].y; }
+        if (g < g_end) { const float2 t = pa[0]; va.x = t.x; va.y = t.y; }
+        if (g + 1 < g_end) { const float2 t = pa[1]; va.z = t.x; va.w = t.y; }
       }
-      split_store(st, st + OP_BYTES, tile_off(r, 4 * q), va);
-      if (r < 64) {
+      R.a[i] = va;
+      if (i < 2) {   // rows r < 64 also carry B
+        float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
         if (b0 + r < nb) {
           const float2* pb = B + (long long)(b0 + r) * ld + g;
-          if (g < g_end) { vb.x = pb[0].x; vb.y = pb[0].y; }
-          if (g + 1 < g_end) { vb.z = pb[1].x; vb.w = pb[1].y; }
+          if (g < g_end) { const float2 t = pb[0]; vb.x = t.x; vb.y = t.y; }
+          if (g + 1 < g_end) { const float2 t = pb[1]; vb.z = t.x; vb.w = t.y; }
         }
+        R.b[i] = vb;
+      }
+    }
+  };
+  auto store = [&](unsigned char* st, const Regs& R) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + 256 * i, r = e >> 3, q = e & 7;
+      split_store(st, st + OP_BYTES, tile_off(r, 4 * q), R.a[i]);
+      if (i < 2) {
+        const float4 vb = R.b[i];
         split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r, 4 * q), vb);
         split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r + 64, 4 * q),
                     make_float4(vb.y, -vb.x, vb.w, -vb.z));
@@ -281,7 +300,7 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
     }
   };
   float acc[64];
-  const bool ok = tc_mainloop(S, tmem, nchunks, acc, fill);
+  const bool ok = tc_mainloop<Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -1;
@@ -309,31 +328,48 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
   const int b0 = blockIdx.x * 64;
   const long long g0 = (long long)blockIdx.y * TM;
   const int nchunks = (nk + KC / 2 - 1) / (KC / 2);
-  auto fill = [&](unsigned char* st, int c) {
+  // A rows = grid points: element (g, k) of A_k(g), e = tid + 256 i (i < 8):
+  // k = e / 128, g = g0 + e % 128 (loads run along g, coalesced).
+  // B rows: j < 64 -> (Re C, -Im C), 64 + j -> (Im C, Re C), for b = b0 + j;
+  // e = tid + 256 i (i < 4): j = e / 16, k = e % 16.
+  struct Regs { float2 a[8], c[4]; };
+  auto load = [&](int c, Regs& R) {
     const int k0 = c * (KC / 2);
-    // A rows = grid points: element (g, k) of A_k(g); loads run along g (coalesced)
-    for (int e = tid; e < TM * (KC / 2); e += 256) {
-      const int kk = e >> 7, r = e & 127;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = tid + 256 * i, kk = e >> 7, r = e & 127;
       const long long g = g0 + r;
       float2 v = make_float2(0.f, 0.f);
       if (k0 + kk < nk && g < ng) v = A[(long long)(k0 + kk) * ld + g];
-      split_store2(st, st + OP_BYTES, tile_off(r, 2 * kk), v.x, v.y);
+      R.a[i] = v;
     }
-    // B rows: j < 64 -> (Re C, -Im C), 64 + j -> (Im C, Re C), for b = b0 + j
-    for (int e = tid; e < 64 * (KC / 2); e += 256) {
-      const int j = e >> 4, kk = e & 15;
-      float cr = 0.f, ci = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + 256 * i, j = e >> 4, kk = e & 15;
+      float2 v = make_float2(0.f, 0.f);
       if (k0 + kk < nk && b0 + j < nb) {
         const long long o = 2 * ((long long)(k0 + kk) * nb + b0 + j);
-        cr = (float)C[o];
-        ci = (float)C[o + 1];
+        v = make_float2((float)C[o], (float)C[o + 1]);
       }
+      R.c[i] = v;
+    }
+  };
+  auto store = [&](unsigned char* st, const Regs& R) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int e = tid + 256 * i, kk = e >> 7, r = e & 127;
+      split_store2(st, st + OP_BYTES, tile_off(r, 2 * kk), R.a[i].x, R.a[i].y);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int e = tid + 256 * i, j = e >> 4, kk = e & 15;
+      const float cr = R.c[i].x, ci = R.c[i].y;
       split_store2(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j, 2 * kk), cr, -ci);
       split_store2(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j + 64, 2 * kk), ci, cr);
     }
   };
   float acc[64];
-  const bool ok = tc_mainloop(S, tmem, nchunks, acc, fill);
+  const bool ok = tc_mainloop<Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -2;
