@@ -13,16 +13,24 @@
 // hi.hi + hi.lo + lo.hi accumulate in FP32 in tensor memory (the lo.lo term is
 // below FP32 rounding).
 //
-// Per CTA: a 128 x 128 FP32 accumulator in TMEM (128 columns); 256 threads load
-// a K chunk of 32 real terms, split it and store hi / lo in the canonical
-// K-major no-swizzle layout (core matrices of 8 rows x 16 bytes; LBO = 128 B
-// between core matrices along K, SBO = 1024 B between 8-row groups) in one of
-// two shared-memory stages; one thread issues 4 K-steps x 3 products of
-// tcgen05.mma (M = 128, N = 128, K = 8) and commits them to the stage's
-// mbarrier, which the threads wait on before refilling that stage. Warps 0-3
-// read the accumulator back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31).
-// Every mbarrier wait is bounded: on timeout the CTA records an error in the
-// status word, stops issuing work, waits (bounded) for what it issued and
+// Per CTA (512 threads, one per SM): two 128 x 128 FP32 accumulators in TMEM
+// (256 columns). K runs in chunks of 32 real terms: the threads load chunk c+2
+// into registers while chunk c is split and stored, in the canonical K-major
+// no-swizzle layout (core matrices of 8 rows x 16 bytes; LBO = 128 B between
+// core matrices along K, SBO = 1024 B between 8-row groups; eight consecutive
+// threads fill one core matrix, so the 16-byte stores are free of bank
+// conflicts), into one of two shared-memory stages. One thread issues 4 K-steps
+// x 3 products of tcgen05.mma (M = 128, N = 128, K = 8) and commits them to the
+// stage's mbarrier; a stage is refilled only after its commit has been seen.
+//
+// The tensor core's FP32 accumulation truncates, so a long chain of MMAs into
+// one accumulator drifts toward zero (about 2^-24 per accumulation). The
+// accumulator therefore restarts every kGroup chunks (12 MMAs each, drift
+// ~3e-6 relative), alternating between the two TMEM buffers; a finished group
+// is read back (tcgen05.ld, warp w owns lanes 32 (w % 4)..+31) and added in
+// FP32 registers, round-to-nearest, while the next group's MMAs run.
+// Every mbarrier wait is bounded: on timeout the CTA records ACE_ERR_TIMEOUT in
+// the status word, stops issuing work, waits (bounded) for what it issued and
 // releases its tensor memory.
 #include <cstdint>
 
@@ -32,13 +40,16 @@ namespace ace {
 
 namespace {
 
-constexpr int TM = 128;            // rows per CTA (M of the MMA)
-constexpr int TN = 128;            // accumulator columns (N of the MMA)
-constexpr int KC = 32;             // real K terms per stage
+constexpr int THREADS = 512;
+constexpr int TM = 128;                    // rows per CTA (M of the MMA)
+constexpr int TN = 128;                    // columns of one accumulator (N of the MMA)
+constexpr int TMEM_COLS = 2 * TN;          // two accumulators
+constexpr int KC = 32;                     // real K terms per stage
 constexpr int SBO = (KC / 4) * 128;        // bytes between 8-row groups = 1024
 constexpr int OP_BYTES = TM * KC * 4;      // one operand tile (128 x 32 FP32) = 16 KB
 constexpr int STAGE_BYTES = 4 * OP_BYTES;  // A_hi, A_lo, B_hi, B_lo = 64 KB
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024;
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024 + 64;
+constexpr int kGroup = 4;                  // chunks per accumulator group
 constexpr unsigned kWaitLimit = 1u << 24;
 
 // instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
@@ -49,6 +60,7 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// shared-memory matrix descriptor: start, LBO = 128 B, SBO, descriptor version 1, no swizzle
 __device__ __forceinline__ uint64_t mat_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
          ((uint64_t)(SBO >> 4) << 32) | (1ull << 46);
@@ -65,11 +77,6 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
   const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
   *reinterpret_cast<float4*>(hi + off) = h;
   *reinterpret_cast<float4*>(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-}
-__device__ __forceinline__ void split_store2(unsigned char* hi, unsigned char* lo, int off, float a, float b) {
-  const float ha = tf32_hi(a), hb = tf32_hi(b);
-  *reinterpret_cast<float2*>(hi + off) = make_float2(ha, hb);
-  *reinterpret_cast<float2*>(lo + off) = make_float2(a - ha, b - hb);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -107,8 +114,8 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+// 32 consecutive accumulator columns of this thread's lane, added into acc
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
   uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -121,10 +128,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) acc[i] += __uint_as_float(r[i]);
 }
 
-// Shared prologue / epilogue of both kernels.
 struct TcState {
   uint64_t* bar;        // [2] stage barriers
   uint32_t* tmem_slot;  // TMEM base address written by tcgen05.alloc
@@ -142,9 +148,9 @@ __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
     mbar_init(&s.bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (threadIdx.x < 32) {   // warp 0 allocates the 128-column accumulator
+  if (threadIdx.x < 32) {   // warp 0 allocates the two accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s.tmem_slot)),
-                 "r"(TN)
+                 "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -154,101 +160,100 @@ __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
   return s;
 }
 
-__device__ __forceinline__ void tc_teardown(const TcState& s, uint32_t tmem) {
+__device__ __forceinline__ void tc_teardown(uint32_t tmem) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
-// Block-uniform wait for the outstanding commit of stage s: thread 0 polls
-// (bounded) and the block takes its answer; on success the stage's phase flips.
-__device__ __forceinline__ bool stage_wait(const TcState& S, int s, unsigned (&phase)[2], int (&issued)[2]) {
-  const bool mine = threadIdx.x == 0 ? mbar_wait(&S.bar[s], phase[s]) : true;
-  const bool all = __syncthreads_and(mine ? 1 : 0) != 0;
-  if (all) {
-    phase[s] ^= 1;
-    issued[s] = 0;
-  }
-  return all;
-}
-
-// One K chunk in a stage: 4 K-steps x 3 split products, committed to `bar`.
-__device__ __forceinline__ void issue_chunk(uint32_t tmem, const unsigned char* st, uint64_t* bar, bool first) {
+// One K chunk in a stage: 4 K-steps x 3 split products into accumulator `dtmem`,
+// committed to `bar`.
+__device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char* st, uint64_t* bar, bool first) {
   const uint32_t ah = smem_u32(st), al = ah + OP_BYTES, bh = ah + 2 * OP_BYTES, bl = ah + 3 * OP_BYTES;
 #pragma unroll
   for (int ks = 0; ks < KC / 8; ++ks) {
     const uint32_t o = ks * 256;   // two core matrices of 16 B along K per step
-    mma_tf32(tmem, mat_desc(ah + o), mat_desc(bh + o), (first && ks == 0) ? 0u : 1u);
-    mma_tf32(tmem, mat_desc(ah + o), mat_desc(bl + o), 1u);
-    mma_tf32(tmem, mat_desc(al + o), mat_desc(bh + o), 1u);
+    mma_tf32(dtmem, mat_desc(ah + o), mat_desc(bh + o), (first && ks == 0) ? 0u : 1u);
+    mma_tf32(dtmem, mat_desc(ah + o), mat_desc(bl + o), 1u);
+    mma_tf32(dtmem, mat_desc(al + o), mat_desc(bh + o), 1u);
   }
   mma_commit(bar);
 }
 
-// Main loop shared by both kernels. fill(stage, c) stores K chunk c. The TMEM
-// accumulator restarts every kGroup chunks and is drained into FP32 registers:
-// the tensor core's FP32 accumulation truncates, so a long chain of MMAs into
-// one accumulator drifts toward zero (about 2^-24 per accumulation); groups
-// of kGroup chunks (12 MMAs each) bound that drift to ~3e-6 relative, and the
-// register sums across groups round to nearest. Thread (warp w, lane) ends
-// with acc[j] = D[row 32 (w % 4) + lane][col 64 (w / 4) + j].
-constexpr int kGroup = 4;
-
+// Main loop shared by both kernels: load(c, regs) fetches chunk c from global
+// memory, store(stage, regs) splits it into the stage. On return thread
+// (warp w, lane) holds acc[j] = D[row 32 (w % 4) + lane][col 32 (w / 4) + j].
 template <typename Regs, typename Load, typename Store>
-__device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks, float (&acc)[64],
+__device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks, float (&acc)[32],
                                             Load load, Store store) {
   const int tid = threadIdx.x, w = tid >> 5;
-  const uint32_t taddr = tmem + ((uint32_t)(32 * (w & 3)) << 16) + 64 * (w >> 2);
+  const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + 32 * (w >> 2);
+  __shared__ int s_ok;
   unsigned phase[2] = {0, 0};
-  int issued[2] = {0, 0};   // commits on a stage not yet waited for (0 or 1)
+  int issued[2] = {0, 0};   // commit on the stage not yet seen (0 or 1)
+  int drain[2] = {0, 0};    // 1 + accumulator buffer to read once that commit is seen
   bool ok = true;
 #pragma unroll
-  for (int j = 0; j < 64; ++j) acc[j] = 0.f;
-  Regs cur, nxt;   // chunk c in registers; chunk c + 1 loads while c is stored and issued
-  if (nchunks > 0) load(0, cur);
+  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+
+  // block-uniform bounded wait for the commit on stage s, then the pending drain
+  auto settle = [&](int s) -> bool {
+    if (tid == 0) s_ok = mbar_wait(&S.bar[s], phase[s]) ? 1 : 0;
+    __syncthreads();
+    const bool good = s_ok != 0;
+    __syncthreads();   // s_ok is rewritten by the next wait
+    if (!good) return false;
+    phase[s] ^= 1;
+    issued[s] = 0;
+    if (drain[s]) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tmem_add32(tmem + lane_col + (uint32_t)(TN * (drain[s] - 1)), acc);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      drain[s] = 0;
+    }
+    return true;
+  };
+
+  Regs r0, r1, r2;   // chunks c, c + 1, c + 2 (rotated by register moves)
+  if (nchunks > 0) load(0, r0);
+  if (nchunks > 1) load(1, r1);
   for (int c = 0; c < nchunks && ok; ++c) {
     const int s = c & 1;
     unsigned char* st = S.stage + s * STAGE_BYTES;
-    if (c + 1 < nchunks) load(c + 1, nxt);
+    if (c + 2 < nchunks) load(c + 2, r2);
     if (issued[s]) {   // the MMAs of chunk c-2 read this stage
-      ok = stage_wait(S, s, phase, issued);
+      ok = settle(s);
       if (!ok) break;
     }
-    store(st, cur);
-    cur = nxt;
+    store(st, r0);
+    r0 = r1;
+    r1 = r2;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    const int group = c / kGroup;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      issue_chunk(tmem, st, &S.bar[s], (c % kGroup) == 0);
+      issue_chunk(tmem + (uint32_t)(TN * (group & 1)), st, &S.bar[s], (c % kGroup) == 0);
     }
     issued[s] = 1;
-    if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) {
-      ok = stage_wait(S, s, phase, issued);   // this commit covers every MMA issued so far
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float v[32];
-      tmem_ld32(taddr, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] += v[j];
-      tmem_ld32(taddr + 32, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) acc[32 + j] += v[j];
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncthreads();   // all reads done before the next group's first MMA overwrites
-    }
+    if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) drain[s] = 1 + (group & 1);
   }
-  // commits still in flight (only after a timeout): bounded wait before TMEM is freed
-  for (int s = 0; s < 2; ++s)
-    if (issued[s]) ok = stage_wait(S, s, phase, issued) && ok;
+  // remaining commits, in chunk order (bounded; also after a timeout)
+  if (nchunks > 0) {
+    const int last = (nchunks - 1) & 1;
+    if (issued[last ^ 1]) ok = settle(last ^ 1) && ok;
+    if (issued[last]) ok = settle(last) && ok;
+  }
   return ok;
 }
 
 // ---------------------------------------------------------------- gram
 // Grid: (ceil(na/128), ceil(nb/64), splits). part is FP64 complex [splits][na][nb].
-__global__ void __launch_bounds__(256, 1)
+// Chunk element e (A: 0..1023, B: 0..511) -> row 8 (e / 64) + e % 8, complex
+// pair (e / 8) % 8 (four real K terms).
+__global__ void __launch_bounds__(THREADS, 1)
 gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ B, int nb, long long ld,
                long long ng, double* __restrict__ part, long long chunk, int* status) {
   extern __shared__ unsigned char smem_raw[];
@@ -259,66 +264,62 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
   const long long g_begin = (long long)blockIdx.z * chunk;
   const long long g_end = g_begin + chunk < ng ? g_begin + chunk : ng;
   const int nchunks = g_end > g_begin ? (int)((g_end - g_begin + KC / 2 - 1) / (KC / 2)) : 0;
-  // A: 128 rows x 16 complex; B: 64 rows x 16 complex -> 128 operand rows.
-  // Element e = tid + 256 i (i < 4): row e / 8, complex pair e % 8 (4 real K terms).
-  struct Regs { float4 a[4], b[2]; };
-  auto load = [&](int c, Regs& R) {
+  struct Regs { float4 a[2], b; };
+  auto rowq = [](int e, int& r, int& q) { r = ((e >> 6) << 3) | (e & 7); q = (e >> 3) & 7; };
+  auto load = [&](int c, Regs& Rg) {
     const long long g0 = g_begin + (long long)c * (KC / 2);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + 256 * i, r = e >> 3, q = e & 7;
-      const long long g = g0 + 2 * q;
-      float4 va = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (a0 + r < na) {
-        const float2* pa = A + (long long)(a0 + r) * ld + g;
-        if (g < g_end) { const float2 t = pa[0]; va.x = t.x; va.y = t.y; }
-        if (g + 1 < g_end) { const float2 t = pa[1]; va.z = t.x; va.w = t.y; }
-      }
-      R.a[i] = va;
-      if (i < 2) {   // rows r < 64 also carry B
-        float4 vb = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (b0 + r < nb) {
-          const float2* pb = B + (long long)(b0 + r) * ld + g;
-          if (g < g_end) { const float2 t = pb[0]; vb.x = t.x; vb.y = t.y; }
-          if (g + 1 < g_end) { const float2 t = pb[1]; vb.z = t.x; vb.w = t.y; }
-        }
-        R.b[i] = vb;
-      }
+    for (int i = 0; i < 2; ++i) {
+      int r, q;
+      rowq(tid + THREADS * i, r, q);
+      const long long g = g0 + 2 * q;   // even; g_end is even, so g < g_end covers g + 1
+      Rg.a[i] = (a0 + r < na && g < g_end)
+                    ? *reinterpret_cast<const float4*>(A + (long long)(a0 + r) * ld + g)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    int r, q;
+    rowq(tid, r, q);
+    const long long g = g0 + 2 * q;
+    Rg.b = (b0 + r < nb && g < g_end) ? *reinterpret_cast<const float4*>(B + (long long)(b0 + r) * ld + g)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
   };
-  auto store = [&](unsigned char* st, const Regs& R) {
+  auto store = [&](unsigned char* st, const Regs& Rg) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + 256 * i, r = e >> 3, q = e & 7;
-      split_store(st, st + OP_BYTES, tile_off(r, 4 * q), R.a[i]);
-      if (i < 2) {
-        const float4 vb = R.b[i];
-        split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r, 4 * q), vb);
-        split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r + 64, 4 * q),
-                    make_float4(vb.y, -vb.x, vb.w, -vb.z));
-      }
+    for (int i = 0; i < 2; ++i) {
+      int r, q;
+      rowq(tid + THREADS * i, r, q);
+      split_store(st, st + OP_BYTES, tile_off(r, 4 * q), Rg.a[i]);
     }
+    int r, q;
+    rowq(tid, r, q);
+    const float4 vb = Rg.b;
+    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r, 4 * q), vb);
+    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r + 64, 4 * q),
+                make_float4(vb.y, -vb.x, vb.w, -vb.z));
   };
-  float acc[64];
+  float acc[32];
   const bool ok = tc_mainloop<Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -1;
   }
   const int w = tid >> 5, lane = tid & 31;
-  const int a = a0 + 32 * (w & 3) + lane, part_ri = w >> 2;   // 0: real columns, 1: imaginary
+  const int a = a0 + 32 * (w & 3) + lane;
+  const int ri = (w >> 2) >> 1, bq = ((w >> 2) & 1) * 32;   // columns 0-63 real, 64-127 imaginary
   if (ok && a < na) {
-    double* out = part + ((long long)blockIdx.z * na + a) * nb * 2 + part_ri;
+    double* out = part + ((long long)blockIdx.z * na + a) * nb * 2 + ri;
 #pragma unroll
-    for (int j = 0; j < 64; ++j)
-      if (b0 + j < nb) out[2 * (b0 + j)] = (double)acc[j];
+    for (int j = 0; j < 32; ++j)
+      if (b0 + bq + j < nb) out[2 * (b0 + bq + j)] = (double)acc[j];
   }
-  tc_teardown(S, tmem);
+  tc_teardown(tmem);
 }
 
 // ---------------------------------------------------------------- outer
 // Grid: (ceil(nb/64), ceil(ng/128)). C: FP64 complex [nk][nb].
-__global__ void __launch_bounds__(256, 1)
+// A element e (0..1023): grid point g0 + e % 128, K pair e / 128 (k = 2 (e / 128)).
+// B element e (0..511): b = b0 + e % 64, K pair e / 64.
+__global__ void __launch_bounds__(THREADS, 1)
 outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
                 long long ng, double alpha, float* __restrict__ Out, int* status) {
   extern __shared__ unsigned char smem_raw[];
@@ -328,47 +329,48 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
   const int b0 = blockIdx.x * 64;
   const long long g0 = (long long)blockIdx.y * TM;
   const int nchunks = (nk + KC / 2 - 1) / (KC / 2);
-  // A rows = grid points: element (g, k) of A_k(g), e = tid + 256 i (i < 8):
-  // k = e / 128, g = g0 + e % 128 (loads run along g, coalesced).
-  // B rows: j < 64 -> (Re C, -Im C), 64 + j -> (Im C, Re C), for b = b0 + j;
-  // e = tid + 256 i (i < 4): j = e / 16, k = e % 16.
-  struct Regs { float2 a[8], c[4]; };
-  auto load = [&](int c, Regs& R) {
+  struct Regs { float4 a[2], c; };
+  auto load = [&](int c, Regs& Rg) {
     const int k0 = c * (KC / 2);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int e = tid + 256 * i, kk = e >> 7, r = e & 127;
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + THREADS * i, r = e & 127, k = k0 + 2 * (e >> 7);
       const long long g = g0 + r;
-      float2 v = make_float2(0.f, 0.f);
-      if (k0 + kk < nk && g < ng) v = A[(long long)(k0 + kk) * ld + g];
-      R.a[i] = v;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + 256 * i, j = e >> 4, kk = e & 15;
-      float2 v = make_float2(0.f, 0.f);
-      if (k0 + kk < nk && b0 + j < nb) {
-        const long long o = 2 * ((long long)(k0 + kk) * nb + b0 + j);
-        v = make_float2((float)C[o], (float)C[o + 1]);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g < ng) {
+        if (k < nk) { const float2 t = A[(long long)k * ld + g]; v.x = t.x; v.y = t.y; }
+        if (k + 1 < nk) { const float2 t = A[(long long)(k + 1) * ld + g]; v.z = t.x; v.w = t.y; }
       }
-      R.c[i] = v;
+      Rg.a[i] = v;
     }
+    const int j = tid & 63, k = k0 + 2 * (tid >> 6);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b0 + j < nb) {
+      if (k < nk) {
+        const long long o = 2 * ((long long)k * nb + b0 + j);
+        v.x = (float)C[o];
+        v.y = (float)C[o + 1];
+      }
+      if (k + 1 < nk) {
+        const long long o = 2 * ((long long)(k + 1) * nb + b0 + j);
+        v.z = (float)C[o];
+        v.w = (float)C[o + 1];
+      }
+    }
+    Rg.c = v;   // (Re C_k, Im C_k, Re C_k+1, Im C_k+1)
   };
-  auto store = [&](unsigned char* st, const Regs& R) {
+  auto store = [&](unsigned char* st, const Regs& Rg) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int e = tid + 256 * i, kk = e >> 7, r = e & 127;
-      split_store2(st, st + OP_BYTES, tile_off(r, 2 * kk), R.a[i].x, R.a[i].y);
+    for (int i = 0; i < 2; ++i) {
+      const int e = tid + THREADS * i, r = e & 127, kq = 4 * (e >> 7);
+      split_store(st, st + OP_BYTES, tile_off(r, kq), Rg.a[i]);
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int e = tid + 256 * i, j = e >> 4, kk = e & 15;
-      const float cr = R.c[i].x, ci = R.c[i].y;
-      split_store2(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j, 2 * kk), cr, -ci);
-      split_store2(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j + 64, 2 * kk), ci, cr);
-    }
+    const int j = tid & 63, kq = 4 * (tid >> 6);
+    const float4 v = Rg.c;
+    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j, kq), make_float4(v.x, -v.y, v.z, -v.w));
+    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j + 64, kq), make_float4(v.y, v.x, v.w, v.z));
   };
-  float acc[64];
+  float acc[32];
   const bool ok = tc_mainloop<Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
@@ -376,13 +378,13 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
   }
   const int w = tid >> 5, lane = tid & 31;
   const long long g = g0 + 32 * (w & 3) + lane;
-  const int part_ri = w >> 2;
+  const int ri = (w >> 2) >> 1, bq = ((w >> 2) & 1) * 32;
   if (ok && g < ng) {
 #pragma unroll
-    for (int j = 0; j < 64; ++j)
-      if (b0 + j < nb) Out[2 * ((long long)(b0 + j) * ld + g) + part_ri] = (float)alpha * acc[j];
+    for (int j = 0; j < 32; ++j)
+      if (b0 + bq + j < nb) Out[2 * ((long long)(b0 + bq + j) * ld + g) + ri] = (float)alpha * acc[j];
   }
-  tc_teardown(S, tmem);
+  tc_teardown(tmem);
 }
 
 // Exact diagonal of the gram product: Mc[a][a] = (scale Re sum_g conj(A_a) B_a, 0),
@@ -434,7 +436,7 @@ bool tc_gemm_prepare() {
 
 int gram_tc_splits(long long ng, int na, int nb) {
   const long long tiles = (long long)((na + TM - 1) / TM) * ((nb + 63) / 64);
-  long long s = 152 / tiles;   // one wave of one CTA per SM (132 KB of shared memory each)
+  long long s = 152 / tiles;   // one wave of one CTA per SM
   const long long max_s = (ng + KC / 2 - 1) / (KC / 2);
   if (s > max_s) s = max_s;
   if (s < 1) s = 1;
@@ -446,15 +448,15 @@ void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, 
   long long chunk = (ng + splits - 1) / splits;
   chunk = (chunk + KC / 2 - 1) / (KC / 2) * (KC / 2);
   const dim3 grid((na + TM - 1) / TM, (nb + 63) / 64, splits);
-  gram_tc_kernel<<<grid, 256, SMEM_BYTES, st>>>(static_cast<const float2*>(A), na, static_cast<const float2*>(B), nb,
-                                                ld, ng, part, chunk, status);
+  gram_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(static_cast<const float2*>(A), na,
+                                                    static_cast<const float2*>(B), nb, ld, ng, part, chunk, status);
 }
 
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
                      void* Out, int* status, cudaStream_t st) {
   const dim3 grid((nb + 63) / 64, (unsigned)((ng + TM - 1) / TM));
-  outer_tc_kernel<<<grid, 256, SMEM_BYTES, st>>>(static_cast<const float2*>(A), nk, C, nb, ld, ng, alpha,
-                                                 static_cast<float*>(Out), status);
+  outer_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(static_cast<const float2*>(A), nk, C, nb, ld, ng, alpha,
+                                                     static_cast<float*>(Out), status);
 }
 
 size_t diag_dot_part_doubles(int na) { return (size_t)na * kDiagSplits; }
