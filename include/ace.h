@@ -97,6 +97,11 @@ typedef struct {
 /* ACE_DTYPE_C64: run M = Phi^* W, Xi = W L^{-*} and the apply on CUDA cores in
  * FP32 instead of the tensor cores (tcgen05 TF32 with a 3-term split). */
 #define ACE_FLAG_SIMT_GEMM 8
+/* Graph mode: issue pass A of every pair batch on one stream and passes B-D on
+ * a second, so that pass A of batch k+1 (which waits only for pass C of batch
+ * k) overlaps pass D of batch k. Needs two scratch buffers: lanes is raised to
+ * at least 2. Results are bitwise those of the default schedule. */
+#define ACE_FLAG_OVERLAP 16
 
 typedef struct ace_plan ace_plan;
 

@@ -80,6 +80,8 @@ struct ace_plan {
   bool graphs = true;
   bool engine = true;            // persistent pair engine (else four kernels per batch)
   bool tc = false;               // tensor-core GEMMs (complex FP32 storage)
+  bool overlap = false;          // pass A of the next batch overlaps pass D (graph mode)
+  cudaEvent_t ov_ev[2] = {};
   EngineInfo einfo;
   std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
   Schedule build;                // symmetric schedule of the W build
@@ -366,6 +368,40 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
     }
     return kernels;
   }
+  if (p->overlap && base.mode != 1) {
+    // Two streams: lane 0 runs pass A of every batch, lane 1 runs B, C and D.
+    // A(k+1) waits only for C(k), so it overlaps D(k) (filling D's tail);
+    // the scratch alternates between two buffers, and A(k+2) follows C(k+1),
+    // which follows D(k) on lane 1, so a buffer is free before it is rewritten.
+    cudaStream_t la = p->lane[0], lb = p->lane[1];
+    cudaEventRecord(p->fork_ev, cs);
+    cudaStreamWaitEvent(la, p->fork_ev, 0);
+    cudaStreamWaitEvent(lb, p->fork_ev, 0);
+    bool ok = true;
+    for (size_t k = 0; k < sc.batches.size(); ++k) {
+      PairLaunch L = base;
+      L.S = S0 + (k & 1) * lane_bytes(p);
+      L.Epart = E0;
+      L.ev = nullptr;
+      L.dtiles = sc.dtiles + sc.toff[k];
+      L.pass_mask = 1;
+      ok = ok && launch_one(p, L, sc.batches[k], la);
+      cudaEventRecord(p->ov_ev[0], la);
+      cudaStreamWaitEvent(lb, p->ov_ev[0], 0);
+      L.pass_mask = 2 | 4;
+      ok = ok && launch_one(p, L, sc.batches[k], lb);
+      cudaEventRecord(p->ov_ev[1], lb);
+      cudaStreamWaitEvent(la, p->ov_ev[1], 0);
+      L.pass_mask = 8;
+      ok = ok && launch_one(p, L, sc.batches[k], lb);
+      kernels += 4;
+    }
+    cudaEventRecord(p->join_ev[0], la);
+    cudaStreamWaitEvent(cs, p->join_ev[0], 0);
+    cudaEventRecord(p->join_ev[1], lb);
+    cudaStreamWaitEvent(cs, p->join_ev[1], 0);
+    return ok ? kernels : -1;
+  }
   const int nl = p->lanes;
   auto fork = [&]() {
     cudaEventRecord(p->fork_ev, cs);
@@ -529,6 +565,8 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
   p->engine = (d->flags & ACE_FLAG_ENGINE) != 0;
   p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM);
+  p->overlap = p->graphs && !p->engine && (d->flags & ACE_FLAG_OVERLAP);
+  if (p->overlap && p->lanes < 2) p->lanes = 2;
   const size_t slot = (size_t)p->ng * p->csize;
   const int tt = p->tile * p->tile;
   if (d->max_pairs) {
@@ -587,6 +625,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   for (int i = 0; i < p->lanes && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&p->lane[i], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
   for (int i = 0; i < p->lanes && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->ov_ev[i], cudaEventDisableTiming);
   if (e == cudaSuccess) {
     PairLaunch prep = base_launch(p);
     prep.prepare_only = true;
@@ -628,6 +667,8 @@ ace_status ace_plan_destroy(ace_plan* p) {
   }
   if (p->cap) cudaStreamDestroy(p->cap);
   if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+  for (cudaEvent_t e : p->ov_ev)
+    if (e) cudaEventDestroy(e);
   free_schedule(p->build);
   for (auto& r : p->rect) free_schedule(r.second);
   cudaFree(p->Kt);

@@ -54,6 +54,7 @@ diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int
   __shared__ double2 a[NB][NB + 1];
   __shared__ double2 col[NB];
   __shared__ int fail;
+  __shared__ double rcp;   // one FP64 reciprocal per step, shared (FP64 division is costly here)
   const int tid = threadIdx.x;
   if (status[0] != 0) return;
   for (int e = tid; e < NB * NB; e += blockDim.x) {
@@ -70,12 +71,14 @@ diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int
       } else if (!(d > 0.0)) {
         fail = 1; status[0] = -2; status[1] = p0 + j + 1;
       } else {
-        a[j][j] = make_double2(sqrt(d), 0.0);
+        const double l = sqrt(d);
+        a[j][j] = make_double2(l, 0.0);
+        rcp = 1.0 / l;
       }
     }
     __syncthreads();
     if (fail) return;
-    const double inv = 1.0 / a[j][j].x;
+    const double inv = rcp;
     if (tid > j && tid < nb) {
       a[tid][j].x *= inv;
       a[tid][j].y *= inv;
@@ -96,9 +99,10 @@ diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int
   __syncthreads();
   // in-place inverse, columns from the right
   for (int j = nb - 1; j >= 0; --j) {
-    const double xjj = 1.0 / a[j][j].x;
+    if (tid == 0) rcp = 1.0 / a[j][j].x;
     if (tid > j && tid < nb) col[tid] = a[tid][j];
     __syncthreads();
+    const double xjj = rcp;
     if (tid > j && tid < nb) {
       double2 s = make_double2(0.0, 0.0);
       for (int k = j + 1; k <= tid; ++k) s = zfma(s, a[tid][k], col[k]);

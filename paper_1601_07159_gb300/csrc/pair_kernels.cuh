@@ -662,28 +662,33 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   if constexpr (sizeof(R) != 8) {
     if (L.real_io) return false;
   }
+  const int mask = L.pass_mask ? L.pass_mask : 15;
   mark(0);
-  if constexpr (sizeof(R) == 8) {
-    if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
-    else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
-  } else {
-    launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+  if (mask & 1) {
+    if constexpr (sizeof(R) == 8) {
+      if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
+      else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+    } else {
+      launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
+    }
   }
   mark(1);
-  launch_pdl(!L.no_pdl, pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
+  if (mask & 2) launch_pdl(!L.no_pdl, pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
   mark(2);
   if (L.mode == 1) {
     mark(3);
     mark(4);
     return true;
   }
-  launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
+  if (mask & 4) launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
   mark(3);
-  if constexpr (sizeof(R) == 8) {
-    if (L.real_io) launch_pdl(!L.no_pdl, pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
-    else launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
-  } else {
-    launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+  if (mask & 8) {
+    if constexpr (sizeof(R) == 8) {
+      if (L.real_io) launch_pdl(!L.no_pdl, pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
+      else launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+    } else {
+      launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+    }
   }
   mark(4);
   return true;

@@ -115,18 +115,20 @@ def test_bitwise_reproducible(ace):
     assert rel(_host(c["W"]), ref) < 1e-6 and rel(_host(a["W"]), ref) < 1e-6
 
 
-@pytest.mark.parametrize("engine,lanes,graphs", [(True, 1, True), (True, 1, False), (False, 3, True)])
-def test_schedules_match_bitwise(ace, engine, lanes, graphs):
+@pytest.mark.parametrize("engine,lanes,graphs,overlap", [(True, 1, True, False), (True, 1, False, False),
+                                                        (False, 3, True, False), (False, 0, True, True)])
+def test_schedules_match_bitwise(ace, engine, lanes, graphs, overlap):
     """Every way of running the pair schedule gives the same bits as eager
-    four-kernel launches: the persistent engine (in or out of a graph) and the
+    four-kernel launches: the persistent engine (in or out of a graph), the
     four-kernel path replayed from a graph with a round's batches spread over
-    lanes. Each output element is written by one tile per round and rounds run
-    in order. New pointers capture a new graph."""
+    lanes, and the two-stream schedule in which pass A of a batch overlaps
+    pass D of the previous one. Each output element is written by one tile per
+    round and rounds run in order. New pointers capture a new graph."""
     s, phi, psi, kern = _inputs(24, 10.0, 21, 10, "c64", "erfc", 0.3, seed=8)
     eager = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
                      graphs=False)
     graph = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
-                     lanes=lanes, graphs=graphs, engine=engine)
+                     lanes=lanes, graphs=graphs, engine=engine, overlap=overlap)
     phi_d = _dev(phi, "c64", ace)
     psi_d = _dev(psi, "c64", ace)
     a = eager.build(phi_d)
@@ -144,7 +146,8 @@ def test_schedules_match_bitwise(ace, engine, lanes, graphs):
     yb2 = graph.exchange_apply(phi_d, psi_d)
     assert torch.equal(yb1, yb2)
     d = float(torch.linalg.vector_norm(ya - yb2) / torch.linalg.vector_norm(ya))
-    print(f"exchange apply, engine={engine} lanes={lanes} graphs={graphs}: rel diff to eager {d:.3e}")
+    print(f"exchange apply, engine={engine} lanes={lanes} graphs={graphs} overlap={overlap}: "
+          f"rel diff to eager {d:.3e}")
     assert d < 1e-6
     ea, ga = eager.energy_grad(phi_d, grad=True, grad_scale=-1.5)
     eb, gb = graph.energy_grad(phi_d, grad=True, grad_scale=-1.5)
