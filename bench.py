@@ -54,7 +54,8 @@ def parse():
                    help="four kernels per batch, launched eagerly (per-pass timings)")
     p.add_argument("--engine", action="store_true", help="persistent pair engine")
     p.add_argument("--no-pdl", action="store_true", help="no programmatic dependent launch")
-    p.add_argument("--overlap", action="store_true", help="overlap pass A of a batch with pass D of the previous")
+    p.add_argument("--no-overlap", action="store_true",
+                   help="spread a round's batches over lanes instead of overlapping pass A with pass D")
     return p.parse_args()
 
 
@@ -226,7 +227,7 @@ def run_ours(args):
     plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega,
                     max_pairs=args.max_pairs, tile=args.tile, lanes=args.lanes,
                     graphs=not args.eager, engine=args.engine and not args.eager,
-                    pdl=not args.no_pdl, overlap=args.overlap)
+                    pdl=not args.no_pdl, overlap=not args.no_overlap)
     td = torch.complex64
     phi_h = torch.from_numpy(phi).to(td).pin_memory()
     psi_h = torch.from_numpy(psi).to(td).pin_memory()

@@ -76,8 +76,9 @@ typedef struct {
   int max_pairs;     /* pair solves in flight per batch (0 = library default); sets the
                         size of the pair-spectrum scratch in the workspace */
   int tile;          /* orbitals per pair tile, 1..8 (0 = default 8) */
-  int lanes;         /* concurrent batch streams inside one call, 1..8 (0 = default 2);
-                        the pair scratch is lanes * max_pairs slots */
+  int lanes;         /* concurrent batch streams inside one call with
+                        ACE_FLAG_NO_OVERLAP, 1..8 (0 = default 2; at least 2
+                        otherwise); the pair scratch is lanes * max_pairs slots */
   int flags;         /* ACE_FLAG_* */
 } ace_desc;
 
@@ -97,11 +98,12 @@ typedef struct {
 /* ACE_DTYPE_C64: run M = Phi^* W, Xi = W L^{-*} and the apply on CUDA cores in
  * FP32 instead of the tensor cores (tcgen05 TF32 with a 3-term split). */
 #define ACE_FLAG_SIMT_GEMM 8
-/* Graph mode: issue pass A of every pair batch on one stream and passes B-D on
- * a second, so that pass A of batch k+1 (which waits only for pass C of batch
- * k) overlaps pass D of batch k. Needs two scratch buffers: lanes is raised to
- * at least 2. Results are bitwise those of the default schedule. */
-#define ACE_FLAG_OVERLAP 16
+/* By default, graph mode issues pass A of every pair batch on one stream and
+ * passes B-D on a second, so that pass A of batch k+1 (which waits for pass C of
+ * batch k) overlaps pass D of batch k; the scratch holds two batches (lanes is
+ * raised to at least 2). This flag turns that off: the batches of a round are
+ * then spread over `lanes` streams instead. Results are bitwise the same. */
+#define ACE_FLAG_NO_OVERLAP 16
 
 typedef struct ace_plan ace_plan;
 

@@ -117,7 +117,7 @@ class Plan:
                  omega: float = 0.0, g0: float | None = None, alpha: float = 1.0,
                  max_pairs: int = 0, tile: int = 0, lanes: int = 0, graphs: bool = True,
                  engine: bool = False, pdl: bool = True, tensor_cores: bool = True,
-                 overlap: bool = False):
+                 overlap: bool = True):
         if isinstance(L, (int, float)):
             L = (float(L),) * 3
         d = Desc()
@@ -132,7 +132,7 @@ class Plan:
         d.max_pairs = max_pairs
         d.tile = tile
         d.lanes = lanes
-        d.flags = (0 if graphs else 1) | (2 if engine else 0) | (0 if pdl else 4) | (0 if tensor_cores else 8) | (16 if overlap else 0)
+        d.flags = (0 if graphs else 1) | (2 if engine else 0) | (0 if pdl else 4) | (0 if tensor_cores else 8) | (0 if overlap else 16)
         h = _vp()
         _check(_lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h

@@ -80,8 +80,9 @@ struct ace_plan {
   bool graphs = true;
   bool engine = true;            // persistent pair engine (else four kernels per batch)
   bool tc = false;               // tensor-core GEMMs (complex FP32 storage)
-  bool overlap = false;          // pass A of the next batch overlaps pass D (graph mode)
+  bool overlap = false;          // graph mode: pass A of batch k+1 overlaps pass D of batch k
   cudaEvent_t ov_ev[2] = {};
+
   EngineInfo einfo;
   std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
   Schedule build;                // symmetric schedule of the W build
@@ -370,9 +371,10 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
   }
   if (p->overlap && base.mode != 1) {
     // Two streams: lane 0 runs pass A of every batch, lane 1 runs B, C and D.
-    // A(k+1) waits only for C(k), so it overlaps D(k) (filling D's tail);
-    // the scratch alternates between two buffers, and A(k+2) follows C(k+1),
-    // which follows D(k) on lane 1, so a buffer is free before it is rewritten.
+    // A(k+1) waits for C(k), so it overlaps D(k) and fills D's tail; the
+    // scratch alternates between two buffers, and C(k) completes after D(k-1)
+    // (same stream), so a buffer is free before A rewrites it. Letting A run
+    // further ahead, or moving B or C to lane 0, measured slower.
     cudaStream_t la = p->lane[0], lb = p->lane[1];
     cudaEventRecord(p->fork_ev, cs);
     cudaStreamWaitEvent(la, p->fork_ev, 0);
@@ -565,7 +567,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
   p->engine = (d->flags & ACE_FLAG_ENGINE) != 0;
   p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM);
-  p->overlap = p->graphs && !p->engine && (d->flags & ACE_FLAG_OVERLAP);
+  p->overlap = p->graphs && !p->engine && !(d->flags & ACE_FLAG_NO_OVERLAP);
   if (p->overlap && p->lanes < 2) p->lanes = 2;
   const size_t slot = (size_t)p->ng * p->csize;
   const int tt = p->tile * p->tile;

@@ -5,8 +5,8 @@
 // Blocks of NB = 32 columns. For panel p (rows/cols [p0, p0 + nb)):
 //   diag    one CTA: A_pp -> L_pp (right-looking Cholesky in shared memory,
 //           status word on a non-finite or non-positive pivot), D_p = L_pp^{-1}
-//           (column-by-column inverse of a triangular matrix); L_pp is stored
-//           in A, D_p in the diagonal block of X.
+//           (recursive-doubling inverse of a triangular matrix); L_pp is
+//           stored in A, D_p in the diagonal block of X.
 //   panel   L_ip = A_ip D_p^*  for every row i below the panel (one CTA per 16
 //           rows, in place: a CTA reads and writes only its own rows).
 //   update  A_ik -= sum_l L_il conj(L_kl) over the panel columns l, for the
@@ -48,73 +48,86 @@ __global__ void neg_copy_kernel(const double2* __restrict__ M, long long count, 
   if (i < count) A[i] = make_double2(-M[i].x, -M[i].y);
 }
 
-// Factor and invert the diagonal block of panel p (nb <= NB).
+// Factor and invert the diagonal block of panel p (nb <= NB); 1024 threads,
+// thread e owns element (e / NB, e % NB). The block is padded to NB with the
+// identity, so every loop runs NB uniform steps.
+// Cholesky on unscaled columns: step j subtracts a_ij conj(a_kj) / d_j from the
+// trailing lower triangle (d_j = a_jj at step j), so a step needs one barrier
+// and one FP64 reciprocal per warp; afterwards L_jj = sqrt(d_j) and
+// L_ij = a_ij / sqrt(d_j) in one parallel pass.
+// Inverse by recursive doubling: for a lower-triangular [[A, 0], [B, C]],
+// the inverse is [[A^-1, 0], [-C^-1 (B A^-1), C^-1]]; five levels (block edge
+// 2, 4, ..., 32) of small products replace NB dependent column steps. The
+// intermediate B A^-1 is kept, transposed, in the unused upper triangle of X.
 __global__ void __launch_bounds__(1024)
 diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int nb, int* status) {
   __shared__ double2 a[NB][NB + 1];
-  __shared__ double2 col[NB];
-  __shared__ int fail;
-  __shared__ double rcp;   // one FP64 reciprocal per step, shared (FP64 division is costly here)
-  const int tid = threadIdx.x;
+  __shared__ double2 x[NB][NB + 1];
+  __shared__ double dl[NB], dil[NB];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int ei = tid / NB, ek = tid % NB;
   if (status[0] != 0) return;
-  for (int e = tid; e < NB * NB; e += blockDim.x) {
-    const int i = e / NB, k = e % NB;
-    a[i][k] = (i < nb && k <= i) ? A[(long long)(p0 + i) * n + p0 + k] : make_double2(0.0, 0.0);
+  {
+    double2 v = make_double2(ei == ek ? 1.0 : 0.0, 0.0);
+    if (ei < nb && ek <= ei) v = A[(long long)(p0 + ei) * n + p0 + ek];
+    a[ei][ek] = v;
+    x[ei][ek] = make_double2(0.0, 0.0);
   }
-  if (tid == 0) fail = 0;
   __syncthreads();
-  for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
-      const double d = a[j][j].x;
-      if (!isfinite(d)) {
-        fail = 1; status[0] = -3; status[1] = p0 + j + 1;
-      } else if (!(d > 0.0)) {
-        fail = 1; status[0] = -2; status[1] = p0 + j + 1;
-      } else {
-        const double l = sqrt(d);
-        a[j][j] = make_double2(l, 0.0);
-        rcp = 1.0 / l;
+  for (int j = 0; j < NB; ++j) {
+    const double d = a[j][j].x;
+    if (!isfinite(d) || !(d > 0.0)) {   // same value in every thread: uniform exit
+      if (tid == 0) {
+        status[0] = isfinite(d) ? -2 : -3;
+        status[1] = p0 + j + 1;
       }
+      return;
     }
-    __syncthreads();
-    if (fail) return;
-    const double inv = rcp;
-    if (tid > j && tid < nb) {
-      a[tid][j].x *= inv;
-      a[tid][j].y *= inv;
-      col[tid] = a[tid][j];
-    }
-    __syncthreads();
-    for (int e = tid; e < NB * NB; e += blockDim.x) {
-      const int i = e / NB, k = e % NB;
-      if (i > j && k > j && k <= i && i < nb) a[i][k] = zfmac(a[i][k], make_double2(-col[i].x, -col[i].y), col[k]);
+    double r = 0.0;
+    if (lane == 0) r = 1.0 / d;
+    r = __shfl_sync(0xffffffffu, r, 0);
+    if (ei > j && ek > j && ek <= ei) {
+      const double2 u = a[ei][j];
+      const double2 w = a[ek][j];
+      a[ei][ek] = zfmac(a[ei][ek], make_double2(-u.x * r, -u.y * r), w);
     }
     __syncthreads();
   }
-  // L_pp back to A
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, k = e % nb;
-    if (k <= i) A[(long long)(p0 + i) * n + p0 + k] = a[i][k];
+  if (tid < NB) {
+    const double l = sqrt(a[tid][tid].x);
+    dl[tid] = l;
+    dil[tid] = 1.0 / l;
   }
   __syncthreads();
-  // in-place inverse, columns from the right
-  for (int j = nb - 1; j >= 0; --j) {
-    if (tid == 0) rcp = 1.0 / a[j][j].x;
-    if (tid > j && tid < nb) col[tid] = a[tid][j];
-    __syncthreads();
-    const double xjj = rcp;
-    if (tid > j && tid < nb) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int k = j + 1; k <= tid; ++k) s = zfma(s, a[tid][k], col[k]);
-      a[tid][j] = make_double2(-xjj * s.x, -xjj * s.y);
+  if (ek < ei) {
+    a[ei][ek].x *= dil[ek];
+    a[ei][ek].y *= dil[ek];
+  } else if (ek == ei) {
+    a[ei][ei] = make_double2(dl[ei], 0.0);
+    x[ei][ei] = make_double2(dil[ei], 0.0);
+  }
+  __syncthreads();
+  if (ei < nb && ek <= ei) A[(long long)(p0 + ei) * n + p0 + ek] = a[ei][ek];
+  for (int h = 1; h < NB; h *= 2) {     // blocks of edge 2h at rows/cols b .. b + 2h
+    const int cnt = (NB / (2 * h)) * h * h;
+    // T = B A^{-1}: T_rc = sum_{m >= c} a[b+h+r][b+m] x[b+m][b+c], stored at x[b+c][b+h+r]
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int blk = e / (h * h), r = (e / h) % h, c = e % h, b = blk * 2 * h;
+      double2 t = make_double2(0.0, 0.0);
+      for (int m = c; m < h; ++m) t = zfma(t, a[b + h + r][b + m], x[b + m][b + c]);
+      x[b + c][b + h + r] = t;
     }
-    if (tid == 0) a[j][j] = make_double2(xjj, 0.0);
+    __syncthreads();
+    // X_B = -C^{-1} T: X[b+h+r][b+c] = -sum_{m <= r} x[b+h+r][b+h+m] T_mc
+    for (int e = tid; e < cnt; e += blockDim.x) {
+      const int blk = e / (h * h), r = (e / h) % h, c = e % h, b = blk * 2 * h;
+      double2 t = make_double2(0.0, 0.0);
+      for (int m = 0; m <= r; ++m) t = zfma(t, x[b + h + r][b + h + m], x[b + c][b + h + m]);
+      x[b + h + r][b + c] = make_double2(-t.x, -t.y);
+    }
     __syncthreads();
   }
-  for (int e = tid; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, k = e % nb;
-    X[(long long)(p0 + i) * n + p0 + k] = (k <= i) ? a[i][k] : make_double2(0.0, 0.0);
-  }
+  if (ei < nb && ek < nb) X[(long long)(p0 + ei) * n + p0 + ek] = ek <= ei ? x[ei][ek] : make_double2(0.0, 0.0);
 }
 
 // L_ip = A_ip D_p^* for rows i in [r0, n): one CTA per TT rows, all nb columns.
@@ -173,29 +186,42 @@ update_kernel(double2* __restrict__ A, int n, int p0, int nb, int r0, const int*
 }
 
 // T(r, j) = sum_{k = j}^{q0 - 1} L(q0 + r, k) X(k, j), r < nb, j < q0 (X lower triangular).
+// Block (32, KS): x indexes j, y strides over k; the KS partial sums are added
+// in a fixed order, so the result does not depend on timing.
+constexpr int KS = 8;
 __global__ void __launch_bounds__(256)
 inv_row_kernel(const double2* __restrict__ A, const double2* __restrict__ X, double2* __restrict__ T,
                int n, int q0, int nb, const int* status) {
+  __shared__ double2 red[KS][32];
   if (status[0] != 0) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nb * q0) return;
-  const int r = idx / q0, j = idx % q0;
+  const int r = blockIdx.y, j = blockIdx.x * 32 + threadIdx.x, ty = threadIdx.y;
   double2 s = make_double2(0.0, 0.0);
-  for (int k = j; k < q0; ++k) s = zfma(s, A[(long long)(q0 + r) * n + k], X[(long long)k * n + j]);
-  T[(long long)r * q0 + j] = s;
+  if (j < q0)
+    for (int k = j + ty; k < q0; k += KS) s = zfma(s, A[(long long)(q0 + r) * n + k], X[(long long)k * n + j]);
+  red[ty][threadIdx.x] = s;
+  __syncthreads();
+  if (ty == 0 && j < q0) {
+    for (int y = 1; y < KS; ++y) s = make_double2(s.x + red[y][threadIdx.x].x, s.y + red[y][threadIdx.x].y);
+    T[(long long)r * q0 + j] = s;
+  }
 }
 
-// X(q0 + r, j) = -sum_c D_q(r, c) T(c, j), r < nb, j < q0.
+// X(q0 + r, j) = -sum_c D_q(r, c) T(c, j), r < nb, j < q0 (same block shape, y strides over c).
 __global__ void __launch_bounds__(256)
 inv_apply_kernel(const double2* __restrict__ T, double2* __restrict__ X, int n, int q0, int nb,
                  const int* status) {
+  __shared__ double2 red[KS][32];
   if (status[0] != 0) return;
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nb * q0) return;
-  const int r = idx / q0, j = idx % q0;
+  const int r = blockIdx.y, j = blockIdx.x * 32 + threadIdx.x, ty = threadIdx.y;
   double2 s = make_double2(0.0, 0.0);
-  for (int c = 0; c <= r; ++c) s = zfma(s, X[(long long)(q0 + r) * n + q0 + c], T[(long long)c * q0 + j]);
-  X[(long long)(q0 + r) * n + j] = make_double2(-s.x, -s.y);
+  if (j < q0)
+    for (int c = ty; c <= r; c += KS) s = zfma(s, X[(long long)(q0 + r) * n + q0 + c], T[(long long)c * q0 + j]);
+  red[ty][threadIdx.x] = s;
+  __syncthreads();
+  if (ty == 0 && j < q0) {
+    for (int y = 1; y < KS; ++y) s = make_double2(s.x + red[y][threadIdx.x].x, s.y + red[y][threadIdx.x].y);
+    X[(long long)(q0 + r) * n + j] = make_double2(-s.x, -s.y);
+  }
 }
 
 __global__ void linvh_kernel(const double2* __restrict__ X, int n, double* __restrict__ LinvH,
@@ -238,9 +264,9 @@ int launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int
   }
   for (int q0 = NB; q0 < n; q0 += NB) {
     const int nb = (q0 + NB <= n) ? NB : n - q0;
-    const int cnt = nb * q0;
-    inv_row_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(A, X, T, n, q0, nb, status);
-    inv_apply_kernel<<<(cnt + 255) / 256, 256, 0, st>>>(T, X, n, q0, nb, status);
+    const dim3 grid((q0 + 31) / 32, nb), block(32, KS);
+    inv_row_kernel<<<grid, block, 0, st>>>(A, X, T, n, q0, nb, status);
+    inv_apply_kernel<<<grid, block, 0, st>>>(T, X, n, q0, nb, status);
     launches += 2;
   }
   linvh_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(X, n, LinvH, status);
