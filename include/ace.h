@@ -150,6 +150,35 @@ ace_status ace_exchange_apply(ace_plan* plan, const void* Phi, const void* Psi, 
 ace_status ace_build(ace_plan* plan, const void* Phi, void* W_out, void* Xi_out,
                      double* M_out, double* Ex_out, void* ws, size_t ws_bytes, void* stream);
 
+/* Batched ACE construction: ace_build for n_sys independent systems (each with
+ * its own plan: grid edge, N, dtype and kernel may all differ) issued as ONE
+ * captured CUDA graph. The systems are spread over `chains` concurrent
+ * streams (0 = 3), longest first, each to the chain with the least estimated
+ * work (N(N+1)/2 N_g); inside a chain they run in turn, each with its own
+ * two-stream pair schedule. The graph is cached process-wide under all the
+ * pointers (plans, Phi[i], Xi[i], Ex, ws) and replayed on later calls.
+ * plans: n_sys distinct plans on the current device. Phi[i], Xi[i]: N_i
+ * vectors of plan i's layout (device, 16-byte aligned). Ex: NULL or device
+ * double[n_sys], Ex[i] = 1/2 Re tr M_i. W is kept in the workspace only.
+ * ws: ace_workspace_size_batched(plans, n_sys) bytes, 256-byte aligned.
+ * Device-side failures land in each plan's status word (ace_status_sync). */
+size_t ace_workspace_size_batched(ace_plan* const* plans, int n_sys);
+ace_status ace_build_batched(ace_plan* const* plans, const void* const* Phi, void* const* Xi,
+                             double* Ex, int n_sys, int chains, void* ws, size_t ws_bytes,
+                             void* stream);
+
+/* Autotuner (schedule choice only; results are the same for every choice up
+ * to FP32 rounding order): times ace_build of the descriptor's problem on the
+ * current device for each candidate schedule -- tile edge 8, 6 or 4 orbitals,
+ * pair-batch scratch of about 36, 72 or 144 MiB, the two-stream overlapped
+ * pair schedule or two lanes without overlap -- on seeded pseudo-random
+ * orbitals, `reps` timed builds each (0 = 3) after one untimed build, and
+ * writes the fastest into *best (a copy of *d with tile, max_pairs, lanes and
+ * flags set) and its milliseconds per build into *ms_out (nullable).
+ * Allocates its own device buffers (about 2 N N_g vectors plus the largest
+ * workspace) and synchronises; call it outside timed or captured regions. */
+ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_out);
+
 /* Y = V_ACE Psi = -Xi (dV Xi^* Psi) (Eq. ACE). Xi: N vectors from ace_build,
  * Psi and Y: n_b vectors; Y must not alias Xi or Psi. No Poisson solves. */
 ace_status ace_apply(ace_plan* plan, const void* Xi, const void* Psi, int n_b, void* Y,

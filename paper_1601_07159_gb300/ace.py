@@ -80,6 +80,14 @@ _lib.ace_profile_begin.argtypes = [_vp, ctypes.c_int]
 _lib.ace_profile_begin.restype = ctypes.c_int
 _lib.ace_profile_end.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.ace_profile_end.restype = ctypes.c_int
+_lib.ace_workspace_size_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+_lib.ace_workspace_size_batched.restype = ctypes.c_size_t
+_lib.ace_build_batched.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp,
+                                   ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]
+_lib.ace_build_batched.restype = ctypes.c_int
+_lib.ace_autotune.argtypes = [ctypes.POINTER(Desc), ctypes.c_int, ctypes.POINTER(Desc),
+                              ctypes.POINTER(ctypes.c_double)]
+_lib.ace_autotune.restype = ctypes.c_int
 
 
 class AceError(RuntimeError):
@@ -133,6 +141,7 @@ class Plan:
         d.tile = tile
         d.lanes = lanes
         d.flags = (0 if graphs else 1) | (2 if engine else 0) | (0 if pdl else 4) | (0 if tensor_cores else 8) | (0 if overlap else 16)
+        self.schedule = {"tile": tile, "max_pairs": max_pairs, "lanes": lanes, "overlap": overlap}
         h = _vp()
         _check(_lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -262,6 +271,98 @@ class Plan:
         info = ctypes.c_int(0)
         code = _lib.ace_status_sync(self._h, _stream(), ctypes.byref(info))
         return code, info.value
+
+
+def _desc(n, L, n_occ, dtype, kernel, omega, g0, alpha) -> Desc:
+    if isinstance(L, (int, float)):
+        L = (float(L),) * 3
+    d = Desc()
+    d.n = n
+    d.L[0], d.L[1], d.L[2] = L
+    d.n_occ = n_occ
+    d.dtype = DTYPES[dtype]
+    d.kernel = KERNELS[kernel]
+    d.omega = omega
+    d.g0_value = math.nan if g0 is None else g0
+    d.alpha = alpha
+    return d
+
+
+def autotune(n: int, L, n_occ: int, dtype: str = "c64", kernel: str = "bare", omega: float = 0.0,
+             g0: float | None = None, alpha: float = 1.0, reps: int = 3) -> dict:
+    """ace_autotune: the fastest schedule for this problem shape on the current
+    device, as Plan keyword arguments plus the measured ms per build."""
+    d = _desc(n, L, n_occ, dtype, kernel, omega, g0, alpha)
+    best = Desc()
+    ms = ctypes.c_double(0.0)
+    _check(_lib.ace_autotune(ctypes.byref(d), reps, ctypes.byref(best), ctypes.byref(ms)))
+    return {"tile": best.tile, "max_pairs": best.max_pairs, "lanes": best.lanes,
+            "overlap": not (best.flags & 16), "ms": ms.value}
+
+
+class TuningTable:
+    """Autotuner results keyed by problem shape (n, N, dtype, kernel), kept in
+    a JSON file so that a shape is timed once per machine."""
+
+    def __init__(self, path: str | None = None):
+        self.path = path
+        self.table = {}
+        if path and os.path.exists(path):
+            import json
+            with open(path) as f:
+                self.table = json.load(f)
+
+    @staticmethod
+    def key(n, n_occ, dtype, kernel) -> str:
+        return f"{n}|{n_occ}|{dtype}|{kernel}"
+
+    def schedule(self, n, L, n_occ, dtype="c64", kernel="bare", omega=0.0, g0=None, alpha=1.0) -> dict:
+        k = self.key(n, n_occ, dtype, kernel)
+        if k not in self.table:
+            self.table[k] = autotune(n, L, n_occ, dtype, kernel, omega, g0, alpha)
+            if self.path:
+                import json
+                os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
+                with open(self.path, "w") as f:
+                    json.dump(self.table, f, indent=1, sort_keys=True)
+        return self.table[k]
+
+    def plan(self, n, L, n_occ, dtype="c64", kernel="bare", omega=0.0, g0=None, alpha=1.0) -> "Plan":
+        t = self.schedule(n, L, n_occ, dtype, kernel, omega, g0, alpha)
+        return Plan(n, L, n_occ, dtype=dtype, kernel=kernel, omega=omega, g0=g0, alpha=alpha,
+                    tile=t["tile"], max_pairs=t["max_pairs"], lanes=t["lanes"], overlap=t["overlap"])
+
+
+class Batch:
+    """ace_build_batched over a fixed list of plans (one per system), with the
+    batch workspace allocated once so that the captured graph is replayed."""
+
+    def __init__(self, plans, chains: int = 0):
+        self.plans = list(plans)
+        self.chains = chains
+        n = len(self.plans)
+        self._hp = (_vp * n)(*[p._h for p in self.plans])
+        nbytes = int(_lib.ace_workspace_size_batched(self._hp, n))
+        self.ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=self.plans[0].device) if n else None
+        self.ex = torch.empty(n, dtype=torch.float64, device=self.plans[0].device) if n else None
+
+    def build(self, phis, xis=None):
+        """Xi_i and E_x,i = 1/2 Re tr M_i for every system (Alg. 2 steps 2-3)."""
+        n = len(self.plans)
+        if len(phis) != n:
+            raise ValueError("one phi per plan")
+        if xis is None:
+            xis = [p.empty(p.n_occ) for p in self.plans]
+        for p, phi, xi in zip(self.plans, phis, xis):
+            p._vec(phi, "phi")
+            p._vec(xi, "xi")
+            if phi.shape[0] != p.n_occ or xi.shape[0] != p.n_occ:
+                raise ValueError("phi and xi must hold n_occ vectors")
+        hphi = (_vp * n)(*[t.data_ptr() for t in phis])
+        hxi = (_vp * n)(*[t.data_ptr() for t in xis])
+        _check(_lib.ace_build_batched(self._hp, hphi, hxi, _ptr(self.ex), n, self.chains, _ptr(self.ws),
+                                      self.ws.numel() if self.ws is not None else 0, _stream()))
+        return xis, self.ex
 
 
 class ExchangeEnergy(torch.autograd.Function):

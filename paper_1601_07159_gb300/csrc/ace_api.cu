@@ -4,7 +4,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <deque>
+#include <mutex>
 #include <limits>
 #include <string>
 #include <vector>
@@ -509,6 +511,69 @@ void drop_graphs(ace_plan* p) {
   p->graph_cache.clear();
 }
 
+// The W build's pair section on `cs`: W = 0, then W = V_X[Phi] Phi over the
+// unique pairs (Eq. W). Returns the kernel count, or -1.
+long long issue_build_pairs(ace_plan* p, const void* Phi, void* W, const WsLayout& Wl, cudaStream_t cs) {
+  PairLaunch L = base_launch(p);
+  L.X = Phi;
+  L.Y = Phi;
+  L.OutX = W;
+  L.OutY = W;
+  L.mode = 0;
+  cudaMemsetAsync(W, 0, (size_t)p->d.n_occ * p->ng * p->vsize, cs);
+  return issue_pairs(p, L, p->build, Wl.S, nullptr, Wl.ctr, cs);
+}
+
+// The build's dense section on `cs`: M = dV Phi^* W, Hermitian part (Eq.
+// ACEconstruct2); -M = L L^* and L^{-*} in FP64; Xi = W L^{-*} (Eq. Wtilde).
+long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* Xi, const WsLayout& Wl,
+                            cudaStream_t cs) {
+  const int N = p->d.n_occ;
+  const int splits = gram_parts(p, N, N);
+  if (p->tc) launch_gram_tc(Phi, N, W, N, p->ng, p->ng, Wl.part, splits, p->status, cs);
+  else launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
+  launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
+  if (p->tc) launch_diag_exact(Phi, W, N, p->ng, p->ng, p->dv, Wl.part, p->Mc, cs);
+  const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
+  if (p->tc) launch_outer_tc(W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi, p->status, cs);
+  else launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi, cs);
+  return 2 + (p->tc ? 2 : 0) + kc + 1;
+}
+
+// One captured graph per batch of systems (ace_build_batched), shared by all
+// plans of the process and keyed by every pointer the graph bakes in.
+struct BatchGraph {
+  std::vector<uintptr_t> key;
+  std::vector<ace_plan*> plans;
+  std::vector<long long> kernels;   // per system
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long last_use = 0;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_graphs;
+unsigned long long g_batch_clock = 0;
+constexpr int kMaxBatchGraphs = 4;
+
+void drop_batch_graphs_of(const ace_plan* p) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  for (size_t i = 0; i < g_batch_graphs.size();) {
+    auto& g = g_batch_graphs[i];
+    if (std::find(g.plans.begin(), g.plans.end(), p) != g.plans.end()) {
+      cudaGraphExecDestroy(g.exec);
+      g_batch_graphs.erase(g_batch_graphs.begin() + i);
+    } else {
+      ++i;
+    }
+  }
+}
+
+// Estimated cost of one system's build (pair solves x grid points), used to
+// balance the chains of a batch (longest-processing-time-first).
+double build_cost(const ace_plan* p) {
+  const double N = p->d.n_occ;
+  return 0.5 * N * (N + 1.0) * (double)p->ng + N * N * (double)p->ng * 0.05;
+}
+
 }  // namespace
 
 ace_status ace_internal_plan_info(const ace_plan* p, int* device, int* n_occ, long long* ng,
@@ -662,6 +727,7 @@ ace_status ace_plan_destroy(ace_plan* p) {
   if (!p) return ACE_OK;
   cudaDeviceSynchronize();
   drop_graphs(p);
+  drop_batch_graphs_of(p);
   for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
   for (int i = 0; i < kMaxLanes; ++i) {
     if (p->lane[i]) cudaStreamDestroy(p->lane[i]);
@@ -739,38 +805,244 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   const int N = p->d.n_occ;
   const WsLayout Wl = layout(p, ACE_OP_BUILD, 0, (char*)ws);
   void* W = W_out ? W_out : (void*)Wl.Wtmp;
-  const size_t wbytes = (size_t)N * p->ng * p->vsize;
   // W = V_X[Phi] Phi over the unique pairs (Eq. W)
-  PairLaunch L = base_launch(p);
-  L.X = Phi;
-  L.Y = Phi;
-  L.OutX = W;
-  L.OutY = W;
-  L.mode = 0;
   const uintptr_t kp[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, 0, 0, 2, 0, 0};
   s = run_graph(p, kp, st, true, [&](cudaStream_t cs) -> long long {
-    cudaMemsetAsync(W, 0, wbytes, cs);
-    return issue_pairs(p, L, p->build, Wl.S, nullptr, Wl.ctr, cs);
+    return issue_build_pairs(p, Phi, W, Wl, cs);
   });
   if (s != ACE_OK) return s;
-  // M = dV Phi^* W, Hermitian part (Eq. ACEconstruct2); E_x = 1/2 Re tr M;
-  // -M = L L^* and L^{-*} in FP64; Xi = W L^{-*} (Eq. Wtilde)
+  // M, its Cholesky factor, L^{-*} and Xi = W L^{-*}
   const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, 4, 0, 0, 0};
   s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
-    const int splits = gram_parts(p, N, N);
-    if (p->tc) launch_gram_tc(Phi, N, W, N, p->ng, p->ng, Wl.part, splits, p->status, cs);
-    else launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
-    launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
-    if (p->tc) launch_diag_exact(Phi, W, N, p->ng, p->ng, p->dv, Wl.part, p->Mc, cs);
-    const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
-    if (p->tc) launch_outer_tc(W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, p->status, cs);
-    else launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi_out, cs);
-    return 2 + (p->tc ? 2 : 0) + kc + 1;
+    return issue_build_dense(p, Phi, W, Xi_out, Wl, cs);
   });
   if (s != ACE_OK) return s;
   // caller-owned small outputs, outside the graph (their pointers vary per call)
   p->launches += launch_m_outputs(p->Mc, N, p->real, M_out, Ex_out, st);
   return cuda_check("ace_build");
+}
+
+size_t ace_workspace_size_batched(ace_plan* const* plans, int n_sys) {
+  if (!plans || n_sys < 0) return 0;
+  size_t total = 0;
+  for (int i = 0; i < n_sys; ++i) {
+    if (!plans[i]) return 0;
+    total += align256(layout(plans[i], ACE_OP_BUILD, 0, nullptr).total);
+  }
+  return total;
+}
+
+ace_status ace_build_batched(ace_plan* const* plans, const void* const* Phi, void* const* Xi, double* Ex,
+                             int n_sys, int chains, void* ws, size_t ws_bytes, void* stream) {
+  if (n_sys < 0 || chains < 0) return fail(ACE_ERR_ARG, "n_sys and chains must be >= 0");
+  if (n_sys == 0) return ACE_OK;
+  if (!plans || !Phi || !Xi) return fail(ACE_ERR_ARG, "plans, Phi and Xi are required");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(ACE_ERR_CUDA, "no current device");
+  for (int i = 0; i < n_sys; ++i) {
+    ace_plan* p = plans[i];
+    if (!p) return fail(ACE_ERR_ARG, "plan " + std::to_string(i) + " is NULL");
+    if (p->device != dev) return fail(ACE_ERR_ARG, "plan " + std::to_string(i) + " is on another device");
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == p) return fail(ACE_ERR_ARG, "a plan appears twice in the batch");
+    if (!Phi[i] || !Xi[i] || !aligned16(Phi[i]) || !aligned16(Xi[i]))
+      return fail(ACE_ERR_ARG, "system " + std::to_string(i) + ": Phi/Xi NULL or not 16-byte aligned");
+    if (Phi[i] == Xi[i]) return fail(ACE_ERR_ARG, "system " + std::to_string(i) + ": Xi aliases Phi");
+  }
+  const size_t need = ace_workspace_size_batched(plans, n_sys);
+  if (ws_bytes < need) return fail(ACE_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need) + " bytes");
+  if (!ws || ((uintptr_t)ws & 255u)) return fail(ACE_ERR_ARG, "workspace NULL or not 256-byte aligned");
+  const int K = std::max(1, std::min(chains ? chains : 3, n_sys));
+  cudaStream_t st = (cudaStream_t)stream;
+
+  std::vector<uintptr_t> key = {(uintptr_t)n_sys, (uintptr_t)K, (uintptr_t)ws, (uintptr_t)Ex, (uintptr_t)dev};
+  for (int i = 0; i < n_sys; ++i) {
+    key.push_back((uintptr_t)plans[i]);
+    key.push_back((uintptr_t)Phi[i]);
+    key.push_back((uintptr_t)Xi[i]);
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  BatchGraph* hit = nullptr;
+  for (auto& g : g_batch_graphs)
+    if (g.key == key) hit = &g;
+  if (!hit) {
+    if ((int)g_batch_graphs.size() >= kMaxBatchGraphs) {
+      size_t victim = 0;
+      for (size_t i = 1; i < g_batch_graphs.size(); ++i)
+        if (g_batch_graphs[i].last_use < g_batch_graphs[victim].last_use) victim = i;
+      cudaGraphExecDestroy(g_batch_graphs[victim].exec);
+      g_batch_graphs.erase(g_batch_graphs.begin() + victim);
+    }
+    // systems by decreasing cost, each to the chain with the least work so far
+    std::vector<int> order(n_sys);
+    for (int i = 0; i < n_sys; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return build_cost(plans[a]) > build_cost(plans[b]); });
+    std::vector<std::vector<int>> chain(K);
+    std::vector<double> load(K, 0.0);
+    for (int i : order) {
+      const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      chain[c].push_back(i);
+      load[c] += build_cost(plans[i]);
+    }
+    std::vector<size_t> off(n_sys + 1, 0);
+    for (int i = 0; i < n_sys; ++i) off[i + 1] = off[i] + align256(layout(plans[i], ACE_OP_BUILD, 0, nullptr).total);
+
+    BatchGraph g;
+    g.key = key;
+    g.plans.assign(plans, plans + n_sys);
+    g.kernels.assign(n_sys, 0);
+    cudaStream_t cs = nullptr;
+    std::vector<cudaStream_t> cst(K, nullptr);
+    std::vector<cudaEvent_t> jev(K, nullptr);
+    cudaEvent_t fev = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    for (int c = 0; c < K && e == cudaSuccess; ++c) e = cudaStreamCreateWithFlags(&cst[c], cudaStreamNonBlocking);
+    for (int c = 0; c < K && e == cudaSuccess; ++c) e = cudaEventCreateWithFlags(&jev[c], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fev, cudaEventDisableTiming);
+    bool ok = e == cudaSuccess;
+    cudaGraph_t graph = nullptr;
+    if (ok) ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      cudaEventRecord(fev, cs);
+      for (int c = 0; c < K; ++c) {
+        cudaStreamWaitEvent(cst[c], fev, 0);
+        for (int i : chain[c]) {
+          ace_plan* p = plans[i];
+          const WsLayout Wl = layout(p, ACE_OP_BUILD, 0, (char*)ws + off[i]);
+          std::vector<cudaEvent_t> prof_ev;   // no per-pass events inside the batch graph
+          prof_ev.swap(p->ev);
+          const long long k1 = issue_build_pairs(p, Phi[i], Wl.Wtmp, Wl, cst[c]);
+          prof_ev.swap(p->ev);
+          const long long k2 = issue_build_dense(p, Phi[i], Wl.Wtmp, Xi[i], Wl, cst[c]);
+          const long long k3 = Ex ? launch_m_outputs(p->Mc, p->d.n_occ, p->real, nullptr, Ex + i, cst[c]) : 0;
+          if (k1 < 0) ok = false;
+          g.kernels[i] = k1 + k2 + k3;
+        }
+        cudaEventRecord(jev[c], cst[c]);
+        cudaStreamWaitEvent(cs, jev[c], 0);
+      }
+      const cudaError_t e1 = cudaStreamEndCapture(cs, &graph);
+      if (e1 != cudaSuccess) ok = false;
+    }
+    if (ok && graph) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    const cudaError_t ce = cudaGetLastError();
+    if (fev) cudaEventDestroy(fev);
+    for (int c = 0; c < K; ++c) {
+      if (jev[c]) cudaEventDestroy(jev[c]);
+      if (cst[c]) cudaStreamDestroy(cst[c]);
+    }
+    if (cs) cudaStreamDestroy(cs);
+    if (!ok) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      return fail(ce != cudaSuccess ? ACE_ERR_CUDA : ACE_ERR_UNSUPPORTED,
+                  std::string("batched graph capture failed: ") +
+                      (ce != cudaSuccess ? cudaGetErrorString(ce) : "an edge is not built"));
+    }
+    g_batch_graphs.push_back(std::move(g));
+    hit = &g_batch_graphs.back();
+  }
+  hit->last_use = ++g_batch_clock;
+  if (cudaGraphLaunch(hit->exec, st) != cudaSuccess) return cuda_check("batched graph launch");
+  for (int i = 0; i < n_sys; ++i) plans[i]->launches += hit->kernels[i];
+  return cuda_check("ace_build_batched");
+}
+
+ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_out) {
+  if (!d || !best) return fail(ACE_ERR_ARG, "desc and best are required");
+  if (reps <= 0) reps = 3;
+  // probe the descriptor once (validation, sizes)
+  ace_plan* probe = nullptr;
+  ace_status s = ace_plan_create(d, &probe);
+  if (s != ACE_OK) return s;
+  const int N = probe->d.n_occ;
+  const long long ng = probe->ng;
+  const size_t vsize = probe->vsize, slot = (size_t)ng * probe->csize;
+  const bool f64 = probe->f64;
+  ace_plan_destroy(probe);
+
+  // candidates: tile edge x batch scratch budget x pair schedule
+  std::vector<ace_desc> cand;
+  const int tiles[3] = {8, 6, 4};
+  const long long budgets[3] = {72ll << 20, 36ll << 20, 144ll << 20};
+  for (int tile : tiles) {
+    if (tile > N && tile != tiles[0]) continue;   // tiles wider than N all act as one tile
+    const int tt = tile * tile;
+    for (long long b : budgets) {
+      long long mp = b / (long long)slot;
+      if (mp > (long long)kMaxTiles * tt) mp = (long long)kMaxTiles * tt;
+      if (mp < tt) mp = tt;
+      for (int ov = 1; ov >= 0; --ov) {
+        ace_desc c = *d;
+        c.tile = tile;
+        c.max_pairs = (int)mp;
+        c.lanes = 2;
+        c.flags = (d->flags & ~(ACE_FLAG_NO_OVERLAP | ACE_FLAG_NO_GRAPH | ACE_FLAG_ENGINE)) |
+                  (ov ? 0 : ACE_FLAG_NO_OVERLAP);
+        bool dup = false;
+        for (const auto& o : cand)
+          dup = dup || (o.tile == c.tile && o.max_pairs == c.max_pairs && o.flags == c.flags);
+        if (!dup) cand.push_back(c);
+      }
+    }
+  }
+  void *Phi = nullptr, *Xi = nullptr, *ws = nullptr;
+  size_t ws_cap = 0;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  const size_t vbytes = (size_t)N * ng * vsize;
+  cudaError_t e = cudaMalloc(&Phi, vbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&Xi, vbytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) launch_fill_random(Phi, (long long)(vbytes / (f64 ? 8 : 4)), f64, 1601071590ull, st);
+  double best_ms = -1.0;
+  s = e == cudaSuccess ? ACE_OK : fail(ACE_ERR_CUDA, std::string("autotune setup: ") + cudaGetErrorString(e));
+  for (size_t i = 0; i < cand.size() && s == ACE_OK; ++i) {
+    ace_plan* p = nullptr;
+    if (ace_plan_create(&cand[i], &p) != ACE_OK) continue;   // e.g. out of memory for a large budget
+    const size_t need = layout(p, ACE_OP_BUILD, 0, nullptr).total;
+    if (need > ws_cap) {
+      cudaFree(ws);
+      ws = nullptr;
+      ws_cap = 0;
+      if (cudaMalloc(&ws, need) != cudaSuccess) {
+        cudaGetLastError();
+        ace_plan_destroy(p);
+        continue;
+      }
+      ws_cap = need;
+    }
+    s = ace_build(p, Phi, nullptr, Xi, nullptr, nullptr, ws, ws_cap, st);   // capture + warm-up
+    if (s == ACE_OK) s = ace_status_sync(p, st, nullptr);
+    if (s == ACE_OK) {
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && s == ACE_OK; ++r) s = ace_build(p, Phi, nullptr, Xi, nullptr, nullptr, ws, ws_cap, st);
+      cudaEventRecord(e1, st);
+      if (s == ACE_OK) s = ace_status_sync(p, st, nullptr);
+      float ms = 0.f;
+      if (s == ACE_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess) {
+        const double per = (double)ms / reps;
+        if (best_ms < 0 || per < best_ms) {
+          best_ms = per;
+          *best = cand[i];
+        }
+      }
+    }
+    ace_plan_destroy(p);
+  }
+  cudaFree(ws);
+  cudaFree(Phi);
+  cudaFree(Xi);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (s != ACE_OK) return s;
+  if (best_ms < 0) return fail(ACE_ERR_CUDA, "autotune: no candidate could be timed");
+  if (ms_out) *ms_out = best_ms;
+  return ACE_OK;
 }
 
 ace_status ace_apply(ace_plan* p, const void* Xi, const void* Psi, int nb, void* Y, void* ws,

@@ -122,5 +122,7 @@ void prepare_cholesky(int n);
 void launch_scale(bool f64, bool real, void* X, long long count, double s, cudaStream_t st);
 void launch_energy_reduce(const double* part, int count, double factor, double* out, cudaStream_t st);
 void launch_zero(void* p, size_t bytes, cudaStream_t st);
+// count values (reals) uniform in [-1, 1) from a hash of (seed, index).
+void launch_fill_random(void* x, long long count, bool f64, unsigned long long seed, cudaStream_t st);
 
 }  // namespace ace

@@ -291,4 +291,29 @@ void launch_energy_reduce(const double* part, int count, double factor, double* 
 
 void launch_zero(void* p, size_t bytes, cudaStream_t st) { cudaMemsetAsync(p, 0, bytes, st); }
 
+namespace {
+// Uniform values in [-1, 1) from a splitmix64 hash of (seed, index): timing
+// inputs for the autotuner (any values with -M positive definite will do).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+template <typename T>
+__global__ void fill_random_kernel(T* x, long long count, unsigned long long seed) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long h = splitmix64(seed ^ splitmix64((unsigned long long)i));
+    x[i] = (T)((double)(h >> 11) * (2.0 / 9007199254740992.0) - 1.0);
+  }
+}
+}  // namespace
+
+void launch_fill_random(void* x, long long count, bool f64, unsigned long long seed, cudaStream_t st) {
+  const long long blocks = (count + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 152 * 16 ? (blocks > 0 ? blocks : 1) : 152 * 16);
+  if (f64) fill_random_kernel<double><<<grid, 256, 0, st>>>(static_cast<double*>(x), count, seed);
+  else fill_random_kernel<float><<<grid, 256, 0, st>>>(static_cast<float*>(x), count, seed);
+}
+
 }  // namespace ace

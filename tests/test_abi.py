@@ -71,3 +71,23 @@ def test_validation_without_gpu(lib):
     assert lib.ace_supported_edge(48, 2) == 1 and lib.ace_supported_edge(64, 2) == 1
     assert lib.ace_supported_edge(7, 2) == 0 and lib.ace_supported_edge(64, 1) == 0
     assert lib.ace_workspace_size(None, 0, 4) == 0
+
+
+def test_batched_and_autotune_validation_without_gpu(lib):
+    """The batched build and the autotuner reject bad arguments on the host,
+    before any device call; an empty batch is a no-op."""
+    from paper_1601_07159_gb300.ace import ACE_OK, ACE_ERR_ARG
+    vp = ctypes.c_void_p
+    lib.ace_build_batched.restype = ctypes.c_int
+    lib.ace_build_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), vp,
+                                      ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, vp]
+    lib.ace_workspace_size_batched.restype = ctypes.c_size_t
+    lib.ace_workspace_size_batched.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    lib.ace_autotune.restype = ctypes.c_int
+    lib.ace_autotune.argtypes = [vp, ctypes.c_int, vp, vp]
+    assert lib.ace_build_batched(None, None, None, None, 0, 0, None, 0, None) == ACE_OK
+    assert lib.ace_build_batched(None, None, None, None, -1, 0, None, 0, None) == ACE_ERR_ARG
+    assert lib.ace_build_batched(None, None, None, None, 2, 0, None, 0, None) == ACE_ERR_ARG
+    assert lib.ace_build_batched(None, None, None, None, 1, -2, None, 0, None) == ACE_ERR_ARG
+    assert lib.ace_workspace_size_batched(None, 3) == 0
+    assert lib.ace_autotune(None, 3, None, None) == ACE_ERR_ARG
