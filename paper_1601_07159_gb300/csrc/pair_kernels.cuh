@@ -430,8 +430,12 @@ pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
   body_c<R, N, false, plane_items<R, N>()>(P, P.npairs, reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
+// Two blocks per SM: the 128-register cap keeps more of the tile's pair
+// potential loads in flight than the unconstrained allocation (104 registers),
+// which measured faster (as did this plain-load form against streaming the
+// potentials through shared memory with bulk copies).
 template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
   griddep_launch();
   griddep_wait();
