@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     p.add_argument("--max-pairs", type=int, default=0, help="pair solves per batch (0 = plan default)")
     p.add_argument("--tile", type=int, default=0, help="orbitals per tile side (0 = plan default)")
     p.add_argument("--lanes", type=int, default=0, help="concurrent batch streams (0 = plan default)")
@@ -208,6 +209,51 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- cuFFT comparison
+def cufft_baseline(phi_d, s, w_ours, reps=2):
+    """The same W build (unique pairs, both accumulations) written with cuFFT
+    (torch.fft) and torch elementwise kernels: a library comparison, timed
+    only. Row l of the pair triangle is one batch: rho = conj(phi_l) phi_r for
+    r >= l, v = IFFT(K FFT(rho)), W_r -= phi_l v, W_l -= sum_{r>l} phi_r conj(v)."""
+    import torch
+    n = s.n
+    m = np.fft.fftfreq(n, d=1.0 / n)
+    g = 2.0 * math.pi * m / s.L
+    g2 = g[:, None, None] ** 2 + g[None, :, None] ** 2 + g[None, None, :] ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        k = 4.0 * math.pi / g2
+        if s.kernel == "erfc":
+            k = k * (1.0 - np.exp(-g2 / (4.0 * s.omega ** 2)))
+    k[0, 0, 0] = math.pi / s.omega ** 2 if s.kernel == "erfc" else 0.0
+    kt = torch.from_numpy(k).to(torch.float32).cuda()
+    N = s.n_occ
+    w = torch.zeros_like(phi_d)
+
+    def build():
+        w.zero_()
+        for l in range(N):
+            rho = torch.conj(phi_d[l])[None] * phi_d[l:]
+            v = torch.fft.ifftn(torch.fft.fftn(rho, dim=(1, 2, 3)) * kt, dim=(1, 2, 3))
+            w[l:] -= phi_d[l][None] * v
+            if l + 1 < N:
+                w[l] -= torch.sum(phi_d[l + 1:] * torch.conj(v[1:]), dim=0)
+
+    build()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        build()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    diff = float(torch.linalg.vector_norm(w - w_ours) / torch.linalg.vector_norm(w_ours))
+    return {"value": unique_pairs(N) / (ms / 1e3), "unit": UNIT, "ms_per_w_build": ms,
+            "what": "unique-pair W build with torch.fft (cuFFT) + torch elementwise, one triangle row per batch",
+            "rel_diff_W_vs_ours": diff}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args):
     import torch
@@ -354,6 +400,12 @@ def run_ours(args):
         fp64 = {"fp64_ms_per_build": fp64_ms, "mixed_vs_fp64_build_speedup": fp64_ms / build_ms}
         del plan64, phi64, xi64
 
+    cufft = None
+    if not args.no_cufft:
+        w_ours = plan.build(phi_d)["W"]
+        cufft = cufft_baseline(phi_d, s, w_ours)
+        del w_ours
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -380,6 +432,7 @@ def run_ours(args):
                              "alg_model": "32 B/point/unique pair + Phi read + W write",
                              "ms_per_launch": pair_ms, "traffic": traffic, "passes": passes},
                 "cpu_baseline": cpu,
+                "cufft_baseline": cufft,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": Ke},
                 "gpu_launches": prof["launches"] + 0,
