@@ -48,7 +48,8 @@ constexpr int KC = 32;                     // real K terms per stage
 constexpr int SBO = (KC / 4) * 128;        // bytes between 8-row groups = 1024
 constexpr int OP_BYTES = TM * KC * 4;      // one operand tile (128 x 32 FP32) = 16 KB
 constexpr int STAGE_BYTES = 4 * OP_BYTES;  // A_hi, A_lo, B_hi, B_lo = 64 KB
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 1024 + 64;
+constexpr int NSTAGE = 3;                  // shared-memory stages (chunk c uses stage c % NSTAGE)
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 64;
 constexpr int kGroup = 4;                  // chunks per accumulator group
 constexpr unsigned kWaitLimit = 1u << 24;
 
@@ -132,20 +133,19 @@ __device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
 }
 
 struct TcState {
-  uint64_t* bar;        // [2] stage barriers
+  uint64_t* bar;        // [NSTAGE] stage barriers
   uint32_t* tmem_slot;  // TMEM base address written by tcgen05.alloc
-  unsigned char* stage; // 2 stages of 64 KB
+  unsigned char* stage; // NSTAGE stages of 64 KB
 };
 
 __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
   TcState s;
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
   s.stage = base;
-  s.bar = reinterpret_cast<uint64_t*>(base + 2 * STAGE_BYTES);
-  s.tmem_slot = reinterpret_cast<uint32_t*>(base + 2 * STAGE_BYTES + 16);
+  s.bar = reinterpret_cast<uint64_t*>(base + NSTAGE * STAGE_BYTES);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(base + NSTAGE * STAGE_BYTES + 32);
   if (threadIdx.x == 0) {
-    mbar_init(&s.bar[0], 1);
-    mbar_init(&s.bar[1], 1);
+    for (int i = 0; i < NSTAGE; ++i) mbar_init(&s.bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (threadIdx.x < 32) {   // warp 0 allocates the two accumulators
@@ -185,33 +185,41 @@ __device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char*
 // Main loop shared by both kernels: load(c, regs) fetches chunk c from global
 // memory, store(stage, regs) splits it into the stage. On return thread
 // (warp w, lane) holds acc[j] = D[row 32 (w % 4) + lane][col 32 (w / 4) + j].
+// Each thread waits (bounded) for the commit of the chunk that last used a
+// stage before storing into it, and drains a finished accumulator group when
+// that commit is the group's last; one block barrier per chunk hands the
+// stage to the issuing thread. A lost wait sets s_fail, which every thread
+// reads after that barrier, so all leave the loop together.
 template <typename Regs, typename Load, typename Store>
 __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks, float (&acc)[32],
                                             Load load, Store store) {
   const int tid = threadIdx.x, w = tid >> 5;
   const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + 32 * (w >> 2);
-  __shared__ int s_ok;
-  unsigned phase[2] = {0, 0};
-  int issued[2] = {0, 0};   // commit on the stage not yet seen (0 or 1)
-  int drain[2] = {0, 0};    // 1 + accumulator buffer to read once that commit is seen
+  __shared__ int s_fail;
+  // per-stage state in registers: bit s of `phase` / `issued` (commit on the
+  // stage not yet seen), two bits per stage of `drain` (1 + accumulator buffer
+  // to read once that commit is seen, 0 for none)
+  unsigned phase = 0, issued = 0, drain = 0;
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
 
-  // block-uniform bounded wait for the commit on stage s, then the pending drain
+  // this thread's bounded wait for the commit on stage s, then the pending drain
   auto settle = [&](int s) -> bool {
-    if (tid == 0) s_ok = mbar_wait(&S.bar[s], phase[s]) ? 1 : 0;
-    __syncthreads();
-    const bool good = s_ok != 0;
-    __syncthreads();   // s_ok is rewritten by the next wait
-    if (!good) return false;
-    phase[s] ^= 1;
-    issued[s] = 0;
-    if (drain[s]) {
+    if (!mbar_wait(&S.bar[s], (phase >> s) & 1u)) {
+      s_fail = 1;
+      return false;
+    }
+    phase ^= 1u << s;
+    issued &= ~(1u << s);
+    const unsigned d = (drain >> (2 * s)) & 3u;
+    if (d) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tmem_add32(tmem + lane_col + (uint32_t)(TN * (drain[s] - 1)), acc);
+      tmem_add32(tmem + lane_col + (uint32_t)(TN * (d - 1)), acc);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      drain[s] = 0;
+      drain &= ~(3u << (2 * s));
     }
     return true;
   };
@@ -219,34 +227,36 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
   Regs r0, r1, r2;   // chunks c, c + 1, c + 2 (rotated by register moves)
   if (nchunks > 0) load(0, r0);
   if (nchunks > 1) load(1, r1);
-  for (int c = 0; c < nchunks && ok; ++c) {
-    const int s = c & 1;
+  int s = 0;
+  for (int c = 0; c < nchunks; ++c) {
     unsigned char* st = S.stage + s * STAGE_BYTES;
     if (c + 2 < nchunks) load(c + 2, r2);
-    if (issued[s]) {   // the MMAs of chunk c-2 read this stage
-      ok = settle(s);
-      if (!ok) break;
-    }
+    if ((issued >> s) & 1u) settle(s);   // the MMAs of chunk c - NSTAGE read this stage
     store(st, r0);
     r0 = r1;
     r1 = r2;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
+    if (s_fail) {
+      ok = false;
+      break;
+    }
     const int group = c / kGroup;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       issue_chunk(tmem + (uint32_t)(TN * (group & 1)), st, &S.bar[s], (c % kGroup) == 0);
     }
-    issued[s] = 1;
-    if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) drain[s] = 1 + (group & 1);
+    issued |= 1u << s;
+    if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) drain |= (1u + (unsigned)(group & 1)) << (2 * s);
+    s = s + 1 == NSTAGE ? 0 : s + 1;
   }
-  // remaining commits, in chunk order (bounded; also after a timeout)
-  if (nchunks > 0) {
-    const int last = (nchunks - 1) & 1;
-    if (issued[last ^ 1]) ok = settle(last ^ 1) && ok;
-    if (issued[last]) ok = settle(last) && ok;
+  // remaining commits, in chunk order (bounded; also after a lost wait)
+  for (int i = 0; i < NSTAGE; ++i) {
+    if (((issued >> s) & 1u) && !settle(s)) ok = false;
+    s = s + 1 == NSTAGE ? 0 : s + 1;
   }
-  return ok;
+  __syncthreads();
+  return ok && !s_fail;
 }
 
 // ---------------------------------------------------------------- gram
