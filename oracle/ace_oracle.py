@@ -146,6 +146,20 @@ def ace_build(phi: np.ndarray, kern: np.ndarray, dv: float) -> dict:
     return {"W": W, "M": M, "L": L, "Xi": Xi, "Ex": 0.5 * float(np.real(np.trace(M)))}
 
 
+def ace_build_oversampled(phi: np.ndarray, n_occ: int, kern: np.ndarray, dv: float) -> dict:
+    """ACE with oversampling r = N_phi / N_e > 1 (Sec. 3, last paragraph): the
+    exchange operator is that of the N_e = n_occ occupied orbitals phi[:n_occ],
+    W_i = V_X[phi_occ] phi_i for all N_phi orbitals, then M, L, Xi over the N_phi
+    columns as in ace_build. E_x = 1/2 Re tr of the occupied block of M."""
+    phi = np.asarray(phi, dtype=np.complex128)
+    W = exchange_apply(phi[:n_occ], phi, kern)
+    M = overlap_M(phi, W, dv)
+    L = cholesky_neg(M)
+    Xi = xi_from(W, L)
+    ex = 0.5 * float(np.real(np.trace(M[:n_occ, :n_occ])))
+    return {"W": W, "M": M, "L": L, "Xi": Xi, "Ex": ex}
+
+
 def ace_apply(xi: np.ndarray, psi: np.ndarray, dv: float) -> np.ndarray:
     """V_ACE psi = -sum_k xi_k <xi_k, psi> (Eq. ACE)."""
     c = dv * (_mat(xi).conj().T @ _mat(np.asarray(psi, dtype=np.complex128)))

@@ -241,3 +241,29 @@ def test_generator_sphere_counts():
         mx, my, mz = np.meshgrid(m, m, m, indexing="ij")
         want = int(np.sum(0.5 * (2 * math.pi / L) ** 2 * (mx ** 2 + my ** 2 + mz ** 2) <= synth.ECUT_HA))
         assert int(np.sum(0.5 * g2 <= synth.ECUT_HA)) == want
+
+
+# --------------------------------------------------------------------------- oversampling
+@pytest.mark.parametrize("real", [False, True])
+def test_oversampled_ace(real):
+    """Oversampling r = N_phi/N_e > 1 (Sec. 3): V_X stays that of the N_e occupied
+    orbitals, and V_ACE built on the N_phi orbitals reproduces it on all of
+    them -- checked against the dense V_X matrix of Eq. VXkernel -- while the
+    r = 1 operator misses the extra ones; N_phi = N_e reduces to ace_build; E_x
+    is that of the occupied block (Eq. EX)."""
+    s, phi, psi, kern = _small_system(nocc=7, real=real, kernel="erfc", omega=0.5)
+    ne = 4
+    out = oracle.ace_build_oversampled(phi, ne, kern, s.dv)
+    vx = oracle.vx_matrix(phi[:ne], kern)
+    flat = phi.reshape(phi.shape[0], -1)
+    w_dense = (vx @ flat.T).T.reshape(phi.shape)
+    assert rel(out["W"], w_dense) < 1e-12
+    assert rel(oracle.ace_apply(out["Xi"], phi, s.dv), w_dense) < 1e-12
+    r1 = oracle.ace_build(phi[:ne], kern, s.dv)
+    assert rel(oracle.ace_apply(r1["Xi"], phi[ne:], s.dv), w_dense[ne:]) > 1e-3
+    assert rel(out["L"] @ out["L"].conj().T, -out["M"]) < 1e-13
+    assert abs(out["Ex"] - oracle.energy_direct(phi[:ne], kern, s.volume)) < 1e-12 * abs(out["Ex"])
+    same = oracle.ace_build_oversampled(phi[:ne], ne, kern, s.dv)
+    for k in ("W", "M", "Xi"):
+        assert rel(same[k], r1[k]) < 1e-14
+    assert abs(same["Ex"] - r1["Ex"]) < 1e-14 * abs(r1["Ex"])
