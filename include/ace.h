@@ -60,7 +60,8 @@ typedef enum {
 typedef enum { ACE_DTYPE_R64 = 0, ACE_DTYPE_C128 = 1, ACE_DTYPE_C64 = 2 } ace_dtype;
 typedef enum { ACE_KERNEL_BARE = 0, ACE_KERNEL_ERFC = 1 } ace_kernel;
 typedef enum {
-  ACE_OP_EXCHANGE_APPLY = 0, ACE_OP_BUILD = 1, ACE_OP_APPLY = 2, ACE_OP_ENERGY_GRAD = 3
+  ACE_OP_EXCHANGE_APPLY = 0, ACE_OP_BUILD = 1, ACE_OP_APPLY = 2, ACE_OP_ENERGY_GRAD = 3,
+  ACE_OP_BUILD_OVERSAMPLED = 4   /* n_b = N_phi */
 } ace_op;
 
 typedef struct {
@@ -121,7 +122,8 @@ ace_status ace_plan_create(const ace_desc* desc, ace_plan** out);
 ace_status ace_plan_destroy(ace_plan* plan);
 
 /* Bytes of scratch `ws` the entry point `op` needs for n_b target vectors
- * (ignored for ACE_OP_BUILD / ACE_OP_ENERGY_GRAD). 0 on invalid input. */
+ * (N_phi for ACE_OP_BUILD_OVERSAMPLED; ignored for ACE_OP_BUILD /
+ * ACE_OP_ENERGY_GRAD). 0 on invalid input. */
 size_t ace_workspace_size(const ace_plan* plan, int op, int n_b);
 
 /* Y = V_X[Phi] Psi (Eq. applyVX2): N x n_b pair solves, no pair symmetry.
@@ -149,6 +151,20 @@ ace_status ace_exchange_apply(ace_plan* plan, const void* Phi, const void* Psi, 
  * ace_status_sync (ACE_ERR_NOT_POSDEF, info = 1-based pivot); Xi is then undefined. */
 ace_status ace_build(ace_plan* plan, const void* Phi, void* W_out, void* Xi_out,
                      double* M_out, double* Ex_out, void* ws, size_t ws_bytes, void* stream);
+
+/* ACE construction with oversampling (Sec. 3, oversampling ratio
+ * r = N_phi / N_e > 1): V_X is the exchange operator of the plan's N_e = n_occ
+ * occupied orbitals Phi[0..N_e), and W_i = V_X Phi_i for all N_phi orbitals
+ * (the N_e(N_e+1)/2 unique occupied pairs, then N_e (N_phi - N_e) one-sided
+ * pairs); M = dV Phi^* W (N_phi x N_phi, Hermitian part), -M = L L^* in FP64,
+ * Xi = W L^{-*} (N_phi vectors), so that V_ACE = -Xi Xi^* dV agrees with V_X on
+ * span{Phi_0..Phi_{N_phi-1}}. Ex_out = 1/2 Re tr of the occupied block of M.
+ * Phi: N_phi vectors, the occupied ones first. W_out: N_phi vectors or NULL;
+ * Xi_out: N_phi vectors; M_out: NULL or N_phi x N_phi as in ace_build.
+ * n_occ <= N_phi <= 1024; N_phi = n_occ gives ace_build's results.
+ * ws: ace_workspace_size(plan, ACE_OP_BUILD_OVERSAMPLED, N_phi) bytes. */
+ace_status ace_build_oversampled(ace_plan* plan, const void* Phi, int n_phi, void* W_out, void* Xi_out,
+                                 double* M_out, double* Ex_out, void* ws, size_t ws_bytes, void* stream);
 
 /* Batched ACE construction: ace_build for n_sys independent systems (each with
  * its own plan: grid edge, N, dtype and kernel may all differ) issued as ONE

@@ -33,7 +33,7 @@ ACE_ERR_UNSUPPORTED = -7
 DTYPES = {"r64": 0, "c128": 1, "c64": 2}
 TORCH_DTYPES = {"r64": torch.float64, "c128": torch.complex128, "c64": torch.complex64}
 KERNELS = {"bare": 0, "erfc": 1}
-OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD = 0, 1, 2, 3
+OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED = 0, 1, 2, 3, 4
 
 
 class Desc(ctypes.Structure):
@@ -80,6 +80,8 @@ _lib.ace_profile_begin.argtypes = [_vp, ctypes.c_int]
 _lib.ace_profile_begin.restype = ctypes.c_int
 _lib.ace_profile_end.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
 _lib.ace_profile_end.restype = ctypes.c_int
+_lib.ace_build_oversampled.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
+_lib.ace_build_oversampled.restype = ctypes.c_int
 _lib.ace_workspace_size_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
 _lib.ace_workspace_size_batched.restype = ctypes.c_size_t
 _lib.ace_build_batched.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp,
@@ -219,6 +221,29 @@ class Plan:
         ws = self.workspace(OP_BUILD)
         _check(_lib.ace_build(self._h, _ptr(phi), _ptr(w), _ptr(xi), _ptr(m), _ptr(ex), _ptr(ws),
                               ws.numel(), _stream()))
+        if m is not None and self.dtype != "r64":
+            m = torch.view_as_complex(m)
+        return {"Xi": xi, "W": w, "M": m, "Ex": ex}
+
+    def build_oversampled(self, phi, want_w: bool = True, want_m: bool = True, xi=None, w=None):
+        """ACE with oversampling (Sec. 3): phi holds N_phi >= n_occ orbitals, the
+        n_occ occupied ones first; V_X is that of the occupied ones and Xi has
+        N_phi vectors. E_x is that of the occupied block."""
+        self._vec(phi, "phi")
+        n_phi = phi.shape[0]
+        if n_phi < self.n_occ:
+            raise ValueError("phi must hold at least n_occ vectors")
+        xi = self.empty(n_phi) if xi is None else self._vec(xi, "xi")
+        if want_w and w is None:
+            w = self.empty(n_phi)
+        m = None
+        if want_m:
+            shape = (n_phi, n_phi) if self.dtype == "r64" else (n_phi, n_phi, 2)
+            m = torch.empty(shape, dtype=torch.float64, device=self.device)
+        ex = torch.empty((), dtype=torch.float64, device=self.device)
+        ws = self.workspace(OP_BUILD_OVERSAMPLED, n_phi)
+        _check(_lib.ace_build_oversampled(self._h, _ptr(phi), n_phi, _ptr(w), _ptr(xi), _ptr(m), _ptr(ex),
+                                          _ptr(ws), ws.numel(), _stream()))
         if m is not None and self.dtype != "r64":
             m = torch.view_as_complex(m)
         return {"Xi": xi, "W": w, "M": m, "Ex": ex}

@@ -250,6 +250,8 @@ struct WsLayout {
   double* Cm = nullptr;
   char* Wtmp = nullptr;
   char* ctr = nullptr;          // engine queue head + per-batch counters
+  double* work = nullptr;       // oversampled build: Cholesky work and L^{-*} of N_phi
+  double* LinvH = nullptr;
   size_t total = 0;
 };
 
@@ -276,11 +278,20 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   size_t off = 0;
   auto take = [&](size_t bytes) { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
   const int N = p->d.n_occ;
-  const int splits = gram_parts(p, N, op == ACE_OP_APPLY ? nb : N);
-  if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD) {
+  const int splits = op == ACE_OP_BUILD_OVERSAMPLED ? gram_parts(p, nb, nb) : gram_parts(p, N, op == ACE_OP_APPLY ? nb : N);
+  if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD || op == ACE_OP_BUILD_OVERSAMPLED) {
     L.S = take((size_t)p->lanes * lane_bytes(p));
-    const long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
+    long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
+    if (op == ACE_OP_BUILD_OVERSAMPLED && nb > N && rect_batch_bound(p, nb - N) > nbat) nbat = rect_batch_bound(p, nb - N);
     L.ctr = take(engine_ctr_bytes(nbat));
+  }
+  if (op == ACE_OP_BUILD_OVERSAMPLED) {
+    const size_t pd = (size_t)splits * nb * nb * 2;
+    L.part = (double*)take((pd > diag_dot_part_doubles(nb) ? pd : diag_dot_part_doubles(nb)) * sizeof(double));
+    L.Wtmp = take((size_t)nb * p->ng * p->vsize);
+    L.Cm = (double*)take((size_t)nb * nb * 2 * sizeof(double));
+    L.work = (double*)take(cholesky_work_doubles(nb) * sizeof(double));
+    L.LinvH = (double*)take((size_t)nb * nb * 2 * sizeof(double));
   }
   if (op == ACE_OP_ENERGY_GRAD)
     L.Epart = (double*)take((size_t)p->lanes * epart_per_lane(p) * sizeof(double));
@@ -334,9 +345,9 @@ cudaEvent_t* take_events(ace_plan* p, int count, int kind) {
 // are spread over the plan's lanes (fork/join through events), consecutive
 // rounds are joined. Returns the kernel count, or -1 if the edge is not built.
 long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, char* S0, double* E0,
-                      char* ctr, cudaStream_t cs) {
+                      char* ctr, cudaStream_t cs, bool reset_status = true) {
   long long kernels = 0;
-  cudaMemsetAsync(p->status, 0, 2 * sizeof(int), cs);
+  if (reset_status) cudaMemsetAsync(p->status, 0, 2 * sizeof(int), cs);
   if (sc.batches.empty()) return 0;
   if (p->engine) {   // one persistent launch for the whole schedule
     const int m = base.mode == 1 ? 1 : 0;
@@ -504,6 +515,20 @@ PairLaunch base_launch(const ace_plan* p) {
   L.prepare_only = false;
   L.no_pdl = (p->d.flags & ACE_FLAG_NO_PDL) != 0;
   return L;
+}
+
+// The one-sided schedule for n_b target vectors: the plan keeps one per n_b
+// seen; the first call with an n_b builds and uploads it (a small allocation).
+const Schedule* rect_schedule(ace_plan* p, int nb) {
+  for (auto& c : p->rect)
+    if (c.first == nb) return &c.second;
+  p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
+  if (upload(p, p->rect.back().second) != cudaSuccess) {
+    free_schedule(p->rect.back().second);
+    p->rect.pop_back();
+    return nullptr;
+  }
+  return &p->rect.back().second;
 }
 
 void drop_graphs(ace_plan* p) {
@@ -749,8 +774,9 @@ ace_status ace_plan_destroy(ace_plan* p) {
 }
 
 size_t ace_workspace_size(const ace_plan* p, int op, int nb) {
-  if (!p || op < ACE_OP_EXCHANGE_APPLY || op > ACE_OP_ENERGY_GRAD) return 0;
+  if (!p || op < ACE_OP_EXCHANGE_APPLY || op > ACE_OP_BUILD_OVERSAMPLED) return 0;
   if ((op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_APPLY) && nb < 0) return 0;
+  if (op == ACE_OP_BUILD_OVERSAMPLED && (nb < p->d.n_occ || nb > 1024)) return 0;
   return layout(p, op, nb, nullptr).total;
 }
 
@@ -771,19 +797,8 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
   L.OutX = nullptr;
   L.OutY = Y;
   L.mode = 0;
-  // the one-sided schedule depends on n_b; the plan keeps one per n_b seen
-  const Schedule* sc = nullptr;
-  for (auto& c : p->rect)
-    if (c.first == nb) sc = &c.second;
-  if (!sc) {   // first call with this n_b: build and upload its schedule (small allocation)
-    p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
-    if (upload(p, p->rect.back().second) != cudaSuccess) {
-      free_schedule(p->rect.back().second);
-      p->rect.pop_back();
-      return cuda_check("schedule upload");
-    }
-    sc = &p->rect.back().second;
-  }
+  const Schedule* sc = rect_schedule(p, nb);
+  if (!sc) return cuda_check("schedule upload");
   const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)Psi, (uintptr_t)Y, (uintptr_t)ws, (uintptr_t)nb, 1, 0, 0};
   const size_t ybytes = (size_t)nb * p->ng * p->vsize;
   return run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
@@ -820,6 +835,68 @@ ace_status ace_build(ace_plan* p, const void* Phi, void* W_out, void* Xi_out, do
   // caller-owned small outputs, outside the graph (their pointers vary per call)
   p->launches += launch_m_outputs(p->Mc, N, p->real, M_out, Ex_out, st);
   return cuda_check("ace_build");
+}
+
+ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* W_out, void* Xi_out,
+                                 double* M_out, double* Ex_out, void* ws, size_t ws_bytes, void* stream) {
+  if (!p) return fail(ACE_ERR_ARG, "plan is NULL");
+  const int N = p->d.n_occ;
+  if (n_phi < N || n_phi > 1024) return fail(ACE_ERR_ARG, "n_phi must be in [n_occ, 1024]");
+  ace_status s = check_common(p, ws, ws_bytes, ACE_OP_BUILD_OVERSAMPLED, n_phi);
+  if (s != ACE_OK) return s;
+  if (!Phi || !Xi_out) return fail(ACE_ERR_ARG, "Phi and Xi_out are required");
+  if (!aligned16(Phi) || !aligned16(Xi_out) || (W_out && !aligned16(W_out)))
+    return fail(ACE_ERR_ARG, "vectors must be 16-byte aligned");
+  if (Xi_out == Phi || W_out == Phi || (W_out && W_out == Xi_out))
+    return fail(ACE_ERR_ARG, "outputs must not alias Phi or each other");
+  cudaStream_t st = (cudaStream_t)stream;
+  const WsLayout Wl = layout(p, ACE_OP_BUILD_OVERSAMPLED, n_phi, (char*)ws);
+  void* W = W_out ? W_out : (void*)Wl.Wtmp;
+  const size_t vec = (size_t)p->ng * p->vsize;
+  const int nu = n_phi - N;
+  const Schedule* sc = nu > 0 ? rect_schedule(p, nu) : nullptr;
+  if (nu > 0 && !sc) return cuda_check("schedule upload");
+  // W_i = V_X[Phi_occ] Phi_i: unique occupied pairs, then the one-sided pairs
+  // of the occupied orbitals with the N_phi - N_e others (Eq. W, Eq. applyVX2)
+  const uintptr_t kp[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, (uintptr_t)n_phi, 0, 5, 0, 0};
+  s = run_graph(p, kp, st, true, [&](cudaStream_t cs) -> long long {
+    cudaMemsetAsync(W, 0, (size_t)n_phi * vec, cs);
+    PairLaunch L = base_launch(p);
+    L.X = Phi;
+    L.Y = Phi;
+    L.OutX = W;
+    L.OutY = W;
+    L.mode = 0;
+    const long long k1 = issue_pairs(p, L, p->build, Wl.S, nullptr, Wl.ctr, cs);
+    long long k2 = 0;
+    if (nu > 0) {
+      PairLaunch R = base_launch(p);
+      R.X = Phi;
+      R.Y = static_cast<const char*>(Phi) + (size_t)N * vec;
+      R.OutX = nullptr;
+      R.OutY = static_cast<char*>(W) + (size_t)N * vec;
+      R.mode = 0;
+      k2 = issue_pairs(p, R, *sc, Wl.S, nullptr, Wl.ctr, cs, false);
+    }
+    return (k1 < 0 || k2 < 0) ? -1 : k1 + k2;
+  });
+  if (s != ACE_OK) return s;
+  // M = dV Phi^* W (N_phi x N_phi), -M = L L^*, Xi = W L^{-*}
+  const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, (uintptr_t)n_phi, 6, 0, 0};
+  s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
+    const int splits = gram_parts(p, n_phi, n_phi);
+    if (p->tc) launch_gram_tc(Phi, n_phi, W, n_phi, p->ng, p->ng, Wl.part, splits, p->status, cs);
+    else launch_gram(p->f64, p->real, Phi, n_phi, W, n_phi, p->ng, p->ng, Wl.part, splits, cs);
+    launch_gram_reduce(Wl.part, splits, n_phi, n_phi, p->dv, true, false, Wl.Cm, nullptr, cs);
+    if (p->tc) launch_diag_exact(Phi, W, n_phi, p->ng, p->ng, p->dv, Wl.part, Wl.Cm, cs);
+    const int kc = launch_cholesky_inv(Wl.Cm, n_phi, Wl.work, Wl.LinvH, p->status, cs);
+    if (p->tc) launch_outer_tc(W, n_phi, Wl.LinvH, n_phi, p->ng, p->ng, 1.0, Xi_out, p->status, cs);
+    else launch_outer(p->f64, p->real, W, n_phi, Wl.LinvH, n_phi, p->ng, p->ng, 1.0, Xi_out, cs);
+    return 2 + (p->tc ? 2 : 0) + kc + 1;
+  });
+  if (s != ACE_OK) return s;
+  p->launches += launch_m_outputs(Wl.Cm, n_phi, p->real, M_out, Ex_out, st, N);
+  return cuda_check("ace_build_oversampled");
 }
 
 size_t ace_workspace_size_batched(ace_plan* const* plans, int n_sys) {

@@ -101,7 +101,9 @@ void launch_gram_reduce(const double* part, int splits, int na, int nb, double s
                         bool real_out, double* out, double* out_trace_half, cudaStream_t st);
 void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,
                   long long ld, long long ng, double alpha, void* Out, cudaStream_t st);
-int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st);
+// M_out (n x n) and Ex_out = 1/2 Re of the first n_trace diagonal entries (all if < 0).
+int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st,
+                     int n_trace = -1);
 // Tensor-core (tcgen05 kind::tf32, 3-term split) GEMMs for complex FP32 (tc_gemm.cu).
 bool tc_gemm_prepare();
 int gram_tc_splits(long long ng, int na, int nb);

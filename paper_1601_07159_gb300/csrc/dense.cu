@@ -142,10 +142,11 @@ __global__ void gram_reduce_kernel(const double* __restrict__ part, int splits, 
   }
 }
 
-__global__ void trace_half_kernel(const double* __restrict__ m, int n, int real, double* out) {
+// 1/2 Re of the sum of the first `count` diagonal entries of the n x n matrix m.
+__global__ void trace_half_kernel(const double* __restrict__ m, int n, int count, int real, double* out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s = 0.0;
-  for (int k = 0; k < n; ++k) s += real ? m[(long long)k * n + k] : m[2 * ((long long)k * n + k)];
+  for (int k = 0; k < count; ++k) s += real ? m[(long long)k * n + k] : m[2 * ((long long)k * n + k)];
   *out = 0.5 * s;
 }
 
@@ -162,7 +163,8 @@ __global__ void m_copy_kernel(const double* __restrict__ mc, int n, int real, do
 
 // M_out <- M (real part only for real orbitals), Ex_out <- 1/2 Re tr M; both
 // nullable. Returns the number of kernels launched.
-int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st) {
+int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st,
+                     int n_trace) {
   int k = 0;
   if (M_out) {
     const long long nn = (long long)n * n;
@@ -170,7 +172,7 @@ int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* 
     ++k;
   }
   if (Ex_out) {
-    trace_half_kernel<<<1, 32, 0, st>>>(Mc, n, 0, Ex_out);
+    trace_half_kernel<<<1, 32, 0, st>>>(Mc, n, n_trace < 0 ? n : n_trace, 0, Ex_out);
     ++k;
   }
   return k;
@@ -181,7 +183,7 @@ void launch_gram_reduce(const double* part, int splits, int na, int nb, double s
   const long long total = (long long)na * nb;
   gram_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, splits, na, nb, scale,
                                                                       hermitize, real_out, out);
-  if (out_trace_half) trace_half_kernel<<<1, 32, 0, st>>>(out, na, real_out, out_trace_half);
+  if (out_trace_half) trace_half_kernel<<<1, 32, 0, st>>>(out, na, na, real_out, out_trace_half);
 }
 
 // ---------------------------------------------------------------- outer

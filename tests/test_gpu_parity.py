@@ -305,3 +305,53 @@ def test_diff64_full_size_sampled(ace):
     e = ace.exchange_energy(p, plan)
     e.backward()
     assert torch.equal(p.grad, g)
+
+
+@pytest.mark.parametrize("n,L,ne,nphi,dtype,kernel,omega", [
+    (16, 8.0, 5, 9, "c64", "erfc", 0.3),
+    (20, 8.0, 8, 21, "c128", "bare", 0.0),       # N_phi - N_e = 13: two one-sided blocks, ragged
+    (12, 6.0, 3, 6, "r64", "bare", 0.0),
+    (48, 20.5, 16, 24, "c64", "erfc", 0.106),    # the 48^3 cell, r = 1.5
+])
+def test_oversampled_build_parity(ace, n, L, ne, nphi, dtype, kernel, omega):
+    """ACE with oversampling (Sec. 3): W_i = V_X[Phi_occ] Phi_i for all N_phi
+    orbitals, M, Xi over N_phi, E_x of the occupied block, against the oracle;
+    the oversampled V_ACE reproduces W on all N_phi orbitals (Eq. ACEcond on
+    the larger subspace)."""
+    s = synth.System(n=n, L=L, n_occ=nphi, n_bands=1, real=(dtype == "r64"), kernel=kernel, omega=omega)
+    phi = synth.orbitals(s, 3300 + n, ecut=_ecut(n, L))
+    kern = oracle.coulomb_kernel((n, n, n), (L, L, L), kernel, omega)
+    ref = oracle.ace_build_oversampled(phi, ne, kern, s.dv)
+    tol = TOL[dtype]
+    plan = ace.Plan(n, L, ne, dtype=dtype, kernel=kernel, omega=omega)
+    phi_d = _dev(phi, dtype, ace)
+    out = plan.build_oversampled(phi_d)
+    assert plan.status() == (0, 0)
+    assert rel(_host(out["W"]), ref["W"]) < tol["w"]
+    m_ref = ref["M"].real if dtype == "r64" else ref["M"]
+    assert rel(_host(out["M"]), m_ref) < tol["m"]
+    assert rel(_host(out["Xi"]), ref["Xi"]) < tol["xi"]
+    assert abs(out["Ex"].item() - ref["Ex"]) < tol["e"] * abs(ref["Ex"])
+    full = ace.Plan(n, L, nphi, dtype=dtype, kernel=kernel, omega=omega)   # applies N_phi vectors of Xi
+    vphi = full.apply(out["Xi"], phi_d)
+    assert rel(_host(vphi), _host(out["W"])) < tol["xi"]
+    second = plan.build_oversampled(phi_d)                                # graph replay
+    assert torch.equal(second["W"], out["W"]) and torch.equal(second["Xi"], out["Xi"])
+
+
+def test_oversampled_without_extra_orbitals_is_the_build(ace):
+    s, phi, psi, kern = _inputs(24, 10.0, 11, 4, "c64", "erfc", 0.3, seed=9)
+    plan = ace.Plan(24, 10.0, 11, dtype="c64", kernel="erfc", omega=0.3)
+    phi_d = _dev(phi, "c64", ace)
+    a = plan.build(phi_d)
+    b = plan.build_oversampled(phi_d)
+    for k in ("W", "Xi", "M"):
+        assert torch.equal(a[k], b[k]), k
+    assert a["Ex"].item() == b["Ex"].item()
+    with pytest.raises(ValueError):
+        plan.build_oversampled(phi_d[:10])
+    ws = plan.workspace(ace.OP_BUILD_OVERSAMPLED, 11)
+    xi = plan.empty(11)
+    code = ace.lib().ace_build_oversampled(plan._h, ace._ptr(phi_d), 10, None, ace._ptr(xi), None, None,
+                                           ace._ptr(ws), ws.numel(), ace._stream())
+    assert code == ace.ACE_ERR_ARG
