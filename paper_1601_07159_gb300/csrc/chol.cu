@@ -48,23 +48,42 @@ __global__ void neg_copy_kernel(const double2* __restrict__ M, long long count, 
   if (i < count) A[i] = make_double2(-M[i].x, -M[i].y);
 }
 
-// Factor and invert the diagonal block of panel p (nb <= NB); 1024 threads,
-// thread e owns element (e / NB, e % NB). The block is padded to NB with the
-// identity, so every loop runs NB uniform steps.
-// Cholesky on unscaled columns: step j subtracts a_ij conj(a_kj) / d_j from the
-// trailing lower triangle (d_j = a_jj at step j), so a step needs one barrier
-// and one FP64 reciprocal per warp; afterwards L_jj = sqrt(d_j) and
-// L_ij = a_ij / sqrt(d_j) in one parallel pass.
+// Factor and invert the diagonal block of panel p (nb <= NB); 1024 threads.
+// The block is padded to NB with the identity, so every loop runs NB uniform
+// steps.
+// Cholesky on unscaled columns: step j subtracts a_ij conj(a_kj) / d_j from
+// the trailing lower triangle (d_j = a_jj at step j). The trailing triangle's
+// elements are packed densely onto threads (a table ordered by decreasing
+// column, so the elements of step j are the first (NB-1-j)(NB-j)/2), which
+// keeps warps full: FP64 issue is the scarce resource on this part. The thread
+// that updates a_{j+1,j+1} in step j also checks that pivot and forms its
+// reciprocal, so a step needs one barrier and one FP64 reciprocal. The
+// reciprocal is the FP32 one refined by two Newton-Raphson steps in FP64
+// (r <- r + r (1 - d r); each step squares the relative error: 1e-7 -> 1e-14
+// -> rounding). Afterwards L_jj = sqrt(d_j) and L_ij = a_ij / sqrt(d_j) in one
+// parallel pass.
 // Inverse by recursive doubling: for a lower-triangular [[A, 0], [B, C]],
 // the inverse is [[A^-1, 0], [-C^-1 (B A^-1), C^-1]]; five levels (block edge
 // 2, 4, ..., 32) of small products replace NB dependent column steps. The
 // intermediate B A^-1 is kept, transposed, in the unused upper triangle of X.
+__device__ __forceinline__ double recip_nr(double d) {
+  if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;   // outside FP32's comfortable range
+  double r = (double)(1.0f / (float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
+constexpr int kTri = NB * (NB - 1) / 2;   // trailing-triangle elements (i >= k >= 1)
+
 __global__ void __launch_bounds__(1024)
 diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int nb, int* status) {
   __shared__ double2 a[NB][NB + 1];
   __shared__ double2 x[NB][NB + 1];
-  __shared__ double dl[NB], dil[NB];
-  const int tid = threadIdx.x, lane = tid & 31;
+  __shared__ double dl[NB], dil[NB], rj[NB];
+  __shared__ unsigned char ti[kTri], tk[kTri];
+  __shared__ int s_fail, s_piv;
+  const int tid = threadIdx.x;
   const int ei = tid / NB, ek = tid % NB;
   if (status[0] != 0) return;
   {
@@ -73,23 +92,46 @@ diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int
     a[ei][ek] = v;
     x[ei][ek] = make_double2(0.0, 0.0);
   }
+  // packed trailing-triangle table: entries (i, k), k = NB-1 down to 1, i = k .. NB-1
+  if (tid < kTri) {
+    int k = NB - 1, o = 0;
+    while (tid >= o + (NB - k)) {
+      o += NB - k;
+      --k;
+    }
+    ti[tid] = (unsigned char)(k + (tid - o));
+    tk[tid] = (unsigned char)k;
+  }
+  if (tid == 0) s_fail = 0;
+  __syncthreads();
+  auto pivot = [&](int j) {     // one thread: check d_j, store its reciprocal
+    const double d = a[j][j].x;
+    if (!isfinite(d) || !(d > 0.0)) {
+      s_fail = isfinite(d) ? -2 : -3;
+      s_piv = j;
+      rj[j] = 0.0;
+    } else {
+      rj[j] = recip_nr(d);
+    }
+  };
+  if (tid == 0) pivot(0);
   __syncthreads();
   for (int j = 0; j < NB; ++j) {
-    const double d = a[j][j].x;
-    if (!isfinite(d) || !(d > 0.0)) {   // same value in every thread: uniform exit
+    if (s_fail) {               // uniform: read after a barrier
       if (tid == 0) {
-        status[0] = isfinite(d) ? -2 : -3;
-        status[1] = p0 + j + 1;
+        status[0] = s_fail;
+        status[1] = p0 + s_piv + 1;
       }
       return;
     }
-    double r = 0.0;
-    if (lane == 0) r = 1.0 / d;
-    r = __shfl_sync(0xffffffffu, r, 0);
-    if (ei > j && ek > j && ek <= ei) {
-      const double2 u = a[ei][j];
-      const double2 w = a[ek][j];
-      a[ei][ek] = zfmac(a[ei][ek], make_double2(-u.x * r, -u.y * r), w);
+    const int cnt = (NB - 1 - j) * (NB - j) / 2;
+    if (tid < cnt) {
+      const int i = ti[tid], k = tk[tid];
+      const double r = rj[j];
+      const double2 u = a[i][j];
+      const double2 w = a[k][j];
+      a[i][k] = zfmac(a[i][k], make_double2(-u.x * r, -u.y * r), w);
+      if (i == j + 1 && k == j + 1) pivot(j + 1);
     }
     __syncthreads();
   }
