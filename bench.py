@@ -49,6 +49,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
+    p.add_argument("--no-oversampled", action="store_true", help="skip the oversampled-build timing")
     p.add_argument("--max-pairs", type=int, default=0, help="pair solves per batch (0 = plan default)")
     p.add_argument("--tile", type=int, default=0, help="orbitals per tile side (0 = plan default)")
     p.add_argument("--lanes", type=int, default=0, help="concurrent batch streams (0 = plan default)")
@@ -400,6 +401,24 @@ def run_ours(args):
         fp64 = {"fp64_ms_per_build": fp64_ms, "mixed_vs_fp64_build_speedup": fp64_ms / build_ms}
         del plan64, phi64, xi64
 
+    # ACE with oversampling r = 1.5 (Sec. 3): the 128 orbitals plus 64 bands
+    over = None
+    if not args.no_oversampled:
+        phi_all = torch.cat([phi_d, psi_d[:64]]).contiguous()
+        plan.build_oversampled(phi_all, want_w=False, want_m=False)
+        torch.cuda.synchronize()
+        o0 = torch.cuda.Event(enable_timing=True)
+        o1 = torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for _ in range(3):
+            plan.build_oversampled(phi_all, want_w=False, want_m=False)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        code, piv = plan.status()
+        over = {"n_occ": s.n_occ, "n_phi": int(phi_all.shape[0]), "ms_per_build": o0.elapsed_time(o1) / 3,
+                "unique_pairs": unique_pairs(s.n_occ) + s.n_occ * 64, "status": code}
+        del phi_all
+
     cufft = None
     if not args.no_cufft:
         w_ours = plan.build(phi_d)["W"]
@@ -433,6 +452,7 @@ def run_ours(args):
                              "ms_per_launch": pair_ms, "traffic": traffic, "passes": passes},
                 "cpu_baseline": cpu,
                 "cufft_baseline": cufft,
+                "oversampled": over,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": Ke},
                 "gpu_launches": prof["launches"] + 0,

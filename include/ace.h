@@ -61,7 +61,8 @@ typedef enum { ACE_DTYPE_R64 = 0, ACE_DTYPE_C128 = 1, ACE_DTYPE_C64 = 2 } ace_dt
 typedef enum { ACE_KERNEL_BARE = 0, ACE_KERNEL_ERFC = 1 } ace_kernel;
 typedef enum {
   ACE_OP_EXCHANGE_APPLY = 0, ACE_OP_BUILD = 1, ACE_OP_APPLY = 2, ACE_OP_ENERGY_GRAD = 3,
-  ACE_OP_BUILD_OVERSAMPLED = 4   /* n_b = N_phi */
+  ACE_OP_BUILD_OVERSAMPLED = 4,  /* n_b = N_phi */
+  ACE_OP_POISSON = 5             /* n_b = number of densities */
 } ace_op;
 
 typedef struct {
@@ -165,6 +166,16 @@ ace_status ace_build(ace_plan* plan, const void* Phi, void* W_out, void* Xi_out,
  * ws: ace_workspace_size(plan, ACE_OP_BUILD_OVERSAMPLED, N_phi) bytes. */
 ace_status ace_build_oversampled(ace_plan* plan, const void* Phi, int n_phi, void* W_out, void* Xi_out,
                                  double* M_out, double* Ex_out, void* ws, size_t ws_bytes, void* stream);
+
+/* Periodic Poisson solves through the pair passes: V_b(r) = sum_G K(G)
+ * rho_hat_b(G) e^{iG.r} (rho_hat = N_g^-1 sum_r rho e^{-iG.r}) with the plan's
+ * kernel table (alpha K, K(0) = g0). With the bare kernel and rho the electron
+ * density sum_i |psi_i|^2 this is the Hartree potential V_H[rho] of Eq. HF
+ * (K(0) = 0: neutralising background). rho, V: n_b vectors of the plan's
+ * layout and dtype (real densities in R64 plans), V must not alias rho.
+ * ws: ace_workspace_size(plan, ACE_OP_POISSON, n_b) bytes. */
+ace_status ace_poisson(ace_plan* plan, const void* rho, int n_b, void* V, void* ws, size_t ws_bytes,
+                       void* stream);
 
 /* Batched ACE construction: ace_build for n_sys independent systems (each with
  * its own plan: grid edge, N, dtype and kernel may all differ) issued as ONE

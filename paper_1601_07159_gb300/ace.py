@@ -33,7 +33,7 @@ ACE_ERR_UNSUPPORTED = -7
 DTYPES = {"r64": 0, "c128": 1, "c64": 2}
 TORCH_DTYPES = {"r64": torch.float64, "c128": torch.complex128, "c64": torch.complex64}
 KERNELS = {"bare": 0, "erfc": 1}
-OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED = 0, 1, 2, 3, 4
+OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED, OP_POISSON = 0, 1, 2, 3, 4, 5
 
 
 class Desc(ctypes.Structure):
@@ -82,6 +82,8 @@ _lib.ace_profile_end.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.PO
 _lib.ace_profile_end.restype = ctypes.c_int
 _lib.ace_build_oversampled.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]
 _lib.ace_build_oversampled.restype = ctypes.c_int
+_lib.ace_poisson.argtypes = [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
+_lib.ace_poisson.restype = ctypes.c_int
 _lib.ace_workspace_size_batched.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
 _lib.ace_workspace_size_batched.restype = ctypes.c_size_t
 _lib.ace_build_batched.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp,
@@ -247,6 +249,16 @@ class Plan:
         if m is not None and self.dtype != "r64":
             m = torch.view_as_complex(m)
         return {"Xi": xi, "W": w, "M": m, "Ex": ex}
+
+    def poisson(self, rho, out=None):
+        """V_b = sum_G K(G) rho_hat_b(G) e^{iG.r} with the plan's kernel: the
+        Hartree potential of Eq. HF for the bare kernel and the density."""
+        self._vec(rho, "rho")
+        nb = rho.shape[0]
+        v = self.empty(nb) if out is None else self._vec(out, "out")
+        ws = self.workspace(OP_POISSON, nb)
+        _check(_lib.ace_poisson(self._h, _ptr(rho), nb, _ptr(v), _ptr(ws), ws.numel(), _stream()))
+        return v
 
     def apply(self, xi, psi, out=None):
         """Y = V_ACE psi = -Xi (dV Xi^* psi) (Eq. ACE)."""

@@ -89,6 +89,8 @@ struct ace_plan {
   std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
   Schedule build;                // symmetric schedule of the W build
   std::deque<std::pair<int, Schedule>> rect;   // one-sided schedules by n_b
+  std::deque<std::pair<int, Schedule>> pois;   // one-sided schedules of one constant orbital, by n_b
+  void* ones = nullptr;          // N_g vector of ones (the left factor of the Poisson solves)
   void* Kt = nullptr;            // kernel table (float or double)
   double* Mc = nullptr;          // 2 N^2, M (complex, row-major)
   double* work = nullptr;        // 4 N^2, Cholesky work (global fallback)
@@ -279,9 +281,11 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   auto take = [&](size_t bytes) { char* r = base ? base + off : nullptr; off += align256(bytes); return r; };
   const int N = p->d.n_occ;
   const int splits = op == ACE_OP_BUILD_OVERSAMPLED ? gram_parts(p, nb, nb) : gram_parts(p, N, op == ACE_OP_APPLY ? nb : N);
-  if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD || op == ACE_OP_BUILD_OVERSAMPLED) {
+  if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD || op == ACE_OP_BUILD_OVERSAMPLED ||
+      op == ACE_OP_POISSON) {
     L.S = take((size_t)p->lanes * lane_bytes(p));
     long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
+    if (op == ACE_OP_POISSON) nbat = (nb + p->tile - 1) / p->tile;
     if (op == ACE_OP_BUILD_OVERSAMPLED && nb > N && rect_batch_bound(p, nb - N) > nbat) nbat = rect_batch_bound(p, nb - N);
     L.ctr = take(engine_ctr_bytes(nbat));
   }
@@ -531,6 +535,19 @@ const Schedule* rect_schedule(ace_plan* p, int nb) {
   return &p->rect.back().second;
 }
 
+// The one-sided schedule of the Poisson solves (one constant left orbital).
+const Schedule* poisson_schedule(ace_plan* p, int nb) {
+  for (auto& c : p->pois)
+    if (c.first == nb) return &c.second;
+  p->pois.emplace_back(nb, make_rect_schedule(1, nb, p->tile, p->max_pairs));
+  if (upload(p, p->pois.back().second) != cudaSuccess) {
+    free_schedule(p->pois.back().second);
+    p->pois.pop_back();
+    return nullptr;
+  }
+  return &p->pois.back().second;
+}
+
 void drop_graphs(ace_plan* p) {
   for (auto& g : p->graph_cache) cudaGraphExecDestroy(g.exec);
   p->graph_cache.clear();
@@ -708,6 +725,20 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     e = cudaMalloc(&p->Kt, kf.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(p->Kt, kf.data(), kf.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
+  if (e == cudaSuccess) {
+    if (p->vsize == 8 && !p->real) {   // c64: (1.0f, 0.0f) pairs
+      std::vector<float> onef((size_t)2 * p->ng, 0.0f);
+      for (long long i = 0; i < p->ng; ++i) onef[2 * i] = 1.0f;
+      e = cudaMalloc(&p->ones, onef.size() * sizeof(float));
+      if (e == cudaSuccess) e = cudaMemcpy(p->ones, onef.data(), onef.size() * sizeof(float), cudaMemcpyHostToDevice);
+    } else {                           // r64: 1.0; c128: (1.0, 0.0)
+      const size_t stride = p->real ? 1 : 2;
+      std::vector<double> oned((size_t)p->ng * stride, 0.0);
+      for (long long i = 0; i < p->ng; ++i) oned[stride * i] = 1.0;
+      e = cudaMalloc(&p->ones, oned.size() * sizeof(double));
+      if (e == cudaSuccess) e = cudaMemcpy(p->ones, oned.data(), oned.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+  }
   if (e == cudaSuccess) e = cudaMalloc(&p->Mc, (size_t)2 * N * N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->work, cholesky_work_doubles(N) * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&p->LinvH, (size_t)2 * N * N * sizeof(double));
@@ -764,6 +795,8 @@ ace_status ace_plan_destroy(ace_plan* p) {
     if (e) cudaEventDestroy(e);
   free_schedule(p->build);
   for (auto& r : p->rect) free_schedule(r.second);
+  for (auto& r : p->pois) free_schedule(r.second);
+  cudaFree(p->ones);
   cudaFree(p->Kt);
   cudaFree(p->Mc);
   cudaFree(p->work);
@@ -774,8 +807,8 @@ ace_status ace_plan_destroy(ace_plan* p) {
 }
 
 size_t ace_workspace_size(const ace_plan* p, int op, int nb) {
-  if (!p || op < ACE_OP_EXCHANGE_APPLY || op > ACE_OP_BUILD_OVERSAMPLED) return 0;
-  if ((op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_APPLY) && nb < 0) return 0;
+  if (!p || op < ACE_OP_EXCHANGE_APPLY || op > ACE_OP_POISSON) return 0;
+  if ((op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_APPLY || op == ACE_OP_POISSON) && nb < 0) return 0;
   if (op == ACE_OP_BUILD_OVERSAMPLED && (nb < p->d.n_occ || nb > 1024)) return 0;
   return layout(p, op, nb, nullptr).total;
 }
@@ -897,6 +930,35 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
   if (s != ACE_OK) return s;
   p->launches += launch_m_outputs(Wl.Cm, n_phi, p->real, M_out, Ex_out, st, N);
   return cuda_check("ace_build_oversampled");
+}
+
+ace_status ace_poisson(ace_plan* p, const void* rho, int nb, void* V, void* ws, size_t ws_bytes, void* stream) {
+  ace_status s = check_common(p, ws, ws_bytes, ACE_OP_POISSON, nb);
+  if (s != ACE_OK) return s;
+  if (nb < 0) return fail(ACE_ERR_ARG, "n_b must be >= 0");
+  if (nb == 0) return ACE_OK;
+  if (!rho || !V) return fail(ACE_ERR_ARG, "NULL vector pointer");
+  if (!aligned16(rho) || !aligned16(V)) return fail(ACE_ERR_ARG, "vectors must be 16-byte aligned");
+  if (V == rho) return fail(ACE_ERR_ARG, "V must not alias rho");
+  cudaStream_t st = (cudaStream_t)stream;
+  const WsLayout W = layout(p, ACE_OP_POISSON, nb, (char*)ws);
+  const Schedule* sc = poisson_schedule(p, nb);
+  if (!sc) return cuda_check("schedule upload");
+  // one-sided pair solves of the constant orbital 1 with each rho_b: pass D
+  // accumulates Out -= scale * 1 * v, so scale -1 leaves V_b = Poisson[rho_b]
+  PairLaunch L = base_launch(p);
+  L.X = p->ones;
+  L.Y = rho;
+  L.OutX = nullptr;
+  L.OutY = V;
+  L.mode = 0;
+  L.scale = -1.0;
+  const uintptr_t key[8] = {(uintptr_t)rho, (uintptr_t)V, (uintptr_t)ws, (uintptr_t)nb, 0, 7, 0, 0};
+  const size_t vbytes = (size_t)nb * p->ng * p->vsize;
+  return run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
+    cudaMemsetAsync(V, 0, vbytes, cs);
+    return issue_pairs(p, L, *sc, W.S, nullptr, W.ctr, cs);
+  });
 }
 
 size_t ace_workspace_size_batched(ace_plan* const* plans, int n_sys) {
