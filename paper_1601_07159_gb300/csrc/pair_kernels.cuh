@@ -321,8 +321,63 @@ __device__ __forceinline__ void d_full_off(const PairParams<R, N>& P, const Tile
   }
 }
 
+// Off-diagonal full tile with two threads per grid point: thread half h takes
+// the right orbitals r0 + 4h .. r0 + 4h + 3 (its 32 of the tile's 64 pair
+// potentials), so each thread holds half the state of d_full_off and a block
+// keeps twice the loads in flight. Each warp covers 32 consecutive points of
+// one half (coalesced). The left outputs' two partial sums (over the two
+// halves of r) meet through shared memory and are added in a fixed order;
+// thread h then updates Out_l for l0 + 4h .. l0 + 4h + 3 and Out_r for its r.
+constexpr int kDSplitPts = 128;   // points per 256-thread block
+template <typename R, int N, bool REAL>
+__device__ __forceinline__ void d_split_off(const PairParams<R, N>& P, const TileDesc& d, long long vbx, int tid,
+                                            cplx<R>* xch) {
+  constexpr long long NG = (long long)N * N * N;
+  constexpr int B = kTileMax, H = kTileMax / 2;
+  const int h = (tid >> 5) & 1;
+  const int pt = ((tid >> 6) << 5) | (tid & 31);
+  const long long g = vbx * kDSplitPts + pt;
+  const bool act = g < NG;
+  const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
+  cplx<R> xl[B], yr[H], al[B], ar[H];
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    al[o] = cmk<cplx<R>>(R(0), R(0));
+    xl[o] = act ? load_vec<R, REAL>(P.X, (long long)(d.l0 + o) * P.ld + g) : al[o];
+  }
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    ar[o] = al[o];
+    yr[o] = act ? load_vec<R, REAL>(P.Y, (long long)(d.r0 + h * H + o) * P.ld + g) : al[o];
+  }
+  if (act) {
+#pragma unroll
+    for (int li = 0; li < B; ++li) {
+#pragma unroll
+      for (int ri = 0; ri < H; ++ri) {
+        const cplx<R> v = __ldcs(V + (long long)(li * B + h * H + ri) * NG);
+        ar[ri] = cadd(ar[ri], cmul(xl[li], v));
+        al[li] = cadd(al[li], cmulc(v, yr[ri]));
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < H; ++o) xch[o * 256 + tid] = h ? al[o] : al[H + o];   // the partner's half
+  __syncthreads();
+  if (!act) return;
+  const int partner = tid ^ 32;                                           // same point, other half
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    const cplx<R> own = h ? al[H + o] : al[o];
+    const cplx<R> other = xch[o * 256 + partner];
+    const cplx<R> lo = h ? other : own, hi = h ? own : other;              // r-half 0 first, then 1
+    rmw_out<R, REAL, false>(P.OutX, (long long)(d.l0 + h * H + o) * P.ld + g, cadd(lo, hi), P.scale);
+    rmw_out<R, REAL, false>(P.OutY, (long long)(d.r0 + h * H + o) * P.ld + g, ar[o], P.scale);
+  }
+}
+
 // Pass D for point block `vbx` (nthr points) of tile `d`.
-template <typename R, int N, bool REAL, bool COH>
+template <typename R, int N, bool REAL, bool COH, bool FULL_OFF = true>
 __device__ __forceinline__ void body_d(const PairParams<R, N>& P, const TileDesc& d, long long vbx, int tid,
                                        int nthr) {
   constexpr long long NG = (long long)N * N * N;
@@ -331,7 +386,7 @@ __device__ __forceinline__ void body_d(const PairParams<R, N>& P, const TileDesc
   const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
   if (d.kind == 1 && d.nl == kTileMax) {
     d_full_diag<R, N, REAL, COH>(P, d, V, g);
-  } else if (d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
+  } else if (FULL_OFF && d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
     d_full_off<R, N, REAL, COH>(P, d, V, g);
   } else if (d.kind == 1) {
     cplx<R> x[kTileMax], acc[kTileMax];
@@ -430,17 +485,25 @@ pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
   body_c<R, N, false, plane_items<R, N>()>(P, P.npairs, reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
-// Two blocks per SM: the 128-register cap keeps more of the tile's pair
-// potential loads in flight than the unconstrained allocation (104 registers),
-// which measured faster (as did this plain-load form against streaming the
-// potentials through shared memory with bulk copies).
+// Full off-diagonal tiles take two threads per grid point (d_split_off) at
+// four blocks per SM (64 registers): more warps and loads in flight per SM,
+// which measured faster than one thread per point at 2 or 3 blocks per SM
+// (and than streaming the potentials through shared memory with bulk copies).
 template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2)
 pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
+  __shared__ cplx<R> xch[(kTileMax / 2) * 256];
   griddep_launch();
   griddep_wait();
   const TileDesc d = P.tiles[blockIdx.y];
-  body_d<R, N, REAL, false>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
+  if (d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
+    d_split_off<R, N, REAL>(P, d, blockIdx.x, threadIdx.x, xch);
+    return;
+  }
+  // other tiles: one thread per point, 256 points per block (the grid is
+  // sized for 128-point blocks, so the upper half of the blocks has no work)
+  if ((long long)blockIdx.x * 256 >= (long long)N * N * N) return;
+  body_d<R, N, REAL, false, false>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------- persistent engine
@@ -662,7 +725,7 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   const dim3 pblk(N * IPB);
   const unsigned pgrid = (unsigned)((items + IPB - 1) / IPB);
   const unsigned bgrid = (unsigned)(((long long)b.npairs * N * N + 255) / 256);
-  const dim3 dgrid((unsigned)(((long long)N * N * N + 255) / 256), (unsigned)b.ntiles);
+  const dim3 dgrid((unsigned)(((long long)N * N * N + kDSplitPts - 1) / kDSplitPts), (unsigned)b.ntiles);
   if constexpr (sizeof(R) != 8) {
     if (L.real_io) return false;
   }

@@ -119,12 +119,14 @@ def test_bitwise_reproducible(ace):
 @pytest.mark.parametrize("engine,lanes,graphs,overlap", [(True, 1, True, False), (True, 1, False, False),
                                                         (False, 3, True, False), (False, 0, True, True)])
 def test_schedules_match_bitwise(ace, engine, lanes, graphs, overlap):
-    """Every way of running the pair schedule gives the same bits as eager
-    four-kernel launches: the persistent engine (in or out of a graph), the
-    four-kernel path replayed from a graph with a round's batches spread over
-    lanes, and the two-stream schedule in which pass A of a batch overlaps
-    pass D of the previous one. Each output element is written by one tile per
-    round and rounds run in order. New pointers capture a new graph."""
+    """Every way of running the four-kernel pair schedule gives the same bits
+    as eager launches: replayed from a graph with a round's batches spread
+    over lanes, and the two-stream schedule in which pass A of a batch
+    overlaps pass D of the previous one. Each output element is written by one
+    tile per round and rounds run in order; new pointers capture a new graph.
+    The persistent engine accumulates a full off-diagonal tile with one thread
+    per point (the four-kernel pass D splits it over two), so it agrees to
+    rounding, and is bitwise stable from call to call."""
     s, phi, psi, kern = _inputs(24, 10.0, 21, 10, "c64", "erfc", 0.3, seed=8)
     eager = ace.Plan(24, 10.0, 21, dtype="c64", kernel="erfc", omega=0.3, tile=4, max_pairs=16,
                      graphs=False)
@@ -132,13 +134,23 @@ def test_schedules_match_bitwise(ace, engine, lanes, graphs, overlap):
                      lanes=lanes, graphs=graphs, engine=engine, overlap=overlap)
     phi_d = _dev(phi, "c64", ace)
     psi_d = _dev(psi, "c64", ace)
+
+    def same(x, y, tol):
+        if engine:
+            return float(torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(x)) < tol
+        return torch.equal(x, y)
+
     a = eager.build(phi_d)
+    first = None
     for _ in range(2):                       # capture, then replay
         b = graph.build(phi_d)
-        assert torch.equal(a["W"], b["W"]) and torch.equal(a["Xi"], b["Xi"])
+        assert same(a["W"], b["W"], 1e-6) and same(a["Xi"], b["Xi"], 1e-5)
+        if first is None:
+            first = b["W"].clone()
+        assert torch.equal(first, b["W"])
     phi2 = phi_d.clone()
     c = graph.build(phi2)                    # new pointer -> new graph
-    assert torch.equal(a["W"], c["W"])
+    assert torch.equal(first, c["W"])
     # one-sided tiles: the runtime-length loop may contract multiply-adds
     # differently in the two kernels, so modes agree to rounding, and each
     # mode is bitwise stable from call to call
@@ -152,7 +164,7 @@ def test_schedules_match_bitwise(ace, engine, lanes, graphs, overlap):
     assert d < 1e-6
     ea, ga = eager.energy_grad(phi_d, grad=True, grad_scale=-1.5)
     eb, gb = graph.energy_grad(phi_d, grad=True, grad_scale=-1.5)
-    assert torch.equal(ga, gb) and abs(ea.item() - eb.item()) <= 1e-13 * abs(ea.item())
+    assert same(ga, gb, 1e-6) and abs(ea.item() - eb.item()) <= 1e-13 * abs(ea.item())
     assert graph.status() == (0, 0)
     assert rel(_host(gb), -1.5 * oracle.energy_grad(phi, kern, s.dv)) < 1e-5
 
