@@ -259,7 +259,7 @@ struct WsLayout {
 
 // Split-K partial matrices of a gram product (the tensor-core or CUDA-core one).
 int gram_parts(const ace_plan* p, int na, int nb) {
-  return p->tc ? gram_tc_splits(p->ng, na, nb) : gram_splits(p->ng);
+  return p->tc ? gram_tc_splits(p->ng, na, nb) : gram_splits(p->ng, na, nb);
 }
 
 // Upper bound on the batches of the one-sided schedule for n_b vectors.
@@ -646,7 +646,8 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   *out = nullptr;
   if (!d) return fail(ACE_ERR_ARG, "desc is NULL");
   if (d->dtype < ACE_DTYPE_R64 || d->dtype > ACE_DTYPE_C64) return fail(ACE_ERR_ARG, "bad dtype");
-  if (d->kernel != ACE_KERNEL_BARE && d->kernel != ACE_KERNEL_ERFC) return fail(ACE_ERR_ARG, "bad kernel");
+  if (d->kernel != ACE_KERNEL_BARE && d->kernel != ACE_KERNEL_ERFC && d->kernel != ACE_KERNEL_KINETIC)
+    return fail(ACE_ERR_ARG, "bad kernel");
   if (d->n_occ < 1) return fail(ACE_ERR_ARG, "n_occ must be >= 1");
   if (d->n_occ > 1024) return fail(ACE_ERR_UNSUPPORTED, "n_occ > 1024 not supported");
   if (!(d->L[0] > 0 && d->L[1] > 0 && d->L[2] > 0)) return fail(ACE_ERR_ARG, "cell edges must be > 0");
@@ -698,7 +699,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     p->tw[2 * k + 1] = -std::sin(a);
   }
   // kernel table K(G) alpha / N_g in the spectrum layout [kz][kx][ky]
-  const double g0_default = d->kernel == ACE_KERNEL_BARE ? 0.0 : M_PI / (d->omega * d->omega);
+  const double g0_default = d->kernel == ACE_KERNEL_ERFC ? M_PI / (d->omega * d->omega) : 0.0;
   const double g0 = std::isnan(d->g0_value) ? g0_default : d->g0_value;
   std::vector<double> kt((size_t)p->ng);
   auto freq = [n](int i) { return (i <= n / 2) ? i : i - n; };   // |G| symmetric at n/2
@@ -712,6 +713,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
         double k;
         if (g2 == 0.0) k = g0;
         else if (d->kernel == ACE_KERNEL_BARE) k = 4.0 * M_PI / g2;
+        else if (d->kernel == ACE_KERNEL_KINETIC) k = 0.5 * g2;
         else k = 4.0 * M_PI / g2 * (1.0 - std::exp(-g2 / (4.0 * d->omega * d->omega)));
         kt[((size_t)kz * n + kx) * n + ky] = d->alpha * k / (double)p->ng;
       }

@@ -96,7 +96,7 @@ int energy_blocks(int n, int npairs, bool f64);
 // Dense kernels (dense.cu).
 void launch_gram(bool f64, bool real_in, const void* A, int na, const void* B, int nb, long long ld,
                  long long ng, double* part, int splits, cudaStream_t st);
-int gram_splits(long long ng);
+int gram_splits(long long ng, int na, int nb);
 void launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
                         bool real_out, double* out, double* out_trace_half, cudaStream_t st);
 void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,

@@ -61,7 +61,7 @@ extern "C" ace_status ace_apply_static(ace_plan* p, const void* Xi, const void* 
         ACE_ERR_ARG, ("n_occ * n_b = " + std::to_string((long long)N * nb) +
                       " exceeds the static scratch (max " +
                       std::to_string(ACE_STATIC_SCRATCH_BYTES / (4 * sizeof(double))) + ")").c_str());
-  int splits = ace::gram_splits(ng);
+  int splits = ace::gram_splits(ng, N, nb);
   if ((size_t)splits > fit - 1) splits = (int)(fit - 1);
 
   void* base = nullptr;

@@ -30,6 +30,11 @@ gram_kernel(const void* __restrict__ A, int na, const void* __restrict__ B, int 
   const int a0 = blockIdx.x * GT, b0 = blockIdx.y * GT;
   const long long g_begin = (long long)blockIdx.z * chunk;
   const long long g_end = g_begin + chunk < ng ? g_begin + chunk : ng;
+  // this thread's rows a0 + ty + 16 i (i < ni) and columns b0 + tx + 16 j (j < nj)
+  // inside the matrix: small matrices do no work on the tile's padding (on this
+  // part FP64 issue is scarce, and padded warps skip the products entirely)
+  const int ra = na - a0 - ty, rb = nb - b0 - tx;
+  const int ni = ra <= 0 ? 0 : (ra + 15) / 16, nj = rb <= 0 ? 0 : (rb + 15) / 16;
   cplx<R> acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -69,8 +74,11 @@ gram_kernel(const void* __restrict__ A, int na, const void* __restrict__ B, int 
       for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
+        if (i < ni) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = cadd(acc[i][j], cmulc(av[i], bv[j]));
+          for (int j = 0; j < 4; ++j)
+            if (j < nj) acc[i][j] = cadd(acc[i][j], cmulc(av[i], bv[j]));
+        }
     }
     __syncthreads();
   }
@@ -89,9 +97,15 @@ gram_kernel(const void* __restrict__ A, int na, const void* __restrict__ B, int 
   }
 }
 
-int gram_splits(long long ng) {
-  // ~1.2k-point chunks keep the FP32 partial sums short while filling the GPU
+int gram_splits(long long ng, int na, int nb) {
+  // ~1k-point chunks keep the FP32 partial sums short; small matrices on small
+  // grids take shorter chunks so that the launch still covers one wave of SMs
   long long s = (ng + 1023) / 1024;
+  const long long tiles = (long long)((na + GT - 1) / GT) * ((nb + GT - 1) / GT);
+  const long long wave = tiles > 0 ? (152 + tiles - 1) / tiles : 1;
+  const long long max_s = (ng + GK - 1) / GK;   // at least one K stage per split
+  if (s < wave) s = wave;
+  if (s > max_s) s = max_s;
   if (s > 256) s = 256;
   if (s < 1) s = 1;
   return (int)s;
@@ -201,12 +215,17 @@ outer_kernel(const void* __restrict__ A, int nk, const double* __restrict__ C, i
   const int tg = threadIdx.x & 63, tb = threadIdx.x >> 6;   // 64 x 4
   const long long g0 = (long long)blockIdx.x * OG;
   const int b0 = blockIdx.y * OB;
+  // this thread's columns b0 + 4 tb + j (j < nj) inside the output (padded
+  // warps skip the products)
+  const int rbb = nb - b0 - 4 * tb;
+  const int nj = rbb <= 0 ? 0 : (rbb < 4 ? rbb : 4);
   cplx<R> acc[2][4];
 #pragma unroll
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = cmk<cplx<R>>(R(0), R(0));
   for (int k0 = 0; k0 < nk; k0 += OK) {
+    const int kmax = nk - k0 < OK ? nk - k0 : OK;
 #pragma unroll
     for (int e = 0; e < (OK * OG) / 256; ++e) {
       const int idx = threadIdx.x + 256 * e;
@@ -232,6 +251,7 @@ outer_kernel(const void* __restrict__ A, int nk, const double* __restrict__ C, i
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < OK; ++k) {
+      if (k >= kmax) break;
       cplx<R> av[2], cv[4];
 #pragma unroll
       for (int i = 0; i < 2; ++i) av[i] = As[k][tg + 64 * i];
@@ -240,7 +260,8 @@ outer_kernel(const void* __restrict__ A, int nk, const double* __restrict__ C, i
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = cadd(acc[i][j], cmul(av[i], cv[j]));
+        for (int j = 0; j < 4; ++j)
+          if (j < nj) acc[i][j] = cadd(acc[i][j], cmul(av[i], cv[j]));
     }
     __syncthreads();
   }
