@@ -16,7 +16,11 @@
  *   v(r) = sum_G K(G) rho_hat(G) e^{iG.r},  rho_hat(G) = N_g^-1 sum_r rho(r) e^{-iG.r},
  * with K(G) = alpha * 4 pi/|G|^2 (ACE_KERNEL_BARE, K(0) = 0 by default) or
  * alpha * (4 pi/|G|^2)(1 - exp(-|G|^2 / 4 omega^2)) (ACE_KERNEL_ERFC, K(0) =
- * alpha * pi / omega^2 by default). Complex orbitals use the Hermitian form
+ * alpha * pi / omega^2 by default). ACE_KERNEL_KINETIC, K(G) = alpha |G|^2 / 2,
+ * is not an exchange kernel: with it, ace_poisson applies the kinetic-energy
+ * operator -1/2 Laplacian (spectrally) to its vectors, the T of Eq. HF, so a
+ * model Hamiltonian can be applied with this library's FFT passes alone.
+ * Complex orbitals use the Hermitian form
  * V_X(r, r') = -sum_j phi_j(r) conj(phi_j(r')) K(r - r').
  *
  * Conventions shared by every entry point:
@@ -58,7 +62,7 @@ typedef enum {
 } ace_status;
 
 typedef enum { ACE_DTYPE_R64 = 0, ACE_DTYPE_C128 = 1, ACE_DTYPE_C64 = 2 } ace_dtype;
-typedef enum { ACE_KERNEL_BARE = 0, ACE_KERNEL_ERFC = 1 } ace_kernel;
+typedef enum { ACE_KERNEL_BARE = 0, ACE_KERNEL_ERFC = 1, ACE_KERNEL_KINETIC = 2 } ace_kernel;
 typedef enum {
   ACE_OP_EXCHANGE_APPLY = 0, ACE_OP_BUILD = 1, ACE_OP_APPLY = 2, ACE_OP_ENERGY_GRAD = 3,
   ACE_OP_BUILD_OVERSAMPLED = 4,  /* n_b = N_phi */

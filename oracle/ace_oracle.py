@@ -81,6 +81,12 @@ def coulomb_kernel(shape, lengths, kind="bare", omega=0.0, g0=None, alpha=1.0):
 # --------------------------------------------------------------------------
 # Poisson solve and the exchange operator (Eq. applyVX, applyVX2, W)
 # --------------------------------------------------------------------------
+def kinetic_kernel(shape, lengths, alpha=1.0):
+    """alpha |G|^2 / 2 on the wrapped grid: with poisson() below it applies the
+    kinetic-energy operator -1/2 Laplacian of Eq. HF spectrally."""
+    return alpha * 0.5 * reciprocal_sq(shape, lengths)
+
+
 def poisson(rho: np.ndarray, kern: np.ndarray) -> np.ndarray:
     """v = sum_G K(G) rho_hat(G) e^{iG.r}; rho may carry leading batch axes."""
     axes = (-3, -2, -1)

@@ -32,7 +32,7 @@ ACE_ERR_UNSUPPORTED = -7
 
 DTYPES = {"r64": 0, "c128": 1, "c64": 2}
 TORCH_DTYPES = {"r64": torch.float64, "c128": torch.complex128, "c64": torch.complex64}
-KERNELS = {"bare": 0, "erfc": 1}
+KERNELS = {"bare": 0, "erfc": 1, "kinetic": 2}
 OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED, OP_POISSON = 0, 1, 2, 3, 4, 5
 
 

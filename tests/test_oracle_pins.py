@@ -267,3 +267,19 @@ def test_oversampled_ace(real):
     for k in ("W", "M", "Xi"):
         assert rel(same[k], r1[k]) < 1e-14
     assert abs(same["Ex"] - r1["Ex"]) < 1e-14 * abs(r1["Ex"])
+
+
+def test_kinetic_kernel_plane_waves():
+    """The kinetic table |G|^2/2 with the FFT Poisson step applies -1/2 Laplacian:
+    a plane wave e^{ik.r} (k on the grid) is an eigenvector with eigenvalue
+    |k|^2/2, computed here from the integer wavevector."""
+    n, L = 10, 7.0
+    kin = oracle.kinetic_kernel((n, n, n), (L, L, L))
+    for m in [(0, 0, 0), (1, 0, 0), (2, -3, 1), (-4, 4, 2), (5, 0, -5)]:
+        pw = synth.plane_wave_orbitals(n, L, [m])[0]
+        k2 = sum((2.0 * math.pi * mi / L) ** 2 for mi in m)
+        t = oracle.poisson(pw[None], kin)[0]
+        if k2 == 0.0:
+            assert np.max(np.abs(t)) < 1e-13
+        else:
+            assert rel(t, 0.5 * k2 * pw) < 1e-12
