@@ -80,7 +80,8 @@ bool launch_engine_f64(const PairLaunch& L, const EngineLaunch& E, cudaStream_t 
 
 int energy_blocks(int n, int npairs, bool f64) {
   (void)f64;
-  return (int)(((long long)npairs * n * n + 255) / 256);
+  // pass B: one slot per block (256 pencils; 128 for the two-lane form of n >= 64)
+  return (int)(((long long)npairs * n * n + 127) / 128);
 }
 
 }  // namespace ace

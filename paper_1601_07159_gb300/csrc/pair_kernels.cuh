@@ -466,6 +466,104 @@ pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
                                                        reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
+// Pass B for the large edges (n >= 64), whose whole pencil per thread spills:
+// two lanes per z-pencil (lanes 2q, 2q+1 of a warp; 128 pencils per block).
+// Lane h holds the samples z = 2m + h and transforms them with a DFT of N/2:
+//   forward  Y[k] = E[k] + w^k O[k], Y[k + N/2] = E[k] - w^k O[k]
+//            (E, O the half-length transforms of the even / odd samples,
+//            w = exp(-2 pi i / N)); lane h keeps k in [hN/4, (h+1)N/4) and gets
+//            the partner's half of E or w^k O by one shuffle per value;
+//   inverse  x[2m] = IDFT(Y[k] + Y[k + N/2]), x[2m+1] = IDFT((Y[k] - Y[k + N/2]) w^-k)
+//            over k < N/2; each lane forms its quarter of both sequences and
+//            swaps the other lane's by shuffle; lane 0 transforms the first,
+//            lane 1 the second.
+// Lane roles are selected arithmetically (no divergent branches). At n = 48 the
+// shuffles cost more than the occupancy gains, so smaller edges keep one
+// thread per pencil.
+template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
+  T r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+  return r;
+}
+constexpr int kBSplitPencils = 128;   // pencils per 256-thread block of the split pass B
+
+template <typename R, int N>
+__global__ void __launch_bounds__(256, 2)
+pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
+  using C = cplx<R>;
+  constexpr int N2 = N * N, M = N / 2, H = N / 4;
+  static_assert(N % 4 == 0, "the split pass B halves a pencil twice");
+  __shared__ double red[8];
+  griddep_launch();
+  griddep_wait();
+  const int tid = threadIdx.x, h = tid & 1;
+  const long long gid = (long long)blockIdx.x * kBSplitPencils + (tid >> 1);
+  const bool active = gid < (long long)P.npairs * N2;     // same for both lanes of a pencil
+  const int p = active ? (int)(gid / N2) : 0;
+  const int f = active ? (int)(gid % N2) : 0;
+  C* s = P.S + (long long)p * N * N2 + f;
+  const C zero = cmk<C>(R(0), R(0));
+  C a[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) a[m] = active ? s[(long long)(2 * m + h) * N2] : zero;
+  dft<M, N, false, R>(a, P.tw);                            // E (lane 0) or O (lane 1)
+#pragma unroll
+  for (int k = 0; k < M; ++k) {                            // lane 1: w^k O[k]
+    const C t = twiddle<N, N, false, R>(a[k], k, P.tw);
+    a[k] = h ? t : a[k];
+  }
+  C y[M];                                                  // y[j] = Y[hH + j], y[H + j] = Y[hH + j + M]
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const C recv = shfl_pair(h ? a[j] : a[H + j]);
+    const C ev = h ? recv : a[j];
+    const C od = h ? a[H + j] : recv;
+    y[j] = cadd(ev, od);
+    y[H + j] = csub(ev, od);
+  }
+  R acc = R(0);
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    const int kz = h * H + (j < H ? j : j - H + M);
+    const R k = P.Kt[kz * N2 + f];
+    if (mode != 0) acc += k * (y[j].x * y[j].x + y[j].y * y[j].y);
+    y[j] = cscale(y[j], k);
+  }
+  double e = 0.0;
+  if (mode != 0 && active) {
+    int l, r;
+    decode_pair(P.tiles, P.ntiles, p, l, r);
+    e = (l == r ? 1.0 : 2.0) * (double)acc;
+  }
+  if (mode != 1) {
+#pragma unroll
+    for (int j = 0; j < H; ++j) {                          // k = hH + j
+      const C sum = cadd(y[j], y[H + j]);
+      const C dif = twiddle<N, N, true, R>(csub(y[j], y[H + j]), h * H + j, P.tw);
+      const C recv = shfl_pair(h ? sum : dif);
+      a[j] = h ? recv : sum;                               // lane 0: the sums, lane 1: the differences
+      a[H + j] = h ? dif : recv;
+    }
+    dft<M, N, true, R>(a, P.tw);                           // x[2m + h] = a[m]
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) s[(long long)(2 * m + h) * N2] = a[m];
+    }
+  }
+  if (mode != 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if ((tid & 31) == 0) red[tid >> 5] = e;
+    __syncthreads();
+    if (tid == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < 8; ++w) sum += red[w];
+      P.Epart[blockIdx.x] += sum;                          // one block per slot
+    }
+  }
+}
+
 template <typename R, int N>
 __global__ void __launch_bounds__(256, 2)
 pass_b_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
@@ -740,7 +838,14 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
     }
   }
   mark(1);
-  if (mask & 2) launch_pdl(!L.no_pdl, pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
+  if (mask & 2) {
+    if constexpr (N >= 64) {
+      const unsigned sgrid = (unsigned)(((long long)b.npairs * N * N + kBSplitPencils - 1) / kBSplitPencils);
+      launch_pdl(!L.no_pdl, pass_b_split_kernel<R, N>, dim3(sgrid), dim3(256), 0, st, P, L.mode);
+    } else {
+      launch_pdl(!L.no_pdl, pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
+    }
+  }
   mark(2);
   if (L.mode == 1) {
     mark(3);
