@@ -564,6 +564,112 @@ pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
   }
 }
 
+// A length-N transform of a line held by two lanes (lanes 2q, 2q+1): lane h
+// holds the samples 2m + h in a[], and on return holds y[j] = Y[hN/4 + j] and
+// y[N/4 + j] = Y[hN/4 + j + N/2] (the forward or inverse DFT, unnormalised):
+// a DFT of N/2 per lane, the lane-1 twiddles w^{+-k}, one shuffle per value
+// and the radix-2 combine (decimation in time).
+template <int N, bool INV, typename R>
+__device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)[N / 2], int h,
+                                               const TwTable<R, N>& tw) {
+  using C = cplx<R>;
+  constexpr int M = N / 2, H = N / 4;
+  dft<M, N, INV, R>(a, tw);
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    const C t = twiddle<N, N, INV, R>(a[k], k, tw);
+    a[k] = h ? t : a[k];
+  }
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const C recv = shfl_pair(h ? a[j] : a[H + j]);
+    const C ev = h ? recv : a[j];
+    const C od = h ? a[H + j] : recv;
+    y[j] = cadd(ev, od);
+    y[H + j] = csub(ev, od);
+  }
+}
+// Edges whose plane passes use the two-lane line transforms (one plane per block).
+template <typename R, int N> constexpr bool kSplitPlanes = sizeof(R) == 4 && N >= 96 && plane_items<R, N>() == 1;
+
+// frequency index held in y[j] by lane h
+template <int N> __device__ __forceinline__ int split_index(int j, int h) {
+  return h * (N / 4) + (j < N / 4 ? j : j - N / 4 + N / 2);
+}
+
+// Passes A and C for the largest edges (n >= 96), where a whole line per thread
+// needs over 200 registers: one plane per block, two lanes per line (2n
+// threads), each pass's two line transforms by split_line_dft, the transpose
+// through shared memory as in the one-thread-per-line form.
+template <typename R, int N, bool REAL>
+__global__ void __launch_bounds__(2 * N, 2)
+pass_a_split_kernel(const __grid_constant__ PairParams<R, N> P) {
+  using C = cplx<R>;
+  constexpr int M = N / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  griddep_launch();
+  const int tid = threadIdx.x, q = tid >> 1, h = tid & 1;
+  const long long item = blockIdx.x;                      // one (pair, z) plane per block
+  const int p = (int)(item / N), z = (int)(item % N);
+  int l, r;
+  decode_pair(P.tiles, P.ntiles, p, l, r);
+  C a[M], y[M];
+  {   // column x = q: samples y = 2m + h
+    const long long xo = (long long)l * P.ld + (long long)z * N * N + q;
+    const long long yo = (long long)r * P.ld + (long long)z * N * N + q;
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int yy = 2 * m + h;
+      a[m] = cmulc(load_vec<R, REAL>(P.X, xo + yy * N), load_vec<R, REAL>(P.Y, yo + yy * N));
+    }
+    split_line_dft<N, false, R>(a, y, h, P.tw);          // along y
+#pragma unroll
+    for (int j = 0; j < M; ++j) buf[split_index<N>(j, h) * (N + 1) + q] = y[j];
+  }
+  __syncthreads();
+  {   // row ky = q: samples x = 2m + h
+#pragma unroll
+    for (int m = 0; m < M; ++m) a[m] = buf[q * (N + 1) + 2 * m + h];
+    split_line_dft<N, false, R>(a, y, h, P.tw);          // along x
+    griddep_wait();                                        // the previous batch's pass D still reads S
+    C* out = P.S + ((long long)p * N + z) * N * N + q;
+#pragma unroll
+    for (int j = 0; j < M; ++j) out[(long long)split_index<N>(j, h) * N] = y[j];
+  }
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(2 * N, 2)
+pass_c_split_kernel(const __grid_constant__ PairParams<R, N> P) {
+  using C = cplx<R>;
+  constexpr int M = N / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  griddep_launch();
+  griddep_wait();
+  const int tid = threadIdx.x, q = tid >> 1, h = tid & 1;
+  const long long item = blockIdx.x;
+  const int p = (int)(item / N), z = (int)(item % N);
+  C* plane = P.S + ((long long)p * N + z) * N * N;
+  C a[M], y[M];
+  {   // row ky = q of the spectrum: samples kx = 2m + h, inverse along x
+#pragma unroll
+    for (int m = 0; m < M; ++m) a[m] = plane[(long long)(2 * m + h) * N + q];
+    split_line_dft<N, true, R>(a, y, h, P.tw);
+#pragma unroll
+    for (int j = 0; j < M; ++j) buf[q * (N + 1) + split_index<N>(j, h)] = y[j];   // row ky, column x
+  }
+  __syncthreads();
+  {   // column x = q: samples ky = 2m + h, inverse along y
+#pragma unroll
+    for (int m = 0; m < M; ++m) a[m] = buf[(2 * m + h) * (N + 1) + q];
+    split_line_dft<N, true, R>(a, y, h, P.tw);
+#pragma unroll
+    for (int j = 0; j < M; ++j) plane[(long long)split_index<N>(j, h) * N + q] = y[j];
+  }
+}
+
 template <typename R, int N>
 __global__ void __launch_bounds__(256, 2)
 pass_b_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
@@ -814,6 +920,12 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if constexpr (kSplitPlanes<R, N>) {
+      cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
     return true;
   }
   PairParams<R, N> P;
@@ -830,7 +942,9 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   const int mask = L.pass_mask ? L.pass_mask : 15;
   mark(0);
   if (mask & 1) {
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (kSplitPlanes<R, N>) {
+      launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, false>, dim3((unsigned)items), dim3(2 * N), smem, st, P);
+    } else if constexpr (sizeof(R) == 8) {
       if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
       else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
     } else {
@@ -852,7 +966,12 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
     mark(4);
     return true;
   }
-  if (mask & 4) launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
+  if (mask & 4) {
+    if constexpr (kSplitPlanes<R, N>)
+      launch_pdl(!L.no_pdl, pass_c_split_kernel<R, N>, dim3((unsigned)items), dim3(2 * N), smem, st, P);
+    else
+      launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
+  }
   mark(3);
   if (mask & 8) {
     if constexpr (sizeof(R) == 8) {
