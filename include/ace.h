@@ -73,11 +73,14 @@ typedef struct {
   int n;             /* grid points per edge (cubic grid n^3); see ace_supported_edge */
   double L[3];       /* cell edges Lx, Ly, Lz (bohr), > 0 */
   int n_occ;         /* N: number of exchange orbitals phi, >= 1 */
-  int dtype;         /* ace_dtype. R64/C128: FP64 throughout. C64: FP32 pair/FFT path and
-                        FP32 GEMMs, FP64 Cholesky and triangular inverse. */
+  int dtype;         /* ace_dtype. R64/C128: FP64 throughout. C64: FP32 pair/FFT path,
+                        GEMMs on TF32 tensor cores with a 3-term split (FP32
+                        accuracy; see ACE_FLAG_SIMT_GEMM), FP64 Cholesky and
+                        triangular inverse. */
   int kernel;        /* ace_kernel */
   double omega;      /* screening parameter (bohr^-1) for ACE_KERNEL_ERFC, > 0 */
-  double g0_value;   /* K(G=0) before alpha; NaN selects the default (0 bare, pi/omega^2 erfc) */
+  double g0_value;   /* K(G=0) before alpha; NaN selects the default (0 bare and kinetic,
+                        pi/omega^2 erfc) */
   double alpha;      /* overall kernel scale (1 = Hartree-Fock; 0.25 for PBE0/HSE fractions) */
   int max_pairs;     /* pair solves in flight per batch (0 = library default); sets the
                         size of the pair-spectrum scratch in the workspace */

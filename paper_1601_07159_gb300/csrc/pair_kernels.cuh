@@ -17,11 +17,15 @@
 //   pass D  (per point)     Out_r -= x_l v and, for symmetric tiles,
 //                           Out_l -= y_r conj(v); registers hold the tile's
 //                           orbitals and accumulators, one read-modify-write of
-//                           each output per tile, fixed summation order.
+//                           each output per tile, fixed summation order (full
+//                           off-diagonal tiles: two threads per point).
+// At the largest edges a line is held by two lanes instead of one thread
+// (split_line_dft): pass B from n = 64, passes A and C from n = 96.
 //
 // Two ways to run a schedule of batches:
 //  * four kernels per batch (pass_*_kernel), chained with programmatic
-//    dependent launch; used for per-pass timing;
+//    dependent launch, replayed from a CUDA graph (the default) or launched
+//    eagerly (per-pass timing);
 //  * one persistent launch (pair_engine_kernel): co-resident blocks take
 //    tasks (one pass-A/C block of planes, one pass-B block of pencils, one
 //    pass-D block of points) in schedule order from an atomic queue and wait,
@@ -32,7 +36,8 @@
 //
 // Tiles within a batch touch disjoint outputs (the schedule guarantees it) and
 // batches run in order, so the accumulation needs no atomics and the result is
-// bitwise reproducible and identical in both modes.
+// bitwise reproducible. The engine sums a full off-diagonal tile's left
+// outputs in one thread rather than two, so the two modes agree to rounding.
 #pragma once
 #include "ace_internal.h"
 #include "fft_reg.cuh"
