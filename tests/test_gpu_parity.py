@@ -394,3 +394,55 @@ def test_poisson_hartree_parity(ace, n, L, dtype, kernel, omega):
     if kernel == "bare":
         eh = 0.5 * s.dv * float(np.real(np.sum(np.conj(rho[0]) * _host(v)[0])))
         assert eh > 0
+
+
+def _gpu_orbitals(s, seed, ecut=synth.ECUT_HA):
+    """The synthetic recipe on the GPU for sizes a host QR cannot afford:
+    Gaussian-decaying complex coefficients on the sphere |G|^2/2 <= ecut, to
+    the grid by an inverse FFT, orthonormalised by a QR of sqrt(dV) Phi."""
+    n = s.n
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    m = torch.fft.fftfreq(n, d=1.0 / n, device="cuda", dtype=torch.float64) * (2 * math.pi / s.L)
+    g2 = m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2
+    decay = torch.where(0.5 * g2 <= ecut, torch.exp(-g2 / (2 * ecut)), torch.zeros_like(g2)).to(torch.float32)
+    phi = torch.empty((s.n_occ, n, n, n), dtype=torch.complex64, device="cuda")
+    for i in range(0, s.n_occ, 64):
+        k = min(64, s.n_occ - i)
+        c = torch.complex(torch.randn((k, n, n, n), generator=g, device="cuda"),
+                          torch.randn((k, n, n, n), generator=g, device="cuda")) * decay
+        phi[i:i + k] = torch.fft.ifftn(c, dim=(1, 2, 3)) * n ** 3
+    q, r = torch.linalg.qr(math.sqrt(s.dv) * phi.reshape(s.n_occ, -1).T)
+    q = q * torch.sgn(torch.diagonal(r).real)[None, :]
+    return (q.T / math.sqrt(s.dv)).contiguous().reshape(s.n_occ, n, n, n)
+
+
+def test_si512_full_size(ace):
+    """The large workload at full size (96^3, L = 41, N = 1024, screened
+    kernel, FP32 pairs, TF32 3-term GEMMs, FP64 Cholesky), default plan:
+    properties that hold at any size -- V_ACE Phi = W (Eq. ACEcond),
+    dV Xi^* Phi = -L^* (upper triangular), 1/2 tr M = -1/2 ||dV Xi^* Phi||^2
+    (Eq. EX_ACE) -- and sampled single pair solves on the full grid against the
+    FP64 oracle."""
+    s = synth.SI512_96
+    phi = _gpu_orbitals(s, synth.seed_for(5))
+    plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega)
+    out = plan.build(phi)
+    assert plan.status() == (0, 0)
+    vphi = plan.apply(out["Xi"], phi)
+    assert float(torch.linalg.vector_norm(vphi - out["W"]) / torch.linalg.vector_norm(out["W"])) < 1e-5
+    del vphi
+    a = s.dv * (out["Xi"].reshape(s.n_occ, -1).conj() @ phi.reshape(s.n_occ, -1).T).to(torch.complex128)
+    assert float(torch.linalg.norm(torch.tril(a, -1)) / torch.linalg.norm(a)) < 1e-5
+    ex = out["Ex"].item()
+    assert abs(-0.5 * float(torch.linalg.norm(a) ** 2) - ex) < 1e-5 * abs(ex)
+    assert ex < 0
+    del out, a
+    torch.cuda.empty_cache()
+    kern = oracle.coulomb_kernel((s.n,) * 3, (s.L,) * 3, s.kernel, s.omega)
+    one = ace.Plan(s.n, s.L, 1, dtype="c64", kernel=s.kernel, omega=s.omega)
+    for i, j in ((0, 1), (517, 1023), (900, 900)):
+        y = one.exchange_apply(phi[i:i + 1].contiguous(), phi[j:j + 1].contiguous())
+        pi = phi[i].cpu().numpy().astype(np.complex128)
+        pj = phi[j].cpu().numpy().astype(np.complex128)
+        ref = -pi * oracle.poisson((np.conj(pi) * pj)[None], kern)[0]
+        assert rel(_host(y)[0], ref) < 1e-6, (i, j)
