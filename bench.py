@@ -173,8 +173,28 @@ def oracle_step(phi, psi, kern, dv, cols):
                                      "t_apply_s": t_apply}
 
 
+def input_seed(rank):
+    """Seed of rank `rank`'s replica: every rank solves its own system."""
+    return synth.seed_for(2, rank)
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (ms); the time itself without a process group."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_step, steps, world, ms):
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return units_per_step * steps * world / (ms / 1e3)
+
+
 def make_inputs(s, rank=0):
-    seed = synth.seed_for(2, rank)
+    seed = input_seed(rank)
     phi = synth.orbitals(s, seed)
     psi = synth.targets(s, seed)
     return phi, psi
@@ -329,12 +349,9 @@ def run_ours(args):
     elapsed_ms = t_start.elapsed_time(t_end)
     build_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     apply_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     pairs = unique_pairs(s.n_occ)
-    value = pairs * K * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(pairs, K, world, elapsed_ms)
 
     # end to end through the public API: every step copies its inputs (Phi, Psi)
     # from pinned host memory and its results (Y, E_x) back. Streamed the way a
@@ -389,11 +406,8 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = pairs * Ke * world / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, dist, "cuda")
+    e2e_value = whole_job_rate(pairs, Ke, world, e2e_ms)
     h2d = phi_h.numel() * phi_h.element_size() + psi_h.numel() * psi_h.element_size()
     d2h = y_h.numel() * y_h.element_size() + 8
 
@@ -560,15 +574,14 @@ def run_batched(args):
     clk = clocks.stop()
     launches = sum(p.profile_end()["launches"] for p in plans)
     elapsed_ms = t0.elapsed_time(t1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     pairs = sum(unique_pairs(s.n_occ) for s in systems)
-    value = pairs * K * world / (elapsed_ms / 1e3)
+    value = whole_job_rate(pairs, K, world, elapsed_ms)
     # end to end: all Phi host -> device, the batch, all E_x back
     Ke = max(3, K // 5)
     ex_h = torch.empty(len(systems), dtype=torch.float64).pin_memory()
+    if dist:
+        dist.barrier()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -580,7 +593,7 @@ def run_batched(args):
         ex_h.copy_(ex, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     hbm, peak_kind = peaks()
     alg_bytes = sum(32.0 * s.ng * unique_pairs(s.n_occ) + 2.0 * s.n_occ * s.ng * 8 for s in systems)
     achieved = alg_bytes / (elapsed_ms / K / 1e3) / 1e9
@@ -602,7 +615,7 @@ def run_batched(args):
                              "alg_model": "sum over systems of 32 B/point/unique pair + Phi read + W write",
                              "ms_per_launch": elapsed_ms / K, "traffic": None},
                 "cpu_baseline": None,
-                "e2e": {"value": pairs * Ke / (e2e_ms / 1e3), "unit": UNIT,
+                "e2e": {"value": whole_job_rate(pairs, Ke, world, e2e_ms), "unit": UNIT,
                         "h2d_bytes_per_step": sum(h.numel() * h.element_size() for h in phis_h),
                         "d2h_bytes_per_step": 8 * len(systems), "steps": Ke},
                 "gpu_launches": launches, "clocks": clk}
