@@ -19,8 +19,8 @@
 //                           orbitals and accumulators, one read-modify-write of
 //                           each output per tile, fixed summation order (full
 //                           off-diagonal tiles: two threads per point).
-// At the largest edges a line is held by two lanes instead of one thread
-// (split_line_dft): pass B from n = 64, passes A and C from n = 96.
+// In FP32 at the larger edges a line is held by two lanes instead of one
+// thread (split_line_dft): passes A and C from n = 48, pass B from n = 64.
 //
 // Two ways to run a schedule of batches:
 //  * four kernels per batch (pass_*_kernel), chained with programmatic
@@ -594,20 +594,28 @@ __device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)
     y[H + j] = csub(ev, od);
   }
 }
-// Edges whose plane passes use the two-lane line transforms (one plane per block).
-template <typename R, int N> constexpr bool kSplitPlanes = sizeof(R) == 4 && N >= 96 && plane_items<R, N>() == 1;
+// FP32 edges whose plane passes use the two-lane line transforms (one plane
+// per block), and the blocks per SM their launch bounds ask for: at 48^3 the
+// half-length lines need 72-95 registers, so six 96-thread blocks (18-27 warps)
+// fit an SM where the one-thread-per-line form runs 15 warps at 117-128.
+// Below 48 the whole-line form is as fast (several planes per block).
+constexpr int kSplitMinEdge = 48;
+template <typename R, int N> constexpr bool kSplitPlanes = sizeof(R) == 4 && N >= kSplitMinEdge && N % 4 == 0;
+template <int N> constexpr int kSplitBlocks = N >= 96 ? 2 : 6;
+template <typename R, int N> constexpr size_t kSplitSmem = (size_t)N * (N + 1) * sizeof(cplx<R>);
 
 // frequency index held in y[j] by lane h
 template <int N> __device__ __forceinline__ int split_index(int j, int h) {
   return h * (N / 4) + (j < N / 4 ? j : j - N / 4 + N / 2);
 }
 
-// Passes A and C for the largest edges (n >= 96), where a whole line per thread
-// needs over 200 registers: one plane per block, two lanes per line (2n
-// threads), each pass's two line transforms by split_line_dft, the transpose
-// through shared memory as in the one-thread-per-line form.
+// Passes A and C with two lanes per line (FP32, n >= 48): one plane per block
+// (2n threads), each pass's two line transforms by split_line_dft, the
+// transpose through shared memory as in the one-thread-per-line form. Half the
+// registers of a whole line per thread (which at 96^3 would need over 200), so
+// more warps per SM hide the latency of the plane loads and stores.
 template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(2 * N, 2)
+__global__ void __launch_bounds__(2 * N, kSplitBlocks<N>)
 pass_a_split_kernel(const __grid_constant__ PairParams<R, N> P) {
   using C = cplx<R>;
   constexpr int M = N / 2;
@@ -645,7 +653,7 @@ pass_a_split_kernel(const __grid_constant__ PairParams<R, N> P) {
 }
 
 template <typename R, int N>
-__global__ void __launch_bounds__(2 * N, 2)
+__global__ void __launch_bounds__(2 * N, kSplitBlocks<N>)
 pass_c_split_kernel(const __grid_constant__ PairParams<R, N> P) {
   using C = cplx<R>;
   constexpr int M = N / 2;
@@ -926,8 +934,9 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
     cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if constexpr (kSplitPlanes<R, N>) {
-      cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      constexpr int s1 = (int)kSplitSmem<R, N>;
+      cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+      cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
       cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     }
@@ -948,7 +957,7 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   mark(0);
   if (mask & 1) {
     if constexpr (kSplitPlanes<R, N>) {
-      launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, false>, dim3((unsigned)items), dim3(2 * N), smem, st, P);
+      launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, false>, dim3((unsigned)items), dim3(2 * N), kSplitSmem<R, N>, st, P);
     } else if constexpr (sizeof(R) == 8) {
       if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
       else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
@@ -973,7 +982,7 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   }
   if (mask & 4) {
     if constexpr (kSplitPlanes<R, N>)
-      launch_pdl(!L.no_pdl, pass_c_split_kernel<R, N>, dim3((unsigned)items), dim3(2 * N), smem, st, P);
+      launch_pdl(!L.no_pdl, pass_c_split_kernel<R, N>, dim3((unsigned)items), dim3(2 * N), kSplitSmem<R, N>, st, P);
     else
       launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
   }
