@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-cufft", action="store_true", help="skip the cuFFT comparison")
     p.add_argument("--no-oversampled", action="store_true", help="skip the oversampled-build timing")
+    p.add_argument("--no-entries", action="store_true",
+                   help="skip the timings of the direct-energy and Poisson entry points")
     p.add_argument("--max-pairs", type=int, default=0, help="pair solves per batch (0 = plan default)")
     p.add_argument("--tile", type=int, default=0, help="orbitals per tile side (0 = plan default)")
     p.add_argument("--lanes", type=int, default=0, help="concurrent batch streams (0 = plan default)")
@@ -469,6 +471,30 @@ def run_ours(args):
                 "unique_pairs": unique_pairs(s.n_occ) + s.n_occ * 64, "status": code}
         del phi_all
 
+    # the direct energy (Eq. EX: passes A and B of every unique pair with the
+    # Parseval sum, no potentials) and the Poisson entry (V = sum_G K rho_hat
+    # e^{iG.r}, bare kernel, as for the Hartree potential) on the 192 bands
+    entries = None
+    if not args.no_entries:
+        def timed(f, reps=5):
+            f()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+        e_ms = timed(lambda: plan.energy_grad(phi_d))
+        pplan = ace.Plan(s.n, s.L, 1, dtype="c64", kernel="bare")
+        v_d = pplan.empty(s.n_bands)
+        p_ms = timed(lambda: pplan.poisson(psi_d, out=v_d))
+        entries = {"energy_direct": {"ms": e_ms, "unique_pairs": pairs, "pair_solves_per_s": pairs / (e_ms / 1e3)},
+                   "poisson": {"ms": p_ms, "vectors": s.n_bands, "solves_per_s": s.n_bands / (p_ms / 1e3),
+                               "kernel": "bare"}}
+        del pplan, v_d
+
     cufft = None
     if not args.no_cufft:
         w_ours = plan.build(phi_d)["W"]
@@ -502,6 +528,7 @@ def run_ours(args):
                              "ms_per_launch": pair_ms, "traffic": traffic, "passes": passes},
                 "cpu_baseline": cpu,
                 "cufft_baseline": cufft,
+                "entries": entries,
                 "oversampled": over,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": Ke},
