@@ -2,7 +2,9 @@
 // -M = L L^*, then Xi = W L^{-*} of Eq. Wtilde), blocked so that the FP64 work
 // spreads over many SMs (FP64 throughput per SM is low on this part).
 //
-// Blocks of NB = 32 columns. For panel p (rows/cols [p0, p0 + nb)):
+// Blocks of NB = 16 columns (the diagonal blocks run on one SM each, so they
+// are kept small; 32 measured slightly slower). For panel p (rows/cols
+// [p0, p0 + nb)):
 //   diag    one CTA: A_pp -> L_pp (right-looking Cholesky in shared memory,
 //           status word on a non-finite or non-positive pivot), D_p = L_pp^{-1}
 //           (recursive-doubling inverse of a triangular matrix); L_pp is
@@ -25,7 +27,7 @@ namespace ace {
 
 namespace {
 
-constexpr int NB = 32;   // panel width
+constexpr int NB = 16;   // panel width
 constexpr int TT = 16;   // output tile edge of the FP64 tile products
 
 __device__ __forceinline__ double2 zfma(double2 acc, double2 a, double2 b) {   // acc + a b
@@ -48,7 +50,7 @@ __global__ void neg_copy_kernel(const double2* __restrict__ M, long long count, 
   if (i < count) A[i] = make_double2(-M[i].x, -M[i].y);
 }
 
-// Factor and invert the diagonal block of panel p (nb <= NB); 1024 threads.
+// Factor and invert the diagonal block of panel p (nb <= NB); NB * NB threads.
 // The block is padded to NB with the identity, so every loop runs NB uniform
 // steps.
 // Cholesky on unscaled columns: step j subtracts a_ij conj(a_kj) / d_j from
@@ -63,8 +65,8 @@ __global__ void neg_copy_kernel(const double2* __restrict__ M, long long count, 
 // -> rounding). Afterwards L_jj = sqrt(d_j) and L_ij = a_ij / sqrt(d_j) in one
 // parallel pass.
 // Inverse by recursive doubling: for a lower-triangular [[A, 0], [B, C]],
-// the inverse is [[A^-1, 0], [-C^-1 (B A^-1), C^-1]]; five levels (block edge
-// 2, 4, ..., 32) of small products replace NB dependent column steps. The
+// the inverse is [[A^-1, 0], [-C^-1 (B A^-1), C^-1]]; log2 NB levels (block
+// edge 2, 4, ..., NB) of small products replace NB dependent column steps. The
 // intermediate B A^-1 is kept, transposed, in the unused upper triangle of X.
 __device__ __forceinline__ double recip_nr(double d) {
   if (!(d > 1e-30 && d < 1e30)) return 1.0 / d;   // outside FP32's comfortable range
@@ -76,7 +78,7 @@ __device__ __forceinline__ double recip_nr(double d) {
 
 constexpr int kTri = NB * (NB - 1) / 2;   // trailing-triangle elements (i >= k >= 1)
 
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(NB * NB)
 diag_kernel(double2* __restrict__ A, double2* __restrict__ X, int n, int p0, int nb, int* status) {
   __shared__ double2 a[NB][NB + 1];
   __shared__ double2 x[NB][NB + 1];
@@ -294,7 +296,7 @@ int launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int
   ++launches;
   for (int p0 = 0; p0 < n; p0 += NB) {
     const int nb = (p0 + NB <= n) ? NB : n - p0;
-    diag_kernel<<<1, 1024, 0, st>>>(A, X, n, p0, nb, status);
+    diag_kernel<<<1, NB * NB, 0, st>>>(A, X, n, p0, nb, status);
     ++launches;
     const int r0 = p0 + nb;
     if (r0 >= n) break;
