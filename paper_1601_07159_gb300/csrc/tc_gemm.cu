@@ -3,24 +3,30 @@
 //   gram   part[s][a][b] = sum_{g in chunk s} conj(A_a(g)) B_b(g)      (M = dV Phi^* W, C = dV Xi^* psi)
 //   outer  Out_b(g) = alpha sum_k A_k(g) C[k][b]                        (Xi = W L^{-*}, Y = -Xi C)
 //
-// Complex products as real GEMMs on interleaved (re, im) data:
-//   gram:  K' = 2 N_g real terms; output columns j < 64 take B_b as stored
-//          (re, im) -> Re conj(a) b; columns 64 + j take (im, -re) -> Im conj(a) b.
+// Complex products as real GEMMs on interleaved (re, im) data, for a tile of
+// BB = TN / 2 complex output columns b (MMA width N = TN real columns):
+//   gram:  K' = 2 N_g real terms; output columns j < BB take B_b as stored
+//          (re, im) -> Re conj(a) b; columns BB + j take (im, -re) -> Im conj(a) b.
 //   outer: rows = grid points g, K' = 2 K (re, im of A_k(g)); output columns
-//          j < 64 use (Re C, -Im C) -> Re Out, 64 + j use (Im C, Re C) -> Im Out.
+//          j < BB use (Re C, -Im C) -> Re Out, BB + j use (Im C, Re C) -> Im Out.
+// TN is 128, 192 or 256, chosen per call so that the b range is covered with
+// the fewest MMA columns (ties to the wider tile): a wider tile reads each A
+// row from shared memory once for more output columns, and the MMAs of the
+// 3-term split at N = 128 already ask for the whole shared-memory bandwidth.
 // FP32 accuracy from TF32 inputs: each operand is split x = hi + lo (hi = x with
 // the low 13 mantissa bits cleared, lo = x - hi exactly) and three products
 // hi.hi + hi.lo + lo.hi accumulate in FP32 in tensor memory (the lo.lo term is
 // below FP32 rounding).
 //
-// Per CTA (512 threads, one per SM): two 128 x 128 FP32 accumulators in TMEM
-// (256 columns). K runs in chunks of 32 real terms: the threads load chunk c+2
-// into registers while chunk c is split and stored, in the canonical K-major
-// no-swizzle layout (core matrices of 8 rows x 16 bytes; LBO = 128 B between
-// core matrices along K, SBO = 1024 B between 8-row groups; eight consecutive
-// threads fill one core matrix, so the 16-byte stores are free of bank
-// conflicts), into one of two shared-memory stages. One thread issues 4 K-steps
-// x 3 products of tcgen05.mma (M = 128, N = 128, K = 8) and commits them to the
+// Per CTA (512 threads, one per SM): two 128 x TN FP32 accumulators in TMEM.
+// K runs in chunks of 32 real terms: the threads load the next chunk(s) into
+// registers while the current one is split and stored, in the canonical
+// K-major no-swizzle layout (core matrices of 8 rows x 16 bytes; LBO = 128 B
+// between core matrices along K, SBO = 1024 B between 8-row groups; eight
+// consecutive threads fill one core matrix, so the 16-byte stores are free of
+// bank conflicts), into one of NSTAGE shared-memory stages (three of 64 KB at
+// TN = 128, two of 80 / 96 KB at TN = 192 / 256). One thread issues 4 K-steps
+// x 3 products of tcgen05.mma (M = 128, N = TN, K = 8) and commits them to the
 // stage's mbarrier; a stage is refilled only after its commit has been seen.
 //
 // The tensor core's FP32 accumulation truncates, so a long chain of MMAs into
@@ -42,20 +48,25 @@ namespace {
 
 constexpr int THREADS = 512;
 constexpr int TM = 128;                    // rows per CTA (M of the MMA)
-constexpr int TN = 128;                    // columns of one accumulator (N of the MMA)
-constexpr int TMEM_COLS = 2 * TN;          // two accumulators
 constexpr int KC = 32;                     // real K terms per stage
 constexpr int SBO = (KC / 4) * 128;        // bytes between 8-row groups = 1024
-constexpr int OP_BYTES = TM * KC * 4;      // one operand tile (128 x 32 FP32) = 16 KB
-constexpr int STAGE_BYTES = 4 * OP_BYTES;  // A_hi, A_lo, B_hi, B_lo = 64 KB
-constexpr int NSTAGE = 3;                  // shared-memory stages (chunk c uses stage c % NSTAGE)
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 64;
+constexpr int OPA_BYTES = TM * KC * 4;     // one A operand tile (128 x 32 FP32) = 16 KB
 constexpr int kGroup = 4;                  // chunks per accumulator group
 constexpr unsigned kWaitLimit = 1u << 24;
 
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
-                            ((uint32_t)(TM >> 4) << 24);
+template <int TN> struct Tile {
+  static_assert(TN == 128 || TN == 192 || TN == 256, "MMA width");
+  static constexpr int BB = TN / 2;                          // complex output columns per tile
+  static constexpr int NACC = TN / 4;                        // accumulator columns per thread
+  static constexpr int OPB_BYTES = TN * KC * 4;              // one B operand tile
+  static constexpr int STAGE_BYTES = 2 * OPA_BYTES + 2 * OPB_BYTES;   // A_hi, A_lo, B_hi, B_lo
+  static constexpr int NSTAGE = TN == 128 ? 3 : 2;           // chunk c uses stage c % NSTAGE
+  static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 64;
+  static constexpr int TMEM_COLS = TN == 128 ? 256 : 512;    // two accumulators, a power of two
+  // instruction descriptor: D = F32, A = B = TF32, both K-major, N = TN, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                                    ((uint32_t)(TM >> 4) << 24);
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -101,12 +112,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return false;
 }
 
+template <int TN>
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(Tile<TN>::IDESC), "r"(accumulate)
       : "memory");
 }
 
@@ -115,8 +127,9 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-// 32 consecutive accumulator columns of this thread's lane, added into acc
-__device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
+// 32 consecutive accumulator columns of this thread's lane, added into acc[o .. o + 31]
+template <int NACC>
+__device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[NACC], int o) {
   uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -129,28 +142,53 @@ __device__ __forceinline__ void tmem_add32(uint32_t taddr, float (&acc)[32]) {
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) acc[i] += __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) acc[o + i] += __uint_as_float(r[i]);
+}
+
+// 16 columns, added into acc[o .. o + 15]
+template <int NACC>
+__device__ __forceinline__ void tmem_add16(uint32_t taddr, float (&acc)[NACC], int o) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[o + i] += __uint_as_float(r[i]);
+}
+
+// this thread's NACC accumulator columns (32-column pieces, then a 16-column one)
+template <int NACC>
+__device__ __forceinline__ void tmem_add(uint32_t taddr, float (&acc)[NACC]) {
+#pragma unroll
+  for (int o = 0; o + 32 <= NACC; o += 32) tmem_add32<NACC>(taddr + (uint32_t)o, acc, o);
+  if constexpr (NACC % 32 == 16) tmem_add16<NACC>(taddr + (uint32_t)(NACC - 16), acc, NACC - 16);
 }
 
 struct TcState {
   uint64_t* bar;        // [NSTAGE] stage barriers
   uint32_t* tmem_slot;  // TMEM base address written by tcgen05.alloc
-  unsigned char* stage; // NSTAGE stages of 64 KB
+  unsigned char* stage; // NSTAGE stages
 };
 
+template <int TN>
 __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
+  using T = Tile<TN>;
   TcState s;
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
   s.stage = base;
-  s.bar = reinterpret_cast<uint64_t*>(base + NSTAGE * STAGE_BYTES);
-  s.tmem_slot = reinterpret_cast<uint32_t*>(base + NSTAGE * STAGE_BYTES + 32);
+  s.bar = reinterpret_cast<uint64_t*>(base + T::NSTAGE * T::STAGE_BYTES);
+  s.tmem_slot = reinterpret_cast<uint32_t*>(base + T::NSTAGE * T::STAGE_BYTES + 32);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NSTAGE; ++i) mbar_init(&s.bar[i], 1);
+    for (int i = 0; i < T::NSTAGE; ++i) mbar_init(&s.bar[i], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (threadIdx.x < 32) {   // warp 0 allocates the two accumulators
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s.tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(T::TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -160,41 +198,47 @@ __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
   return s;
 }
 
+template <int TN>
 __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Tile<TN>::TMEM_COLS)
+                 : "memory");
 }
 
 // One K chunk in a stage: 4 K-steps x 3 split products into accumulator `dtmem`,
 // committed to `bar`.
+template <int TN>
 __device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char* st, uint64_t* bar, bool first) {
-  const uint32_t ah = smem_u32(st), al = ah + OP_BYTES, bh = ah + 2 * OP_BYTES, bl = ah + 3 * OP_BYTES;
+  const uint32_t ah = smem_u32(st), al = ah + OPA_BYTES, bh = ah + 2 * OPA_BYTES, bl = bh + Tile<TN>::OPB_BYTES;
 #pragma unroll
   for (int ks = 0; ks < KC / 8; ++ks) {
     const uint32_t o = ks * 256;   // two core matrices of 16 B along K per step
-    mma_tf32(dtmem, mat_desc(ah + o), mat_desc(bh + o), (first && ks == 0) ? 0u : 1u);
-    mma_tf32(dtmem, mat_desc(ah + o), mat_desc(bl + o), 1u);
-    mma_tf32(dtmem, mat_desc(al + o), mat_desc(bh + o), 1u);
+    mma_tf32<TN>(dtmem, mat_desc(ah + o), mat_desc(bh + o), (first && ks == 0) ? 0u : 1u);
+    mma_tf32<TN>(dtmem, mat_desc(ah + o), mat_desc(bl + o), 1u);
+    mma_tf32<TN>(dtmem, mat_desc(al + o), mat_desc(bh + o), 1u);
   }
   mma_commit(bar);
 }
 
 // Main loop shared by both kernels: load(c, regs) fetches chunk c from global
-// memory, store(stage, regs) splits it into the stage. On return thread
-// (warp w, lane) holds acc[j] = D[row 32 (w % 4) + lane][col 32 (w / 4) + j].
-// Each thread waits (bounded) for the commit of the chunk that last used a
-// stage before storing into it, and drains a finished accumulator group when
-// that commit is the group's last; one block barrier per chunk hands the
-// stage to the issuing thread. A lost wait sets s_fail, which every thread
-// reads after that barrier, so all leave the loop together.
-template <typename Regs, typename Load, typename Store>
-__device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks, float (&acc)[32],
-                                            Load load, Store store) {
+// memory, store(stage, regs) splits it into the stage. Chunks are fetched
+// NSTAGE - 1 ahead (two register sets in flight at TN = 128, one otherwise).
+// On return thread (warp w, lane) holds acc[j] = D[row 32 (w % 4) + lane][col
+// NACC (w / 4) + j]. Each thread waits (bounded) for the commit of the chunk
+// that last used a stage before storing into it, and drains a finished
+// accumulator group when that commit is the group's last; one block barrier
+// per chunk hands the stage to the issuing thread. A lost wait sets s_fail,
+// which every thread reads after that barrier, so all leave the loop together.
+template <int TN, typename Regs, typename Load, typename Store>
+__device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks,
+                                            float (&acc)[Tile<TN>::NACC], Load load, Store store) {
+  using T = Tile<TN>;
+  constexpr int NS = T::NSTAGE;
   const int tid = threadIdx.x, w = tid >> 5;
-  const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + 32 * (w >> 2);
+  const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(T::NACC * (w >> 2));
   __shared__ int s_fail;
   // per-stage state in registers: bit s of `phase` / `issued` (commit on the
   // stage not yet seen), two bits per stage of `drain` (1 + accumulator buffer
@@ -202,7 +246,7 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
   unsigned phase = 0, issued = 0, drain = 0;
   bool ok = true;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  for (int j = 0; j < T::NACC; ++j) acc[j] = 0.f;
   if (tid == 0) s_fail = 0;
   __syncthreads();
 
@@ -217,64 +261,88 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
     const unsigned d = (drain >> (2 * s)) & 3u;
     if (d) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      tmem_add32(tmem + lane_col + (uint32_t)(TN * (d - 1)), acc);
+      tmem_add<T::NACC>(tmem + lane_col + (uint32_t)(TN * (d - 1)), acc);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       drain &= ~(3u << (2 * s));
     }
     return true;
   };
-
-  Regs r0, r1, r2;   // chunks c, c + 1, c + 2 (rotated by register moves)
-  if (nchunks > 0) load(0, r0);
-  if (nchunks > 1) load(1, r1);
-  int s = 0;
-  for (int c = 0; c < nchunks; ++c) {
-    unsigned char* st = S.stage + s * STAGE_BYTES;
-    if (c + 2 < nchunks) load(c + 2, r2);
+  // chunk c from registers into its stage, then the MMAs; false once a wait was lost
+  auto step = [&](int c, int s, const Regs& cur) -> bool {
+    unsigned char* st = S.stage + s * T::STAGE_BYTES;
     if ((issued >> s) & 1u) settle(s);   // the MMAs of chunk c - NSTAGE read this stage
-    store(st, r0);
-    r0 = r1;
-    r1 = r2;
+    store(st, cur);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (s_fail) {
-      ok = false;
-      break;
-    }
+    if (s_fail) return false;
     const int group = c / kGroup;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      issue_chunk(tmem + (uint32_t)(TN * (group & 1)), st, &S.bar[s], (c % kGroup) == 0);
+      issue_chunk<TN>(tmem + (uint32_t)(TN * (group & 1)), st, &S.bar[s], (c % kGroup) == 0);
     }
     issued |= 1u << s;
     if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) drain |= (1u + (unsigned)(group & 1)) << (2 * s);
-    s = s + 1 == NSTAGE ? 0 : s + 1;
+    return true;
+  };
+
+  int s = 0;
+  if constexpr (NS == 3) {
+    Regs r0, r1, r2;   // chunks c, c + 1, c + 2 (rotated by register moves)
+    if (nchunks > 0) load(0, r0);
+    if (nchunks > 1) load(1, r1);
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 2 < nchunks) load(c + 2, r2);
+      if (!step(c, s, r0)) {
+        ok = false;
+        break;
+      }
+      r0 = r1;
+      r1 = r2;
+      s = s + 1 == NS ? 0 : s + 1;
+    }
+  } else {
+    Regs r0, r1;       // chunks c, c + 1
+    if (nchunks > 0) load(0, r0);
+    for (int c = 0; c < nchunks; ++c) {
+      if (c + 1 < nchunks) load(c + 1, r1);
+      if (!step(c, s, r0)) {
+        ok = false;
+        break;
+      }
+      r0 = r1;
+      s = s + 1 == NS ? 0 : s + 1;
+    }
   }
   // remaining commits, in chunk order (bounded; also after a lost wait)
-  for (int i = 0; i < NSTAGE; ++i) {
+  for (int i = 0; i < NS; ++i) {
     if (((issued >> s) & 1u) && !settle(s)) ok = false;
-    s = s + 1 == NSTAGE ? 0 : s + 1;
+    s = s + 1 == NS ? 0 : s + 1;
   }
   __syncthreads();
   return ok && !s_fail;
 }
 
 // ---------------------------------------------------------------- gram
-// Grid: (ceil(na/128), ceil(nb/64), splits). part is FP64 complex [splits][na][nb].
-// Chunk element e (A: 0..1023, B: 0..511) -> row 8 (e / 64) + e % 8, complex
+// Grid: (ceil(na/128), ceil(nb/BB), splits). part is FP64 complex [splits][na][nb].
+// Chunk element e (A: 0..1023, B: 0..8 BB - 1) -> row 8 (e / 64) + e % 8, complex
 // pair (e / 8) % 8 (four real K terms).
+template <int TN>
 __global__ void __launch_bounds__(THREADS, 1)
 gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ B, int nb, long long ld,
                long long ng, double* __restrict__ part, long long chunk, int* status) {
+  using T = Tile<TN>;
+  constexpr int BB = T::BB, NACC = T::NACC;
+  constexpr int NBE = 8 * BB;                           // B float4 elements per chunk
+  constexpr int NBT = (NBE + THREADS - 1) / THREADS;    // per thread
   extern __shared__ unsigned char smem_raw[];
-  TcState S = tc_setup(smem_raw);
+  TcState S = tc_setup<TN>(smem_raw);
   const uint32_t tmem = *S.tmem_slot;
   const int tid = threadIdx.x;
-  const int a0 = blockIdx.x * TM, b0 = blockIdx.y * 64;
+  const int a0 = blockIdx.x * TM, b0 = blockIdx.y * BB;
   const long long g_begin = (long long)blockIdx.z * chunk;
   const long long g_end = g_begin + chunk < ng ? g_begin + chunk : ng;
   const int nchunks = g_end > g_begin ? (int)((g_end - g_begin + KC / 2 - 1) / (KC / 2)) : 0;
-  struct Regs { float4 a[2], b; };
+  struct Regs { float4 a[2], b[NBT]; };
   auto rowq = [](int e, int& r, int& q) { r = ((e >> 6) << 3) | (e & 7); q = (e >> 3) & 7; };
   auto load = [&](int c, Regs& Rg) {
     const long long g0 = g_begin + (long long)c * (KC / 2);
@@ -287,59 +355,76 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
                     ? *reinterpret_cast<const float4*>(A + (long long)(a0 + r) * ld + g)
                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    int r, q;
-    rowq(tid, r, q);
-    const long long g = g0 + 2 * q;
-    Rg.b = (b0 + r < nb && g < g_end) ? *reinterpret_cast<const float4*>(B + (long long)(b0 + r) * ld + g)
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) {
+      const int e = tid + THREADS * i;
+      int r, q;
+      rowq(e, r, q);
+      const long long g = g0 + 2 * q;
+      Rg.b[i] = (e < NBE && b0 + r < nb && g < g_end)
+                    ? *reinterpret_cast<const float4*>(B + (long long)(b0 + r) * ld + g)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
   };
   auto store = [&](unsigned char* st, const Regs& Rg) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       int r, q;
       rowq(tid + THREADS * i, r, q);
-      split_store(st, st + OP_BYTES, tile_off(r, 4 * q), Rg.a[i]);
+      split_store(st, st + OPA_BYTES, tile_off(r, 4 * q), Rg.a[i]);
     }
-    int r, q;
-    rowq(tid, r, q);
-    const float4 vb = Rg.b;
-    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r, 4 * q), vb);
-    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(r + 64, 4 * q),
-                make_float4(vb.y, -vb.x, vb.w, -vb.z));
+    unsigned char* bh = st + 2 * OPA_BYTES;
+    unsigned char* bl = bh + T::OPB_BYTES;
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) {
+      const int e = tid + THREADS * i;
+      if (e < NBE) {
+        int r, q;
+        rowq(e, r, q);
+        const float4 vb = Rg.b[i];
+        split_store(bh, bl, tile_off(r, 4 * q), vb);
+        split_store(bh, bl, tile_off(r + BB, 4 * q), make_float4(vb.y, -vb.x, vb.w, -vb.z));
+      }
+    }
   };
-  float acc[32];
-  const bool ok = tc_mainloop<Regs>(S, tmem, nchunks, acc, load, store);
+  float acc[NACC];
+  const bool ok = tc_mainloop<TN, Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -1;
   }
   const int w = tid >> 5, lane = tid & 31;
   const int a = a0 + 32 * (w & 3) + lane;
-  const int ri = (w >> 2) >> 1, bq = ((w >> 2) & 1) * 32;   // columns 0-63 real, 64-127 imaginary
+  const int ri = (w >> 2) >> 1, bq = ((w >> 2) & 1) * NACC;   // column blocks 0-1 real, 2-3 imaginary
   if (ok && a < na) {
     double* out = part + ((long long)blockIdx.z * na + a) * nb * 2 + ri;
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
+    for (int j = 0; j < NACC; ++j)
       if (b0 + bq + j < nb) out[2 * (b0 + bq + j)] = (double)acc[j];
   }
-  tc_teardown(tmem);
+  tc_teardown<TN>(tmem);
 }
 
 // ---------------------------------------------------------------- outer
-// Grid: (ceil(nb/64), ceil(ng/128)). C: FP64 complex [nk][nb].
+// Grid: (ceil(nb/BB), ceil(ng/128)). C: FP64 complex [nk][nb].
 // A element e (0..1023): grid point g0 + e % 128, K pair e / 128 (k = 2 (e / 128)).
-// B element e (0..511): b = b0 + e % 64, K pair e / 64.
+// B element e (0..8 BB - 1): b = b0 + e % BB, K pair e / BB.
+template <int TN>
 __global__ void __launch_bounds__(THREADS, 1)
 outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
                 long long ng, double alpha, float* __restrict__ Out, int* status) {
+  using T = Tile<TN>;
+  constexpr int BB = T::BB, NACC = T::NACC;
+  constexpr int NBE = 8 * BB;
+  constexpr int NBT = (NBE + THREADS - 1) / THREADS;
   extern __shared__ unsigned char smem_raw[];
-  TcState S = tc_setup(smem_raw);
+  TcState S = tc_setup<TN>(smem_raw);
   const uint32_t tmem = *S.tmem_slot;
   const int tid = threadIdx.x;
-  const int b0 = blockIdx.x * 64;
+  const int b0 = blockIdx.x * BB;
   const long long g0 = (long long)blockIdx.y * TM;
   const int nchunks = (nk + KC / 2 - 1) / (KC / 2);
-  struct Regs { float4 a[2], c; };
+  struct Regs { float4 a[2], c[NBT]; };
   auto load = [&](int c, Regs& Rg) {
     const int k0 = c * (KC / 2);
 #pragma unroll
@@ -353,48 +438,58 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
       }
       Rg.a[i] = v;
     }
-    const int j = tid & 63, k = k0 + 2 * (tid >> 6);
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (b0 + j < nb) {
-      if (k < nk) {
-        const long long o = 2 * ((long long)k * nb + b0 + j);
-        v.x = (float)C[o];
-        v.y = (float)C[o + 1];
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) {
+      const int e = tid + THREADS * i, j = e % BB, k = k0 + 2 * (e / BB);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < NBE && b0 + j < nb) {
+        if (k < nk) {
+          const long long o = 2 * ((long long)k * nb + b0 + j);
+          v.x = (float)C[o];
+          v.y = (float)C[o + 1];
+        }
+        if (k + 1 < nk) {
+          const long long o = 2 * ((long long)(k + 1) * nb + b0 + j);
+          v.z = (float)C[o];
+          v.w = (float)C[o + 1];
+        }
       }
-      if (k + 1 < nk) {
-        const long long o = 2 * ((long long)(k + 1) * nb + b0 + j);
-        v.z = (float)C[o];
-        v.w = (float)C[o + 1];
-      }
+      Rg.c[i] = v;   // (Re C_k, Im C_k, Re C_k+1, Im C_k+1)
     }
-    Rg.c = v;   // (Re C_k, Im C_k, Re C_k+1, Im C_k+1)
   };
   auto store = [&](unsigned char* st, const Regs& Rg) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int e = tid + THREADS * i, r = e & 127, kq = 4 * (e >> 7);
-      split_store(st, st + OP_BYTES, tile_off(r, kq), Rg.a[i]);
+      split_store(st, st + OPA_BYTES, tile_off(r, kq), Rg.a[i]);
     }
-    const int j = tid & 63, kq = 4 * (tid >> 6);
-    const float4 v = Rg.c;
-    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j, kq), make_float4(v.x, -v.y, v.z, -v.w));
-    split_store(st + 2 * OP_BYTES, st + 3 * OP_BYTES, tile_off(j + 64, kq), make_float4(v.y, v.x, v.w, v.z));
+    unsigned char* bh = st + 2 * OPA_BYTES;
+    unsigned char* bl = bh + T::OPB_BYTES;
+#pragma unroll
+    for (int i = 0; i < NBT; ++i) {
+      const int e = tid + THREADS * i, j = e % BB, kq = 4 * (e / BB);
+      if (e < NBE) {
+        const float4 v = Rg.c[i];
+        split_store(bh, bl, tile_off(j, kq), make_float4(v.x, -v.y, v.z, -v.w));
+        split_store(bh, bl, tile_off(j + BB, kq), make_float4(v.y, v.x, v.w, v.z));
+      }
+    }
   };
-  float acc[32];
-  const bool ok = tc_mainloop<Regs>(S, tmem, nchunks, acc, load, store);
+  float acc[NACC];
+  const bool ok = tc_mainloop<TN, Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -2;
   }
   const int w = tid >> 5, lane = tid & 31;
   const long long g = g0 + 32 * (w & 3) + lane;
-  const int ri = (w >> 2) >> 1, bq = ((w >> 2) & 1) * 32;
+  const int ri = (w >> 2) >> 1, bq = ((w >> 2) & 1) * NACC;
   if (ok && g < ng) {
 #pragma unroll
-    for (int j = 0; j < 32; ++j)
+    for (int j = 0; j < NACC; ++j)
       if (b0 + bq + j < nb) Out[2 * ((long long)(b0 + bq + j) * ld + g) + ri] = (float)alpha * acc[j];
   }
-  tc_teardown(tmem);
+  tc_teardown<TN>(tmem);
 }
 
 // Exact diagonal of the gram product: Mc[a][a] = (scale Re sum_g conj(A_a) B_a, 0),
@@ -436,16 +531,40 @@ __global__ void diag_fix_kernel(const double* __restrict__ part, int na, double 
   Mc[2 * ((long long)a * na + a) + 1] = 0.0;
 }
 
+// MMA width for nb output columns: the fewest MMA columns over the b tiles,
+// ties to the wider tile.
+int tc_width(int nb) {
+  int best = 256;
+  long long cost = -1;
+  for (const int tn : {256, 192, 128}) {
+    const long long c = (long long)((nb + tn / 2 - 1) / (tn / 2)) * tn;
+    if (cost < 0 || c < cost) {
+      cost = c;
+      best = tn;
+    }
+  }
+  return best;
+}
+
+template <int TN> void set_smem(const void* k) {
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<TN>::SMEM_BYTES);
+}
+
 }  // namespace
 
 bool tc_gemm_prepare() {
-  cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-  cudaFuncSetAttribute(outer_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  set_smem<128>((const void*)gram_tc_kernel<128>);
+  set_smem<192>((const void*)gram_tc_kernel<192>);
+  set_smem<256>((const void*)gram_tc_kernel<256>);
+  set_smem<128>((const void*)outer_tc_kernel<128>);
+  set_smem<192>((const void*)outer_tc_kernel<192>);
+  set_smem<256>((const void*)outer_tc_kernel<256>);
   return cudaGetLastError() == cudaSuccess;
 }
 
 int gram_tc_splits(long long ng, int na, int nb) {
-  const long long tiles = (long long)((na + TM - 1) / TM) * ((nb + 63) / 64);
+  const int bb = tc_width(nb) / 2;
+  const long long tiles = (long long)((na + TM - 1) / TM) * ((nb + bb - 1) / bb);
   long long s = 152 / tiles;   // one wave of one CTA per SM
   const long long max_s = (ng + KC / 2 - 1) / (KC / 2);
   if (s > max_s) s = max_s;
@@ -457,16 +576,24 @@ void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, 
                     int splits, int* status, cudaStream_t st) {
   long long chunk = (ng + splits - 1) / splits;
   chunk = (chunk + KC / 2 - 1) / (KC / 2) * (KC / 2);
-  const dim3 grid((na + TM - 1) / TM, (nb + 63) / 64, splits);
-  gram_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(static_cast<const float2*>(A), na,
-                                                    static_cast<const float2*>(B), nb, ld, ng, part, chunk, status);
+  const int tn = tc_width(nb), bb = tn / 2;
+  const dim3 grid((na + TM - 1) / TM, (nb + bb - 1) / bb, splits);
+  const float2* a = static_cast<const float2*>(A);
+  const float2* b = static_cast<const float2*>(B);
+  if (tn == 256) gram_tc_kernel<256><<<grid, THREADS, Tile<256>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
+  else if (tn == 192) gram_tc_kernel<192><<<grid, THREADS, Tile<192>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
+  else gram_tc_kernel<128><<<grid, THREADS, Tile<128>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
 }
 
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
                      void* Out, int* status, cudaStream_t st) {
-  const dim3 grid((nb + 63) / 64, (unsigned)((ng + TM - 1) / TM));
-  outer_tc_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(static_cast<const float2*>(A), nk, C, nb, ld, ng, alpha,
-                                                     static_cast<float*>(Out), status);
+  const int tn = tc_width(nb), bb = tn / 2;
+  const dim3 grid((nb + bb - 1) / bb, (unsigned)((ng + TM - 1) / TM));
+  const float2* a = static_cast<const float2*>(A);
+  float* o = static_cast<float*>(Out);
+  if (tn == 256) outer_tc_kernel<256><<<grid, THREADS, Tile<256>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
+  else if (tn == 192) outer_tc_kernel<192><<<grid, THREADS, Tile<192>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
+  else outer_tc_kernel<128><<<grid, THREADS, Tile<128>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
 }
 
 size_t diag_dot_part_doubles(int na) { return (size_t)na * kDiagSplits; }
