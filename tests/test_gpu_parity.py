@@ -192,6 +192,33 @@ def test_tensor_core_gemms_match_cuda_cores(ace, n, L, nocc, nb):
     assert tc.status() == (0, 0)
 
 
+@pytest.mark.parametrize("nocc,nb", [(100, 64), (20, 96), (20, 128), (150, 150), (20, 200), (20, 257)])
+def test_tensor_core_tile_widths(ace, nocc, nb):
+    """The tensor-core GEMMs pick an MMA width of 128, 192 or 256 columns per
+    call (tiles of 64, 96 or 128 complex columns): n_b = 64 -> 128, 96 and 150
+    and 257 -> 192, 128 and 200 -> 256, N = 100 -> 256 and N = 150 -> 192 for
+    M and Xi, full and partial last tiles. M, Xi and the apply against the FP64
+    oracle and the CUDA-core GEMMs."""
+    n, L = 16, 8.0
+    s, phi, psi, kern = _inputs(n, L, nocc, nb, "c64", "bare", 0.0, seed=57)
+    ref = oracle.ace_build(phi, kern, s.dv)
+    phi_d, psi_d = _dev(phi, "c64", ace), _dev(psi, "c64", ace)
+    tc = ace.Plan(n, L, nocc, dtype="c64", kernel="bare")
+    simt = ace.Plan(n, L, nocc, dtype="c64", kernel="bare", tensor_cores=False)
+    a, b = tc.build(phi_d), simt.build(phi_d)
+    assert tc.status() == (0, 0) and simt.status() == (0, 0)
+    assert rel(_host(a["M"]), ref["M"]) < 1e-5
+    assert rel(_host(a["Xi"]), ref["Xi"]) < 1e-5
+    assert rel(_host(a["Xi"]), _host(b["Xi"])) < 1e-5
+    xi_ref = _dev(ref["Xi"], "c64", ace)
+    y = tc.apply(xi_ref, psi_d)
+    y_simt = simt.apply(xi_ref, psi_d)
+    y_ref = oracle.ace_apply(ref["Xi"], psi, s.dv)
+    assert rel(_host(y), y_ref) < 1e-5
+    assert rel(_host(y), _host(y_simt)) < 1e-5
+    assert tc.status() == (0, 0)
+
+
 def test_single_orbital_and_empty(ace):
     s, phi, psi, kern = _inputs(16, 8.0, 1, 2, "c128", "erfc", 0.4, seed=9)
     plan = ace.Plan(16, 8.0, 1, dtype="c128", kernel="erfc", omega=0.4)
