@@ -574,12 +574,12 @@ long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* X
   const int splits = gram_parts(p, N, N);
   if (p->tc) launch_gram_tc(Phi, N, W, N, p->ng, p->ng, Wl.part, splits, p->status, cs);
   else launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
-  launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
+  const int kr = launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
   if (p->tc) launch_diag_exact(Phi, W, N, p->ng, p->ng, p->dv, Wl.part, p->Mc, cs);
   const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
   if (p->tc) launch_outer_tc(W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi, p->status, cs);
   else launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi, cs);
-  return 2 + (p->tc ? 2 : 0) + kc + 1;
+  return 1 + kr + (p->tc ? 2 : 0) + kc + 1;
 }
 
 // One captured graph per batch of systems (ace_build_batched), shared by all
@@ -922,12 +922,12 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
     const int splits = gram_parts(p, n_phi, n_phi);
     if (p->tc) launch_gram_tc(Phi, n_phi, W, n_phi, p->ng, p->ng, Wl.part, splits, p->status, cs);
     else launch_gram(p->f64, p->real, Phi, n_phi, W, n_phi, p->ng, p->ng, Wl.part, splits, cs);
-    launch_gram_reduce(Wl.part, splits, n_phi, n_phi, p->dv, true, false, Wl.Cm, nullptr, cs);
+    const int kr = launch_gram_reduce(Wl.part, splits, n_phi, n_phi, p->dv, true, false, Wl.Cm, nullptr, cs);
     if (p->tc) launch_diag_exact(Phi, W, n_phi, p->ng, p->ng, p->dv, Wl.part, Wl.Cm, cs);
     const int kc = launch_cholesky_inv(Wl.Cm, n_phi, Wl.work, Wl.LinvH, p->status, cs);
     if (p->tc) launch_outer_tc(W, n_phi, Wl.LinvH, n_phi, p->ng, p->ng, 1.0, Xi_out, p->status, cs);
     else launch_outer(p->f64, p->real, W, n_phi, Wl.LinvH, n_phi, p->ng, p->ng, 1.0, Xi_out, cs);
-    return 2 + (p->tc ? 2 : 0) + kc + 1;
+    return 1 + kr + (p->tc ? 2 : 0) + kc + 1;
   });
   if (s != ACE_OK) return s;
   p->launches += launch_m_outputs(Wl.Cm, n_phi, p->real, M_out, Ex_out, st, N);

@@ -97,8 +97,8 @@ int energy_blocks(int n, int npairs, bool f64);
 void launch_gram(bool f64, bool real_in, const void* A, int na, const void* B, int nb, long long ld,
                  long long ng, double* part, int splits, cudaStream_t st);
 int gram_splits(long long ng, int na, int nb);
-void launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
-                        bool real_out, double* out, double* out_trace_half, cudaStream_t st);
+int launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
+                       bool real_out, double* out, double* out_trace_half, cudaStream_t st);
 void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C, int nb,
                   long long ld, long long ng, double alpha, void* Out, cudaStream_t st);
 // M_out (n x n) and Ex_out = 1/2 Re of the first n_trace diagonal entries (all if < 0).

@@ -124,35 +124,63 @@ void launch_gram(bool f64, bool real_in, const void* A, int na, const void* B, i
   }
 }
 
-// out[a][b] = scale * sum_s part[s][a][b]; hermitize -> (X + X^*)/2;
-// real_out -> imaginary parts dropped (real Gamma-point case).
-// out_trace_half (nullable) <- 1/2 Re tr(out) (computed by block (0,0)).
-__global__ void gram_reduce_kernel(const double* __restrict__ part, int splits, int na, int nb,
-                                   double scale, int hermitize, int real_out, double* __restrict__ out) {
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)na * nb) return;
-  const int a = (int)(idx / nb), b = (int)(idx % nb);
-  const long long stride = (long long)na * nb * 2;
-  double re = 0.0, im = 0.0;
-  for (int s = 0; s < splits; ++s) {
-    re += part[s * stride + 2 * idx];
-    im += part[s * stride + 2 * idx + 1];
-  }
-  if (hermitize) {
-    const long long t = (long long)b * nb + a;
-    double re2 = 0.0, im2 = 0.0;
-    for (int s = 0; s < splits; ++s) {
-      re2 += part[s * stride + 2 * t];
-      im2 += part[s * stride + 2 * t + 1];
+// out[a][b] = scale * sum_s part[s][a][b] (part: FP64 complex [splits][na][nb]);
+// real_out -> imaginary parts dropped (real Gamma-point case). A block sums 32
+// consecutive entries: warp y takes the splits s = y, y + 8, ..., with 16-byte
+// loads coalesced across the warp, and the eight partial sums meet in shared
+// memory in a fixed order, so the result does not depend on timing.
+constexpr int kRedGroups = 8;
+__global__ void __launch_bounds__(32 * kRedGroups)
+gram_reduce_kernel(const double* __restrict__ part, int splits, int na, int nb, double scale, int real_out,
+                   double* __restrict__ out) {
+  __shared__ double2 red[kRedGroups][32];
+  const int lane = threadIdx.x & 31, y = threadIdx.x >> 5;
+  const long long total = (long long)na * nb;
+  const long long idx = (long long)blockIdx.x * 32 + lane;
+  const double2* p2 = reinterpret_cast<const double2*>(part);
+  double2 acc = make_double2(0.0, 0.0);
+  if (idx < total)
+    for (int s = y; s < splits; s += kRedGroups) {
+      const double2 v = p2[(long long)s * total + idx];
+      acc.x += v.x;
+      acc.y += v.y;
     }
-    re = 0.5 * (re + re2);
-    im = 0.5 * (im - im2);
+  red[y][lane] = acc;
+  __syncthreads();
+  if (y != 0 || idx >= total) return;
+  double re = 0.0, im = 0.0;
+#pragma unroll
+  for (int k = 0; k < kRedGroups; ++k) {
+    re += red[k][lane].x;
+    im += red[k][lane].y;
   }
   if (real_out) {
     out[idx] = scale * re;
   } else {
     out[2 * idx] = scale * re;
     out[2 * idx + 1] = scale * im;
+  }
+}
+
+// out <- (out + out^*) / 2 for an n x n matrix, in place: the thread of entry
+// (a, b) with a <= b writes both (a, b) and (b, a).
+__global__ void hermitize_kernel(double* __restrict__ out, int n, int real_out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  const int a = (int)(e / n), b = (int)(e % n);
+  if (a > b) return;
+  const long long ab = (long long)a * n + b, ba = (long long)b * n + a;
+  if (real_out) {
+    const double h = 0.5 * (out[ab] + out[ba]);
+    out[ab] = h;
+    out[ba] = h;
+  } else {
+    const double re = 0.5 * (out[2 * ab] + out[2 * ba]);
+    const double im = 0.5 * (out[2 * ab + 1] - out[2 * ba + 1]);
+    out[2 * ab] = re;
+    out[2 * ab + 1] = im;
+    out[2 * ba] = re;
+    out[2 * ba + 1] = -im;
   }
 }
 
@@ -192,12 +220,21 @@ int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* 
   return k;
 }
 
-void launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
-                        bool real_out, double* out, double* out_trace_half, cudaStream_t st) {
+int launch_gram_reduce(const double* part, int splits, int na, int nb, double scale, bool hermitize,
+                       bool real_out, double* out, double* out_trace_half, cudaStream_t st) {
   const long long total = (long long)na * nb;
-  gram_reduce_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(part, splits, na, nb, scale,
-                                                                      hermitize, real_out, out);
-  if (out_trace_half) trace_half_kernel<<<1, 32, 0, st>>>(out, na, na, real_out, out_trace_half);
+  gram_reduce_kernel<<<(unsigned)((total + 31) / 32), 32 * kRedGroups, 0, st>>>(part, splits, na, nb, scale,
+                                                                              real_out ? 1 : 0, out);
+  int k = 1;
+  if (hermitize) {   // na == nb
+    hermitize_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(out, na, real_out ? 1 : 0);
+    ++k;
+  }
+  if (out_trace_half) {
+    trace_half_kernel<<<1, 32, 0, st>>>(out, na, na, real_out, out_trace_half);
+    ++k;
+  }
+  return k;
 }
 
 // ---------------------------------------------------------------- outer
