@@ -184,12 +184,16 @@ __global__ void hermitize_kernel(double* __restrict__ out, int n, int real_out) 
   }
 }
 
-// 1/2 Re of the sum of the first `count` diagonal entries of the n x n matrix m.
+// 1/2 Re of the sum of the first `count` diagonal entries of the n x n matrix m:
+// one warp, lane l summing the entries l, l + 32, ..., then a fixed shuffle tree.
 __global__ void trace_half_kernel(const double* __restrict__ m, int n, int count, int real, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
   double s = 0.0;
-  for (int k = 0; k < count; ++k) s += real ? m[(long long)k * n + k] : m[2 * ((long long)k * n + k)];
-  *out = 0.5 * s;
+  for (int k = lane; k < count; k += 32) s += real ? m[(long long)k * n + k] : m[2 * ((long long)k * n + k)];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) *out = 0.5 * s;
 }
 
 __global__ void m_copy_kernel(const double* __restrict__ mc, int n, int real, double* __restrict__ out) {
