@@ -494,14 +494,14 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
 
 // Exact diagonal of the gram product: Mc[a][a] = (scale Re sum_g conj(A_a) B_a, 0),
 // FP32 products summed in FP32 over short runs and in FP64 across them.
-// Grid: (na, kDiagSplits); part: FP64 [na][kDiagSplits].
+// Grid: (na, splits), splits <= kDiagSplits; part: FP64 [na][kDiagSplits].
 constexpr int kDiagSplits = 32;
 __global__ void __launch_bounds__(256)
 diag_dot_kernel(const float2* __restrict__ A, const float2* __restrict__ B, long long ld, long long ng,
                 double* __restrict__ part) {
   __shared__ double red[8];
   const int a = blockIdx.x;
-  const long long per = (ng + kDiagSplits - 1) / kDiagSplits;
+  const long long per = (ng + gridDim.y - 1) / gridDim.y;
   const long long g0 = blockIdx.y * per, g1 = g0 + per < ng ? g0 + per : ng;
   double s = 0.0;
   float run = 0.f;
@@ -522,11 +522,12 @@ diag_dot_kernel(const float2* __restrict__ A, const float2* __restrict__ B, long
   }
 }
 
-__global__ void diag_fix_kernel(const double* __restrict__ part, int na, double scale, double* __restrict__ Mc) {
+__global__ void diag_fix_kernel(const double* __restrict__ part, int na, int splits, double scale,
+                                double* __restrict__ Mc) {
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= na) return;
   double t = 0.0;
-  for (int k = 0; k < kDiagSplits; ++k) t += part[(long long)a * kDiagSplits + k];
+  for (int k = 0; k < splits; ++k) t += part[(long long)a * kDiagSplits + k];
   Mc[2 * ((long long)a * na + a)] = scale * t;
   Mc[2 * ((long long)a * na + a) + 1] = 0.0;
 }
@@ -600,9 +601,12 @@ size_t diag_dot_part_doubles(int na) { return (size_t)na * kDiagSplits; }
 
 void launch_diag_exact(const void* A, const void* B, int na, long long ld, long long ng, double scale,
                        double* part, double* Mc, cudaStream_t st) {
-  diag_dot_kernel<<<dim3(na, kDiagSplits), 256, 0, st>>>(static_cast<const float2*>(A),
-                                                         static_cast<const float2*>(B), ld, ng, part);
-  diag_fix_kernel<<<(na + 127) / 128, 128, 0, st>>>(part, na, scale, Mc);
+  // about two waves of 256-thread blocks (eight per SM), at most kDiagSplits per orbital
+  int splits = 2 * 152 * 8 / (na > 0 ? na : 1);
+  splits = splits < 4 ? 4 : (splits > kDiagSplits ? kDiagSplits : splits);
+  diag_dot_kernel<<<dim3(na, splits), 256, 0, st>>>(static_cast<const float2*>(A),
+                                                    static_cast<const float2*>(B), ld, ng, part);
+  diag_fix_kernel<<<(na + 127) / 128, 128, 0, st>>>(part, na, splits, scale, Mc);
 }
 
 }  // namespace ace
