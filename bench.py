@@ -418,9 +418,9 @@ def run_ours(args):
     ng = s.ng
     alg_bytes = 32.0 * ng * pairs + 2.0 * s.n_occ * ng * 8
     # DRAM bytes (read + write) of passes A-D per build from the warm ncu capture
-    # summarised in profiles/pair_passes_si64_48cube_n128.md: 222.9 MB per 64-pair
+    # summarised in profiles/pair_passes_si64_48cube_n128.md: 209.7 MB per 64-pair
     # batch x (120 + 8 x 72/64) batch equivalents; valid for the default plan.
-    traffic = 28.75e9 if (args.max_pairs, args.tile, args.eager, args.engine) == (0, 0, False, False) else None
+    traffic = 27.05e9 if (args.max_pairs, args.tile, args.eager, args.engine) == (0, 0, False, False) else None
     pair_ms = prof["pair_ms"] / K
     achieved = alg_bytes / (pair_ms / 1e3) / 1e9
     pass_alg = {"A": 8.0 * ng * pairs, "B": 16.0 * ng * pairs, "C": 16.0 * ng * pairs,

@@ -38,7 +38,7 @@ struct PairLaunch {
   void* OutX;            // accumulators for the l side (symmetric tiles)
   void* OutY;            // accumulators for the r side
   void* S;               // spectrum scratch, max_pairs * n^3 complex
-  const void* Kt;        // kernel table K(G) alpha / N_g, layout [kz][kx][ky]
+  const void* Kt;        // kernel table K(G) alpha / N_g, folded [kz][kx][ky] over 0..n/2 each
   double* Epart;         // per-block energy partials (nullable)
   double scale;          // Out -= scale * sum
   const double* tw;      // host FP64 twiddles exp(-2 pi i k/n), 2n doubles

@@ -122,6 +122,17 @@ __device__ __forceinline__ cplx<R> load_vec(const void* base, long long idx) {
   }
 }
 
+// The kernel table is folded (K depends on |G|^2 only): index k of an axis and
+// n - k share an entry. kfold(k) = min(k, N - k); the table is [kz][kx][ky] over
+// 0..N/2 each.
+template <int N> __host__ __device__ __forceinline__ constexpr int kfold(int k) { return k <= N / 2 ? k : N - k; }
+template <int N> constexpr int kKH = N / 2 + 1;
+// offset of the (kx, ky) pencil f = kx N + ky in the folded table
+template <int N> __device__ __forceinline__ int kt_pencil(int f) {
+  const int kx = f / N, ky = f - kx * N;
+  return kfold<N>(kx) * kKH<N> + kfold<N>(ky);
+}
+
 template <typename R, int N> __host__ __device__ constexpr int plane_items() {
   // items (pair, z-plane) per CTA of the plane kernels: ~256 threads, <= 96 KB
   constexpr int by_threads = (256 / N) > 0 ? (256 / N) : 1;
@@ -197,9 +208,10 @@ __device__ __forceinline__ void body_b(const PairParams<R, N>& P, const TileDesc
     for (int zz = 0; zz < N; ++zz) a[zz] = ldx<COH>(s + (long long)zz * N2);
     dft<N, N, false, R>(a, P.tw);
     R acc = R(0);
+    const R* kt = P.Kt + kt_pencil<N>(f);
 #pragma unroll
     for (int kz = 0; kz < N; ++kz) {
-      const R k = P.Kt[kz * N2 + f];
+      const R k = kt[kfold<N>(kz) * (kKH<N> * kKH<N>)];
       if (mode != 0) acc += k * (a[kz].x * a[kz].x + a[kz].y * a[kz].y);
       a[kz] = cscale(a[kz], k);
     }
@@ -528,10 +540,11 @@ pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
     y[H + j] = csub(ev, od);
   }
   R acc = R(0);
+  const R* kt = P.Kt + kt_pencil<N>(f);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const int kz = h * H + (j < H ? j : j - H + M);
-    const R k = P.Kt[kz * N2 + f];
+    const R k = kt[kfold<N>(kz) * (kKH<N> * kKH<N>)];
     if (mode != 0) acc += k * (y[j].x * y[j].x + y[j].y * y[j].y);
     y[j] = cscale(y[j], k);
   }
