@@ -13,6 +13,15 @@ Under torchrun each rank runs an independent replica (its own system): the
 work is partitioned into independent problems, no data-path collective;
 value = pairs over all ranks / max-over-ranks time ("scaling": "weak").
 --impl reference times the FP64 CPU oracle on this host (rank 0 only).
+--workload batched64_uneven times one ace_build_batched of 64 uneven systems
+per step instead.
+
+Besides the contract keys, the default line carries: ms per build and per
+apply, the pair pipeline's roofline with its per-pass split (eager runs), the
+end-to-end rate through pinned host buffers, the plain-FP64 build time, a
+cuFFT/torch W build (`cufft_baseline`), the direct-energy and Poisson entry
+points (`entries`), and an oversampled build (`oversampled`); the --no-*
+flags skip those extras.
 """
 from __future__ import annotations
 
