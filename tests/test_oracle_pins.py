@@ -283,3 +283,20 @@ def test_kinetic_kernel_plane_waves():
             assert np.max(np.abs(t)) < 1e-13
         else:
             assert rel(t, 0.5 * k2 * pw) < 1e-12
+
+
+@pytest.mark.parametrize("shape,lengths", [((8, 8, 8), (6.0, 6.0, 6.0)), ((8, 6, 5), (6.0, 5.0, 4.5))])
+def test_kernel_tables_reflection_symmetric(shape, lengths):
+    """Every kernel here depends on |G|^2 only, and the wrapped frequency of
+    index n - k is -(that of k), so each table is unchanged by k -> (n - k) mod n
+    on every axis, the Nyquist index included: the reading that lets the CUDA
+    path store the table over indices 0..n/2 per axis only."""
+    tables = [oracle.coulomb_kernel(shape, lengths, "bare"), oracle.coulomb_kernel(shape, lengths, "erfc", 0.4),
+              oracle.kinetic_kernel(shape, lengths)]
+    for k in tables:
+        for axis, n in enumerate(k.shape):
+            idx = (-np.arange(n)) % n
+            assert np.array_equal(np.take(k, idx, axis=axis), k)
+    # and the folded indices cover every value: min(k, n - k) reaches each class once
+    n = shape[0]
+    assert sorted({min(i, n - i) for i in range(n)}) == list(range(n // 2 + 1))
