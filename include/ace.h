@@ -11,7 +11,7 @@
  *   Eq. EXSR               : screened kernel erfc(omega r)/r
  *
  * Discretisation (all entry points): a periodic orthorhombic cell L[0] x L[1] x
- * L[2] sampled on n x n x n points; dV = Omega / N_g. Inner products are
+ * L[2] sampled on n[0] x n[1] x n[2] points; dV = Omega / N_g. Inner products are
  * <f, g> = dV sum_r conj(f(r)) g(r). The Poisson-type solve is
  *   v(r) = sum_G K(G) rho_hat(G) e^{iG.r},  rho_hat(G) = N_g^-1 sum_r rho(r) e^{-iG.r},
  * with K(G) = alpha * 4 pi/|G|^2 (ACE_KERNEL_BARE, K(0) = 0 by default) or
@@ -26,7 +26,8 @@
  * Conventions shared by every entry point:
  *  - Array arguments are DEVICE pointers owned by the caller. Layout is
  *    orbital-major, x fastest: element (b, z, y, x) of an array of `count`
- *    vectors is at offset ((b * n + z) * n + y) * n + x elements. Storage type is
+ *    vectors is at offset b * ld + (z * n[1] + y) * n[0] + x elements (ld =
+ *    the plan's leading dimension, N_g by default). Storage type is
  *    the plan's dtype: ACE_DTYPE_R64 (double, real Gamma-point orbitals),
  *    ACE_DTYPE_C128 (interleaved double complex) or ACE_DTYPE_C64 (interleaved
  *    float complex). Pointers must be 16-byte aligned.
@@ -57,7 +58,7 @@ typedef enum {
   ACE_ERR_NONFINITE = -3,    /* NaN / Inf met in the Cholesky pivot (device status) */
   ACE_ERR_WORKSPACE = -4,    /* ws_bytes smaller than ace_workspace_size() */
   ACE_ERR_CUDA = -5,         /* a CUDA runtime call or launch failed */
-  ACE_ERR_TIMEOUT = -6,      /* reserved: a bounded device wait ran out */
+  ACE_ERR_TIMEOUT = -6,      /* a bounded device wait ran out (device status) */
   ACE_ERR_UNSUPPORTED = -7   /* grid edge / dtype combination not built */
 } ace_status;
 
@@ -69,19 +70,42 @@ typedef enum {
   ACE_OP_POISSON = 5             /* n_b = number of densities */
 } ace_op;
 
+/* Arithmetic of the dense steps (M = Phi^* W, Xi = W L^{-*}, the apply) for
+ * ACE_DTYPE_C64 plans; FP64 plans (R64, C128) compute everything in FP64 on
+ * CUDA cores and accept ACE_PREC_DEFAULT only. The Cholesky factor and
+ * L^{-1} are FP64 in every mode.
+ *  ACE_PREC_DEFAULT / ACE_PREC_SPLIT_TF32: tcgen05 TF32 tensor cores, each FP32
+ *    operand split into two TF32 terms, three products (FP32 accuracy).
+ *  ACE_PREC_FP32: FP32 on CUDA cores.
+ *  ACE_PREC_XI_FP64: as SPLIT_TF32, except Xi = W L^{-*}, which is computed to
+ *    FP64 accuracy from the FP32 W and the FP64 L^{-*} on the FP16 tensor cores
+ *    (error-free 8-bit integer slices of both operands, exact integer products,
+ *    exact accumulation) and rounded once to FP32.
+ *  ACE_PREC_XI_FP64_SIMT: the same Xi with plain FP64 arithmetic on CUDA cores. */
+typedef enum {
+  ACE_PREC_DEFAULT = 0,
+  ACE_PREC_SPLIT_TF32 = 1,
+  ACE_PREC_FP32 = 2,
+  ACE_PREC_XI_FP64 = 3,
+  ACE_PREC_XI_FP64_SIMT = 4
+} ace_prec;
+
 typedef struct {
-  int n;             /* grid points per edge (cubic grid n^3); see ace_supported_edge */
+  int n[3];          /* grid points along x, y, z (N_g = n[0] n[1] n[2]); see ace_supported_grid */
   double L[3];       /* cell edges Lx, Ly, Lz (bohr), > 0 */
-  int n_occ;         /* N: number of exchange orbitals phi, >= 1 */
+  int n_occ;         /* N: number of exchange orbitals phi, 1..1024 */
   int dtype;         /* ace_dtype. R64/C128: FP64 throughout. C64: FP32 pair/FFT path,
-                        GEMMs on TF32 tensor cores with a 3-term split (FP32
-                        accuracy; see ACE_FLAG_SIMT_GEMM), FP64 Cholesky and
-                        triangular inverse. */
+                        dense steps per `prec`, FP64 Cholesky and triangular inverse. */
+  int prec;          /* ace_prec (0 = default) */
   int kernel;        /* ace_kernel */
   double omega;      /* screening parameter (bohr^-1) for ACE_KERNEL_ERFC, > 0 */
   double g0_value;   /* K(G=0) before alpha; NaN selects the default (0 bare and kinetic,
                         pi/omega^2 erfc) */
   double alpha;      /* overall kernel scale (1 = Hartree-Fock; 0.25 for PBE0/HSE fractions) */
+  long long ld;      /* elements from one vector to the next in every vector array the
+                        plan's calls take (Phi, Psi, W, Xi, Y, gradients, densities):
+                        0 = N_g (packed), else >= N_g and even; elements between N_g
+                        and ld are neither read nor written */
   int max_pairs;     /* pair solves in flight per batch (0 = library default); sets the
                         size of the pair-spectrum scratch in the workspace */
   int tile;          /* orbitals per pair tile, 1..8 (0 = default 8) */
@@ -104,8 +128,8 @@ typedef struct {
  * tuning and diagnosis switch). With ACE_FLAG_NO_GRAPH and without
  * ACE_FLAG_ENGINE, ace_profile_end reports per-pass times. */
 #define ACE_FLAG_NO_PDL 4
-/* ACE_DTYPE_C64: run M = Phi^* W, Xi = W L^{-*} and the apply on CUDA cores in
- * FP32 instead of the tensor cores (tcgen05 TF32 with a 3-term split). */
+/* ACE_DTYPE_C64: the same as prec = ACE_PREC_FP32 (M, Xi and the apply in FP32
+ * on CUDA cores). */
 #define ACE_FLAG_SIMT_GEMM 8
 /* By default, graph mode issues pass A of every pair batch on one stream and
  * passes B-D on a second, so that pass A of batch k+1 (which waits for pass C of
@@ -119,6 +143,9 @@ typedef struct ace_plan ace_plan;
 /* Nonzero when grid edge n is compiled in for the dtype (register-resident FFT
  * lengths; radices 2, 3, 4, 5). */
 int ace_supported_edge(int n, int dtype);
+
+/* Nonzero when the n[0] x n[1] x n[2] grid is compiled in for the dtype. */
+int ace_supported_grid(const int n[3], int dtype);
 
 /* Validate *desc and build a plan on the current device: Coulomb kernel table,
  * FFT twiddles (FP64 host sin/cos), the pair-tile schedule and small FP64 N x N
@@ -227,8 +254,9 @@ ace_status ace_exchange_energy_grad(ace_plan* plan, const void* Phi, double* Ex_
                                     size_t ws_bytes, void* stream);
 
 /* Synchronise `stream` and read the plan's device status word: returns ACE_OK,
- * ACE_ERR_NOT_POSDEF or ACE_ERR_NONFINITE; *info (if non-NULL) gets the
- * 1-based Cholesky pivot that failed, 0 otherwise. Clears the status. */
+ * ACE_ERR_NOT_POSDEF, ACE_ERR_NONFINITE or ACE_ERR_TIMEOUT; *info (if
+ * non-NULL) gets the 1-based Cholesky pivot that failed (the task index or a
+ * negative kernel tag for a timeout), 0 otherwise. Clears the status. */
 ace_status ace_status_sync(ace_plan* plan, void* stream, int* info);
 
 /* Instrumentation (no counterpart in the paper; for benchmarks and profiles).
@@ -261,10 +289,44 @@ ace_status ace_profile_end(ace_plan* plan, double* ms_out, long long* counts_out
  * (cudaGetSymbolAddress) with that device current; make it before any stream
  * capture. All calls on a device share the array: calls that may overlap on
  * the GPU (other streams, other plans) race and must be serialised by the
- * caller. Nothing needs clearing between calls. Results equal ace_apply's up
- * to the order of the split-K sums. Calls no allocator. */
+ * caller. Nothing needs clearing between calls. The GEMMs run on CUDA cores:
+ * for FP64 plans the result equals ace_apply's up to the order of the split-K
+ * sums; for ACE_DTYPE_C64 plans, whose ace_apply uses the TF32 3-term-split
+ * tensor cores, the two agree to the FP32 apply tolerance (about 1e-6
+ * relative), not bit for bit. Calls no allocator. */
 ace_status ace_apply_static(ace_plan* plan, const void* Xi, const void* Psi, int n_b, void* Y,
                             void* stream);
+
+/* Test and diagnosis hooks (no counterpart in the paper; they exist so that
+ * failure handling can be exercised without faulting a GPU).
+ *
+ * ace_debug_engine_wait: for plans with ACE_FLAG_ENGINE, every wait of the
+ * persistent engine on another block's work polls at most `polls` times (0
+ * restores the default of 2^22 polls, about a second or more); with
+ * `unreachable` nonzero each wait asks for one finished task more than the pass
+ * it depends on has, so every dependent wait runs out. A wait that runs out
+ * records ACE_ERR_TIMEOUT (info = the task index) in the plan's status word,
+ * and the launch ends: blocks stop taking tasks and return, nothing of theirs
+ * in flight. Outputs of that call are then undefined. Drops the plan's cached
+ * graphs. Returns ACE_ERR_ARG for a NULL plan.
+ *
+ * ace_debug_fail_alloc: from now on, the k-th device allocation the library
+ * makes (plan set-up, one-sided schedule uploads, ace_autotune's buffers)
+ * fails as if the device were out of memory, so the calling entry point
+ * returns ACE_ERR_CUDA after releasing what it had allocated; k <= 0 turns the
+ * hook off. Returns the number of library allocations counted since the
+ * previous call. Process-wide; not for concurrent use. */
+ace_status ace_debug_engine_wait(ace_plan* plan, unsigned polls, int unreachable);
+
+/* ace_debug_xi_product (ACE_DTYPE_C64 plans): Xi = W L^{-*} (Eq. Wtilde) with
+ * the L^{-*} of the plan's last build, written in FP64 (interleaved double
+ * complex, N vectors of stride ld) so that the FP64 accuracy of the product
+ * itself can be checked: method 1 = the FP16-tensor-core slice product of
+ * ACE_PREC_XI_FP64 (deeper slicing for FP64 output), 2 = plain FP64 on CUDA
+ * cores. W: N complex FP32 vectors. Method 1 allocates its scratch and
+ * synchronises `stream`. */
+ace_status ace_debug_xi_product(ace_plan* plan, const void* W, void* Xi_out, int method, void* stream);
+long long ace_debug_fail_alloc(long long k);
 
 /* Message for the calling thread's last failed call ("" if none). */
 const char* ace_last_error(void);

@@ -36,16 +36,21 @@ KERNELS = {"bare": 0, "erfc": 1, "kinetic": 2}
 OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED, OP_POISSON = 0, 1, 2, 3, 4, 5
 
 
+PRECS = {"default": 0, "split_tf32": 1, "fp32": 2, "xi_fp64": 3, "xi_fp64_simt": 4}
+
+
 class Desc(ctypes.Structure):
     _fields_ = [
-        ("n", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
         ("L", ctypes.c_double * 3),
         ("n_occ", ctypes.c_int),
         ("dtype", ctypes.c_int),
+        ("prec", ctypes.c_int),
         ("kernel", ctypes.c_int),
         ("omega", ctypes.c_double),
         ("g0_value", ctypes.c_double),
         ("alpha", ctypes.c_double),
+        ("ld", ctypes.c_longlong),
         ("max_pairs", ctypes.c_int),
         ("tile", ctypes.c_int),
         ("lanes", ctypes.c_int),
@@ -53,9 +58,21 @@ class Desc(ctypes.Structure):
     ]
 
 
+def _grid(n):
+    """(n_x, n_y, n_z) from an edge or a 3-sequence."""
+    if isinstance(n, int):
+        return (n, n, n)
+    n = tuple(int(v) for v in n)
+    if len(n) != 3:
+        raise ValueError("grid must be an int or three ints (n_x, n_y, n_z)")
+    return n
+
+
 _vp = ctypes.c_void_p
 _lib.ace_supported_edge.argtypes = [ctypes.c_int, ctypes.c_int]
 _lib.ace_supported_edge.restype = ctypes.c_int
+_lib.ace_supported_grid.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+_lib.ace_supported_grid.restype = ctypes.c_int
 _lib.ace_last_error.argtypes = []
 _lib.ace_last_error.restype = ctypes.c_char_p
 _lib.ace_plan_create.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(_vp)]
@@ -92,6 +109,12 @@ _lib.ace_build_batched.restype = ctypes.c_int
 _lib.ace_autotune.argtypes = [ctypes.POINTER(Desc), ctypes.c_int, ctypes.POINTER(Desc),
                               ctypes.POINTER(ctypes.c_double)]
 _lib.ace_autotune.restype = ctypes.c_int
+_lib.ace_debug_engine_wait.argtypes = [_vp, ctypes.c_uint, ctypes.c_int]
+_lib.ace_debug_engine_wait.restype = ctypes.c_int
+_lib.ace_debug_xi_product.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
+_lib.ace_debug_xi_product.restype = ctypes.c_int
+_lib.ace_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+_lib.ace_debug_fail_alloc.restype = ctypes.c_longlong
 
 
 class AceError(RuntimeError):
@@ -107,6 +130,11 @@ def _check(code: int):
 
 def supported_edge(n: int, dtype: str) -> bool:
     return bool(_lib.ace_supported_edge(n, DTYPES[dtype]))
+
+
+def supported_grid(n, dtype: str) -> bool:
+    g = (ctypes.c_int * 3)(*_grid(n))
+    return bool(_lib.ace_supported_grid(g, DTYPES[dtype]))
 
 
 def lib():
@@ -125,22 +153,27 @@ def _stream():
 class Plan:
     """An ACE plan on the current CUDA device (see ace_plan_create)."""
 
-    def __init__(self, n: int, L, n_occ: int, dtype: str = "c64", kernel: str = "bare",
+    def __init__(self, n, L, n_occ: int, dtype: str = "c64", kernel: str = "bare",
                  omega: float = 0.0, g0: float | None = None, alpha: float = 1.0,
                  max_pairs: int = 0, tile: int = 0, lanes: int = 0, graphs: bool = True,
                  engine: bool = False, pdl: bool = True, tensor_cores: bool = True,
-                 overlap: bool = True):
+                 overlap: bool = True, prec: str = "default", ld: int = 0):
+        """n: grid edge or (n_x, n_y, n_z); L: cell edge or (L_x, L_y, L_z);
+        ld: elements from one vector to the next (0 = N_g)."""
         if isinstance(L, (int, float)):
             L = (float(L),) * 3
+        grid = _grid(n)
         d = Desc()
-        d.n = n
+        d.n[0], d.n[1], d.n[2] = grid
         d.L[0], d.L[1], d.L[2] = L
         d.n_occ = n_occ
         d.dtype = DTYPES[dtype]
+        d.prec = PRECS[prec]
         d.kernel = KERNELS[kernel]
         d.omega = omega
         d.g0_value = math.nan if g0 is None else g0
         d.alpha = alpha
+        d.ld = ld
         d.max_pairs = max_pairs
         d.tile = tile
         d.lanes = lanes
@@ -149,8 +182,12 @@ class Plan:
         h = _vp()
         _check(_lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
-        self.n, self.L, self.n_occ, self.dtype = n, tuple(L), n_occ, dtype
-        self.ng = n ** 3
+        self.grid = grid
+        self.n = grid[0] if grid[0] == grid[1] == grid[2] else grid
+        self.L, self.n_occ, self.dtype = tuple(L), n_occ, dtype
+        self.ng = grid[0] * grid[1] * grid[2]
+        self.ld = ld if ld else self.ng
+        self.shape = (grid[2], grid[1], grid[0])     # [z][y][x]
         self.volume = L[0] * L[1] * L[2]
         self.dv = self.volume / self.ng
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -185,14 +222,22 @@ class Plan:
             raise TypeError(f"{name}: expected {self.tdtype}, got {t.dtype}")
         if t.device != self.device:
             raise ValueError(f"{name}: expected device {self.device}")
-        if t.dim() != 4 or tuple(t.shape[1:]) != (self.n,) * 3:
-            raise ValueError(f"{name}: expected shape (count, {self.n}, {self.n}, {self.n})")
-        if not t.is_contiguous():
-            raise ValueError(f"{name}: must be contiguous")
+        if t.dim() != 4 or tuple(t.shape[1:]) != self.shape:
+            raise ValueError(f"{name}: expected shape (count, {self.shape[0]}, {self.shape[1]}, {self.shape[2]})")
+        nz, ny, nx = self.shape
+        want = (self.ld, ny * nx, nx, 1)
+        if t.shape[0] > 1 and t.stride() != want or t.shape[0] <= 1 and t.stride()[1:] != want[1:]:
+            raise ValueError(f"{name}: expected strides {want} (vectors {self.ld} elements apart)")
         return t
 
     def empty(self, count: int) -> torch.Tensor:
-        return torch.empty((count, self.n, self.n, self.n), dtype=self.tdtype, device=self.device)
+        """`count` vectors of the plan's layout: (count, n_z, n_y, n_x), vectors ld
+        elements apart."""
+        if self.ld == self.ng:
+            return torch.empty((count,) + self.shape, dtype=self.tdtype, device=self.device)
+        flat = torch.empty((max(count, 1), self.ld), dtype=self.tdtype, device=self.device)
+        nz, ny, nx = self.shape
+        return flat.as_strided((count,) + self.shape, (self.ld, ny * nx, nx, 1))
 
     # ---------------------------------------------------------------- entry points
     def exchange_apply(self, phi, psi, out=None):
@@ -217,8 +262,8 @@ class Plan:
             w = self.empty(N)
         m = None
         if want_m:
-            shape = (N, N) if self.dtype == "r64" else (N, N, 2)
-            m = torch.empty(shape, dtype=torch.float64, device=self.device)
+            mshape = (N, N) if self.dtype == "r64" else (N, N, 2)
+            m = torch.empty(mshape, dtype=torch.float64, device=self.device)
         ex = torch.empty((), dtype=torch.float64, device=self.device)
         ws = self.workspace(OP_BUILD)
         _check(_lib.ace_build(self._h, _ptr(phi), _ptr(w), _ptr(xi), _ptr(m), _ptr(ex), _ptr(ws),
@@ -240,8 +285,8 @@ class Plan:
             w = self.empty(n_phi)
         m = None
         if want_m:
-            shape = (n_phi, n_phi) if self.dtype == "r64" else (n_phi, n_phi, 2)
-            m = torch.empty(shape, dtype=torch.float64, device=self.device)
+            mshape = (n_phi, n_phi) if self.dtype == "r64" else (n_phi, n_phi, 2)
+            m = torch.empty(mshape, dtype=torch.float64, device=self.device)
         ex = torch.empty((), dtype=torch.float64, device=self.device)
         ws = self.workspace(OP_BUILD_OVERSAMPLED, n_phi)
         _check(_lib.ace_build_oversampled(self._h, _ptr(phi), n_phi, _ptr(w), _ptr(xi), _ptr(m), _ptr(ex),
@@ -303,6 +348,19 @@ class Plan:
         return {"pass_ms": {"A": ms[0], "B": ms[1], "C": ms[2], "D": ms[3]}, "pair_ms": ms[4],
                 "batches": cnt[0], "launches": cnt[1], "dropped": cnt[2]}
 
+    def debug_engine_wait(self, polls: int = 0, unreachable: bool = False):
+        """ace_debug_engine_wait: bound (or make unreachable) the engine's waits."""
+        _check(_lib.ace_debug_engine_wait(self._h, polls, 1 if unreachable else 0))
+
+    def debug_xi_product(self, w, method: int):
+        """ace_debug_xi_product: Xi = W L^{-*} of the last build in FP64 (complex128),
+        method 1 = tensor-core slices, 2 = FP64 CUDA cores."""
+        self._vec(w, "w")
+        out = torch.empty((self.n_occ, self.ld), dtype=torch.complex128, device=self.device)
+        _check(_lib.ace_debug_xi_product(self._h, _ptr(w), _ptr(out), method, _stream()))
+        nz, ny, nx = self.shape
+        return out.as_strided((self.n_occ,) + self.shape, (self.ld, ny * nx, nx, 1))
+
     def status(self) -> tuple[int, int]:
         """(code, pivot) of the device status word after synchronising."""
         info = ctypes.c_int(0)
@@ -310,11 +368,17 @@ class Plan:
         return code, info.value
 
 
+def debug_fail_alloc(k: int) -> int:
+    """ace_debug_fail_alloc: make the k-th library allocation from now fail
+    (k <= 0: off); returns the allocations counted since the previous call."""
+    return int(_lib.ace_debug_fail_alloc(k))
+
+
 def _desc(n, L, n_occ, dtype, kernel, omega, g0, alpha) -> Desc:
     if isinstance(L, (int, float)):
         L = (float(L),) * 3
     d = Desc()
-    d.n = n
+    d.n[0], d.n[1], d.n[2] = _grid(n)
     d.L[0], d.L[1], d.L[2] = L
     d.n_occ = n_occ
     d.dtype = DTYPES[dtype]
@@ -416,8 +480,11 @@ class ExchangeEnergy(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g_out):
+        # the gradient with unit scale from the adjoint kernels, then the chain
+        # rule's upstream factor applied on the device (no host synchronisation)
         (phi,) = ctx.saved_tensors
-        _, g = ctx.plan.energy_grad(phi, grad=True, grad_scale=float(g_out.item()))
+        _, g = ctx.plan.energy_grad(phi, grad=True)
+        g.mul_(g_out.to(g.real.dtype))
         return g, None
 
 

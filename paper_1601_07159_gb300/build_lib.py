@@ -21,8 +21,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 # keep in step with ACE_EDGES_F32 / ACE_EDGES_F64 in csrc/pair_dispatch.cu
 EDGES_F32 = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 96)
-EDGES_F64 = (8, 12, 16, 20, 24, 32, 36, 40, 48)
-PLAIN = ["pair_dispatch.cu", "dense.cu", "chol.cu", "tc_gemm.cu", "ace_api.cu", "apply_static.cu"]
+EDGES_F64 = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 96)
+PLAIN = ["pair_dispatch.cu", "dense.cu", "chol.cu", "tc_gemm.cu", "xi_oz.cu", "ace_api.cu", "apply_static.cu"]
 
 
 def units():

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <atomic>
 #include <deque>
 #include <mutex>
 #include <limits>
@@ -19,6 +20,21 @@ using namespace ace;
 namespace {
 
 thread_local std::string g_last_error;
+
+// Allocation-failure injection (ace_debug_fail_alloc): when g_fail_at > 0 the
+// g_fail_at-th device allocation counted from the hook's last call fails as if
+// the device were out of memory.
+std::atomic<long long> g_fail_at{0};
+std::atomic<long long> g_alloc_count{0};
+
+cudaError_t dev_alloc(void** ptr, size_t bytes) {
+  const long long c = ++g_alloc_count;
+  if (g_fail_at.load() > 0 && c == g_fail_at.load()) {
+    *ptr = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(ptr, bytes);
+}
 
 ace_status fail(ace_status s, const std::string& msg) {
   g_last_error = msg;
@@ -72,8 +88,10 @@ struct ProfRec {
 struct ace_plan {
   ace_desc d{};
   int device = 0;
-  int n = 0;
-  long long ng = 0;
+  int n = 0;                     // grid edge (the pair kernels are compiled per cubic edge)
+  long long ng = 0;              // grid points N_g
+  long long ld = 0;              // elements from one vector to the next
+  int xi = 0;                    // Xi = W L^{-*}: 0 the plan's GEMM, 1 FP16 Ozaki slices, 2 FP64 CUDA cores
   double vol = 0.0, dv = 0.0;
   bool f64 = false, real = false;
   size_t csize = 0;              // bytes per complex scratch element
@@ -83,6 +101,8 @@ struct ace_plan {
   bool engine = true;            // persistent pair engine (else four kernels per batch)
   bool tc = false;               // tensor-core GEMMs (complex FP32 storage)
   bool overlap = false;          // graph mode: pass A of batch k+1 overlaps pass D of batch k
+  unsigned eng_polls = kEngineSpinDefault;   // engine wait limit (ace_debug_engine_wait)
+  unsigned eng_bias = 0;
   cudaEvent_t ov_ev[2] = {};
 
   EngineInfo einfo;
@@ -138,10 +158,10 @@ cudaError_t upload(const ace_plan* p, Schedule& sc) {
   sc.ntasks[0] = t0[0];
   sc.ntasks[1] = t0[1];
   if (all.empty()) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&sc.dtiles, all.size() * sizeof(TileDesc));
+  cudaError_t e = dev_alloc((void**)&sc.dtiles, all.size() * sizeof(TileDesc));
   if (e == cudaSuccess) e = cudaMemcpy(sc.dtiles, all.data(), all.size() * sizeof(TileDesc), cudaMemcpyHostToDevice);
   for (int m = 0; m < 2 && e == cudaSuccess; ++m) {
-    e = cudaMalloc(&sc.deng[m], eng[m].size() * sizeof(EngineBatch));
+    e = dev_alloc((void**)&sc.deng[m], eng[m].size() * sizeof(EngineBatch));
     if (e == cudaSuccess)
       e = cudaMemcpy(sc.deng[m], eng[m].data(), eng[m].size() * sizeof(EngineBatch), cudaMemcpyHostToDevice);
   }
@@ -254,6 +274,7 @@ struct WsLayout {
   char* ctr = nullptr;          // engine queue head + per-batch counters
   double* work = nullptr;       // oversampled build: Cholesky work and L^{-*} of N_phi
   double* LinvH = nullptr;
+  char* xis = nullptr;          // FP64-accurate Xi: row/column exponents and C slices
   size_t total = 0;
 };
 
@@ -292,8 +313,9 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   if (op == ACE_OP_BUILD_OVERSAMPLED) {
     const size_t pd = (size_t)splits * nb * nb * 2;
     L.part = (double*)take((pd > diag_dot_part_doubles(nb) ? pd : diag_dot_part_doubles(nb)) * sizeof(double));
-    L.Wtmp = take((size_t)nb * p->ng * p->vsize);
+    L.Wtmp = take((size_t)nb * p->ld * p->vsize);
     L.Cm = (double*)take((size_t)nb * nb * 2 * sizeof(double));
+    if (p->xi == 1) L.xis = take(xi_oz_scratch_bytes(p->ng, nb, nb, false));
     L.work = (double*)take(cholesky_work_doubles(nb) * sizeof(double));
     L.LinvH = (double*)take((size_t)nb * nb * 2 * sizeof(double));
   }
@@ -302,7 +324,8 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   if (op == ACE_OP_BUILD) {
     const size_t pd = (size_t)splits * N * N * 2;
     L.part = (double*)take((pd > diag_dot_part_doubles(N) ? pd : diag_dot_part_doubles(N)) * sizeof(double));
-    L.Wtmp = take((size_t)N * p->ng * p->vsize);
+    L.Wtmp = take((size_t)N * p->ld * p->vsize);
+    if (p->xi == 1) L.xis = take(xi_oz_scratch_bytes(p->ng, N, N, false));
   }
   if (op == ACE_OP_APPLY) {
     L.part = (double*)take((size_t)splits * N * nb * 2 * sizeof(double));
@@ -371,6 +394,8 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
     E.status = p->status;
     E.blocks = p->einfo.blocks;
     E.smem = p->einfo.smem;
+    E.spin_limit = p->eng_polls;
+    E.wait_bias = p->eng_bias;
     const bool ok = p->f64 ? launch_engine_f64(L, E, cs) : launch_engine_f32(L, E, cs);
     return ok ? 1 : -1;
   }
@@ -511,7 +536,7 @@ ace_status run_graph(ace_plan* p, const uintptr_t key[8], cudaStream_t st, bool 
 PairLaunch base_launch(const ace_plan* p) {
   PairLaunch L{};
   L.n = p->n;
-  L.ld = p->ng;
+  L.ld = p->ld;
   L.Kt = p->Kt;
   L.tw = p->tw.data();
   L.real_io = p->real;
@@ -553,6 +578,26 @@ void drop_graphs(ace_plan* p) {
   p->graph_cache.clear();
 }
 
+// Zero `count` vectors of the plan's layout (only the N_g elements of each).
+void zero_vectors(const ace_plan* p, void* X, long long count, cudaStream_t st) {
+  const size_t row = (size_t)p->ng * p->vsize;
+  if (p->ld == p->ng) cudaMemsetAsync(X, 0, (size_t)count * row, st);
+  else cudaMemset2DAsync(X, (size_t)p->ld * p->vsize, 0, row, (size_t)count, st);
+}
+
+// Xi = W L^{-*} (Eq. Wtilde) for `nk` vectors on `cs` by the plan's Xi mode;
+// returns the kernel count.
+int issue_xi(ace_plan* p, const void* W, int nk, const double* LinvH, void* Xi, char* xis, cudaStream_t cs) {
+  if (p->xi == 1) return launch_xi_oz(W, nk, LinvH, nk, p->ld, p->ng, Xi, false, xis, p->status, cs);
+  if (p->xi == 2) {
+    launch_outer_f64acc(W, nk, LinvH, nk, p->ld, p->ng, Xi, false, cs);
+    return 1;
+  }
+  if (p->tc) launch_outer_tc(W, nk, LinvH, nk, p->ld, p->ng, 1.0, Xi, p->status, cs);
+  else launch_outer(p->f64, p->real, W, nk, LinvH, nk, p->ld, p->ng, 1.0, Xi, cs);
+  return 1;
+}
+
 // The W build's pair section on `cs`: W = 0, then W = V_X[Phi] Phi over the
 // unique pairs (Eq. W). Returns the kernel count, or -1.
 long long issue_build_pairs(ace_plan* p, const void* Phi, void* W, const WsLayout& Wl, cudaStream_t cs) {
@@ -562,7 +607,7 @@ long long issue_build_pairs(ace_plan* p, const void* Phi, void* W, const WsLayou
   L.OutX = W;
   L.OutY = W;
   L.mode = 0;
-  cudaMemsetAsync(W, 0, (size_t)p->d.n_occ * p->ng * p->vsize, cs);
+  zero_vectors(p, W, p->d.n_occ, cs);
   return issue_pairs(p, L, p->build, Wl.S, nullptr, Wl.ctr, cs);
 }
 
@@ -572,14 +617,13 @@ long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* X
                             cudaStream_t cs) {
   const int N = p->d.n_occ;
   const int splits = gram_parts(p, N, N);
-  if (p->tc) launch_gram_tc(Phi, N, W, N, p->ng, p->ng, Wl.part, splits, p->status, cs);
-  else launch_gram(p->f64, p->real, Phi, N, W, N, p->ng, p->ng, Wl.part, splits, cs);
+  if (p->tc) launch_gram_tc(Phi, N, W, N, p->ld, p->ng, Wl.part, splits, p->status, cs);
+  else launch_gram(p->f64, p->real, Phi, N, W, N, p->ld, p->ng, Wl.part, splits, cs);
   const int kr = launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
-  if (p->tc) launch_diag_exact(Phi, W, N, p->ng, p->ng, p->dv, Wl.part, p->Mc, cs);
+  if (p->tc) launch_diag_exact(Phi, W, N, p->ld, p->ng, p->dv, Wl.part, p->Mc, cs);
   const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
-  if (p->tc) launch_outer_tc(W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi, p->status, cs);
-  else launch_outer(p->f64, p->real, W, N, p->LinvH, N, p->ng, p->ng, 1.0, Xi, cs);
-  return 1 + kr + (p->tc ? 2 : 0) + kc + 1;
+  const int kx = issue_xi(p, W, N, p->LinvH, Xi, Wl.xis, cs);
+  return 1 + kr + (p->tc ? 2 : 0) + kc + kx;
 }
 
 // One captured graph per batch of systems (ace_build_batched), shared by all
@@ -618,11 +662,12 @@ double build_cost(const ace_plan* p) {
 
 }  // namespace
 
-ace_status ace_internal_plan_info(const ace_plan* p, int* device, int* n_occ, long long* ng,
+ace_status ace_internal_plan_info(const ace_plan* p, int* device, int* n_occ, long long* ng, long long* ld,
                                   double* dv, int* f64, int* real) {
   *device = p->device;
   *n_occ = p->d.n_occ;
   *ng = p->ng;
+  *ld = p->ld;
   *dv = p->dv;
   *f64 = p->f64 ? 1 : 0;
   *real = p->real ? 1 : 0;
@@ -639,6 +684,11 @@ int ace_supported_edge(int n, int dtype) {
   return 0;
 }
 
+int ace_supported_grid(const int n[3], int dtype) {
+  if (!n || n[0] != n[1] || n[1] != n[2]) return 0;
+  return ace_supported_edge(n[0], dtype);
+}
+
 const char* ace_last_error(void) { return g_last_error.c_str(); }
 
 ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
@@ -653,8 +703,18 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   if (!(d->L[0] > 0 && d->L[1] > 0 && d->L[2] > 0)) return fail(ACE_ERR_ARG, "cell edges must be > 0");
   if (d->kernel == ACE_KERNEL_ERFC && !(d->omega > 0)) return fail(ACE_ERR_ARG, "omega must be > 0");
   if (!std::isfinite(d->alpha)) return fail(ACE_ERR_ARG, "alpha must be finite");
-  if (!ace_supported_edge(d->n, d->dtype))
-    return fail(ACE_ERR_UNSUPPORTED, "grid edge " + std::to_string(d->n) + " not built for this dtype");
+  if (d->n[0] < 1 || d->n[1] < 1 || d->n[2] < 1) return fail(ACE_ERR_ARG, "grid sizes must be >= 1");
+  if (!ace_supported_grid(d->n, d->dtype))
+    return fail(ACE_ERR_UNSUPPORTED, "grid " + std::to_string(d->n[0]) + "x" + std::to_string(d->n[1]) + "x" +
+                                         std::to_string(d->n[2]) + " not built for this dtype");
+  const long long ng_ = (long long)d->n[0] * d->n[1] * d->n[2];
+  if (d->ld != 0 && (d->ld < ng_ || (d->ld & 1)))
+    return fail(ACE_ERR_ARG, "ld must be 0 or an even count >= N_g");
+  if (d->prec < ACE_PREC_DEFAULT || d->prec > ACE_PREC_XI_FP64_SIMT) return fail(ACE_ERR_ARG, "bad prec");
+  if (d->dtype != ACE_DTYPE_C64 && d->prec != ACE_PREC_DEFAULT)
+    return fail(ACE_ERR_UNSUPPORTED, "FP64 plans compute in FP64: prec must be ACE_PREC_DEFAULT");
+  if ((d->flags & ACE_FLAG_SIMT_GEMM) && d->prec != ACE_PREC_DEFAULT && d->prec != ACE_PREC_FP32)
+    return fail(ACE_ERR_ARG, "ACE_FLAG_SIMT_GEMM conflicts with prec");
   if (d->tile < 0 || d->tile > kTileMax) return fail(ACE_ERR_ARG, "tile must be 0..8");
   if (d->max_pairs < 0) return fail(ACE_ERR_ARG, "max_pairs must be >= 0");
   if (d->lanes < 0 || d->lanes > kMaxLanes) return fail(ACE_ERR_ARG, "lanes must be 0..8");
@@ -662,8 +722,9 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   ace_plan* p = new ace_plan();
   p->d = *d;
   cudaGetDevice(&p->device);
-  p->n = d->n;
-  p->ng = (long long)d->n * d->n * d->n;
+  p->n = d->n[0];
+  p->ng = ng_;
+  p->ld = d->ld ? d->ld : ng_;
   p->vol = d->L[0] * d->L[1] * d->L[2];
   p->dv = p->vol / (double)p->ng;
   p->f64 = d->dtype != ACE_DTYPE_C64;
@@ -674,7 +735,8 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->lanes = d->lanes ? d->lanes : 2;
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
   p->engine = (d->flags & ACE_FLAG_ENGINE) != 0;
-  p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM);
+  p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM) && d->prec != ACE_PREC_FP32;
+  p->xi = d->prec == ACE_PREC_XI_FP64 ? 1 : (d->prec == ACE_PREC_XI_FP64_SIMT ? 2 : 0);
   p->overlap = p->graphs && !p->engine && !(d->flags & ACE_FLAG_NO_OVERLAP);
   if (p->overlap && p->lanes < 2) p->lanes = 2;
   const size_t slot = (size_t)p->ng * p->csize;
@@ -723,31 +785,31 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   const int N = d->n_occ;
   cudaError_t e = cudaSuccess;
   if (p->f64) {
-    e = cudaMalloc(&p->Kt, kt.size() * sizeof(double));
+    e = dev_alloc(&p->Kt, kt.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(p->Kt, kt.data(), kt.size() * sizeof(double), cudaMemcpyHostToDevice);
   } else {
     std::vector<float> kf(kt.begin(), kt.end());
-    e = cudaMalloc(&p->Kt, kf.size() * sizeof(float));
+    e = dev_alloc(&p->Kt, kf.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(p->Kt, kf.data(), kf.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) {
     if (p->vsize == 8 && !p->real) {   // c64: (1.0f, 0.0f) pairs
       std::vector<float> onef((size_t)2 * p->ng, 0.0f);
       for (long long i = 0; i < p->ng; ++i) onef[2 * i] = 1.0f;
-      e = cudaMalloc(&p->ones, onef.size() * sizeof(float));
+      e = dev_alloc(&p->ones, onef.size() * sizeof(float));
       if (e == cudaSuccess) e = cudaMemcpy(p->ones, onef.data(), onef.size() * sizeof(float), cudaMemcpyHostToDevice);
     } else {                           // r64: 1.0; c128: (1.0, 0.0)
       const size_t stride = p->real ? 1 : 2;
       std::vector<double> oned((size_t)p->ng * stride, 0.0);
       for (long long i = 0; i < p->ng; ++i) oned[stride * i] = 1.0;
-      e = cudaMalloc(&p->ones, oned.size() * sizeof(double));
+      e = dev_alloc(&p->ones, oned.size() * sizeof(double));
       if (e == cudaSuccess) e = cudaMemcpy(p->ones, oned.data(), oned.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
   }
-  if (e == cudaSuccess) e = cudaMalloc(&p->Mc, (size_t)2 * N * N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->work, cholesky_work_doubles(N) * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->LinvH, (size_t)2 * N * N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&p->status, 2 * sizeof(int));
+  if (e == cudaSuccess) e = dev_alloc((void**)&p->Mc, (size_t)2 * N * N * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&p->work, cholesky_work_doubles(N) * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&p->LinvH, (size_t)2 * N * N * sizeof(double));
+  if (e == cudaSuccess) e = dev_alloc((void**)&p->status, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(p->status, 0, 2 * sizeof(int));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking);
   for (int i = 0; i < p->lanes && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&p->lane[i], cudaStreamNonBlocking);
@@ -761,6 +823,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     launch_one(p, prep, none, nullptr);
     prepare_cholesky(N);
     if (p->tc) tc_gemm_prepare();
+    if (p->xi == 1) xi_oz_prepare();
     if (p->engine) {
       if (p->f64) engine_prepare_f64(p->n, p->einfo);
       else engine_prepare_f32(p->n, p->einfo);
@@ -838,9 +901,8 @@ ace_status ace_exchange_apply(ace_plan* p, const void* Phi, const void* Psi, int
   const Schedule* sc = rect_schedule(p, nb);
   if (!sc) return cuda_check("schedule upload");
   const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)Psi, (uintptr_t)Y, (uintptr_t)ws, (uintptr_t)nb, 1, 0, 0};
-  const size_t ybytes = (size_t)nb * p->ng * p->vsize;
   return run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
-    cudaMemsetAsync(Y, 0, ybytes, cs);
+    zero_vectors(p, Y, nb, cs);
     return issue_pairs(p, L, *sc, W.S, nullptr, W.ctr, cs);
   });
 }
@@ -890,7 +952,7 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
   cudaStream_t st = (cudaStream_t)stream;
   const WsLayout Wl = layout(p, ACE_OP_BUILD_OVERSAMPLED, n_phi, (char*)ws);
   void* W = W_out ? W_out : (void*)Wl.Wtmp;
-  const size_t vec = (size_t)p->ng * p->vsize;
+  const size_t vec = (size_t)p->ld * p->vsize;
   const int nu = n_phi - N;
   const Schedule* sc = nu > 0 ? rect_schedule(p, nu) : nullptr;
   if (nu > 0 && !sc) return cuda_check("schedule upload");
@@ -898,7 +960,7 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
   // of the occupied orbitals with the N_phi - N_e others (Eq. W, Eq. applyVX2)
   const uintptr_t kp[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)ws, (uintptr_t)n_phi, 0, 5, 0, 0};
   s = run_graph(p, kp, st, true, [&](cudaStream_t cs) -> long long {
-    cudaMemsetAsync(W, 0, (size_t)n_phi * vec, cs);
+    zero_vectors(p, W, n_phi, cs);
     PairLaunch L = base_launch(p);
     L.X = Phi;
     L.Y = Phi;
@@ -923,14 +985,13 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
   const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, (uintptr_t)n_phi, 6, 0, 0};
   s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
     const int splits = gram_parts(p, n_phi, n_phi);
-    if (p->tc) launch_gram_tc(Phi, n_phi, W, n_phi, p->ng, p->ng, Wl.part, splits, p->status, cs);
-    else launch_gram(p->f64, p->real, Phi, n_phi, W, n_phi, p->ng, p->ng, Wl.part, splits, cs);
+    if (p->tc) launch_gram_tc(Phi, n_phi, W, n_phi, p->ld, p->ng, Wl.part, splits, p->status, cs);
+    else launch_gram(p->f64, p->real, Phi, n_phi, W, n_phi, p->ld, p->ng, Wl.part, splits, cs);
     const int kr = launch_gram_reduce(Wl.part, splits, n_phi, n_phi, p->dv, true, false, Wl.Cm, nullptr, cs);
-    if (p->tc) launch_diag_exact(Phi, W, n_phi, p->ng, p->ng, p->dv, Wl.part, Wl.Cm, cs);
+    if (p->tc) launch_diag_exact(Phi, W, n_phi, p->ld, p->ng, p->dv, Wl.part, Wl.Cm, cs);
     const int kc = launch_cholesky_inv(Wl.Cm, n_phi, Wl.work, Wl.LinvH, p->status, cs);
-    if (p->tc) launch_outer_tc(W, n_phi, Wl.LinvH, n_phi, p->ng, p->ng, 1.0, Xi_out, p->status, cs);
-    else launch_outer(p->f64, p->real, W, n_phi, Wl.LinvH, n_phi, p->ng, p->ng, 1.0, Xi_out, cs);
-    return 1 + kr + (p->tc ? 2 : 0) + kc + 1;
+    const int kx = issue_xi(p, W, n_phi, Wl.LinvH, Xi_out, Wl.xis, cs);
+    return 1 + kr + (p->tc ? 2 : 0) + kc + kx;
   });
   if (s != ACE_OK) return s;
   p->launches += launch_m_outputs(Wl.Cm, n_phi, p->real, M_out, Ex_out, st, N);
@@ -959,9 +1020,8 @@ ace_status ace_poisson(ace_plan* p, const void* rho, int nb, void* V, void* ws, 
   L.mode = 0;
   L.scale = -1.0;
   const uintptr_t key[8] = {(uintptr_t)rho, (uintptr_t)V, (uintptr_t)ws, (uintptr_t)nb, 0, 7, 0, 0};
-  const size_t vbytes = (size_t)nb * p->ng * p->vsize;
   return run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
-    cudaMemsetAsync(V, 0, vbytes, cs);
+    zero_vectors(p, V, nb, cs);
     return issue_pairs(p, L, *sc, W.S, nullptr, W.ctr, cs);
   });
 }
@@ -1101,7 +1161,7 @@ ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_
   ace_status s = ace_plan_create(d, &probe);
   if (s != ACE_OK) return s;
   const int N = probe->d.n_occ;
-  const long long ng = probe->ng;
+  const long long ng = probe->ng, vstride = probe->ld;
   const size_t vsize = probe->vsize, slot = (size_t)ng * probe->csize;
   const bool f64 = probe->f64;
   ace_plan_destroy(probe);
@@ -1135,9 +1195,9 @@ ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_
   size_t ws_cap = 0;
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  const size_t vbytes = (size_t)N * ng * vsize;
-  cudaError_t e = cudaMalloc(&Phi, vbytes);
-  if (e == cudaSuccess) e = cudaMalloc(&Xi, vbytes);
+  const size_t vbytes = (size_t)N * vstride * vsize;
+  cudaError_t e = dev_alloc(&Phi, vbytes);
+  if (e == cudaSuccess) e = dev_alloc(&Xi, vbytes);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
@@ -1152,7 +1212,7 @@ ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_
       cudaFree(ws);
       ws = nullptr;
       ws_cap = 0;
-      if (cudaMalloc(&ws, need) != cudaSuccess) {
+      if (dev_alloc(&ws, need) != cudaSuccess) {
         cudaGetLastError();
         ace_plan_destroy(p);
         continue;
@@ -1203,11 +1263,11 @@ ace_status ace_apply(ace_plan* p, const void* Xi, const void* Psi, int nb, void*
   const WsLayout Wl = layout(p, ACE_OP_APPLY, nb, (char*)ws);
   const int splits = gram_parts(p, N, nb);
   // C = dV Xi^* Psi, Y = -Xi C (Eq. ACE)
-  if (p->tc) launch_gram_tc(Xi, N, Psi, nb, p->ng, p->ng, Wl.part, splits, p->status, st);
-  else launch_gram(p->f64, p->real, Xi, N, Psi, nb, p->ng, p->ng, Wl.part, splits, st);
+  if (p->tc) launch_gram_tc(Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, p->status, st);
+  else launch_gram(p->f64, p->real, Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, st);
   launch_gram_reduce(Wl.part, splits, N, nb, p->dv, false, false, Wl.Cm, nullptr, st);
-  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ng, p->ng, -1.0, Y, p->status, st);
-  else launch_outer(p->f64, p->real, Xi, N, Wl.Cm, nb, p->ng, p->ng, -1.0, Y, st);
+  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, p->status, st);
+  else launch_outer(p->f64, p->real, Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, st);
   p->launches += 3;
   return cuda_check("ace_apply");
 }
@@ -1234,7 +1294,7 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)Ex_out, (uintptr_t)ws, 0, 3, 0, 0};
   s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
     cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), cs);
-    if (grad_out) cudaMemsetAsync(grad_out, 0, (size_t)N * p->ng * p->vsize, cs);
+    if (grad_out) zero_vectors(p, grad_out, N, cs);
     const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, Wl.ctr, cs);
     // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2  (Kt = alpha K / N_g)
     launch_energy_reduce(Wl.Epart, ecount, -0.5 * p->vol / (double)p->ng, Ex_out, cs);
@@ -1242,7 +1302,7 @@ ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out
   });
   if (s != ACE_OK) return s;
   if (grad_out && grad_scale != 1.0) {   // outside the graph: the scale varies per call
-    launch_scale(p->f64, p->real, grad_out, (long long)N * p->ng, grad_scale, st);
+    launch_scale(p->f64, p->real, grad_out, N, p->ng, p->ld, grad_scale, st);
     p->launches += 1;
   }
   return cuda_check("ace_exchange_energy_grad");
@@ -1298,6 +1358,44 @@ ace_status ace_profile_end(ace_plan* p, double* ms_out, long long* counts_out) {
   p->prof.clear();
   p->ev_used = 0;
   return cuda_check("ace_profile_end");
+}
+
+long long ace_debug_fail_alloc(long long k) {
+  const long long seen = g_alloc_count.exchange(0);
+  g_fail_at.store(k > 0 ? k : 0);
+  return seen;
+}
+
+ace_status ace_debug_engine_wait(ace_plan* p, unsigned polls, int unreachable) {
+  if (!p) return fail(ACE_ERR_ARG, "plan is NULL");
+  p->eng_polls = polls ? polls : kEngineSpinDefault;
+  p->eng_bias = unreachable ? 1u : 0u;
+  drop_graphs(p);   // captured engine launches carry the old limits
+  return ACE_OK;
+}
+
+ace_status ace_debug_xi_product(ace_plan* p, const void* W, void* Xi_out, int method, void* stream) {
+  if (!p) return fail(ACE_ERR_ARG, "plan is NULL");
+  if (p->f64) return fail(ACE_ERR_UNSUPPORTED, "complex FP32 plans only");
+  if (!W || !Xi_out || !aligned16(W) || !aligned16(Xi_out)) return fail(ACE_ERR_ARG, "W / Xi NULL or unaligned");
+  if (method != 1 && method != 2) return fail(ACE_ERR_ARG, "method must be 1 or 2");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) return fail(ACE_ERR_ARG, "wrong device");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int N = p->d.n_occ;
+  if (method == 2) {
+    launch_outer_f64acc(W, N, p->LinvH, N, p->ld, p->ng, Xi_out, true, st);
+    return cuda_check("ace_debug_xi_product");
+  }
+  void* scratch = nullptr;
+  if (dev_alloc(&scratch, xi_oz_scratch_bytes(p->ng, N, N, true)) != cudaSuccess)
+    return fail(ACE_ERR_CUDA, "ace_debug_xi_product: out of memory");
+  xi_oz_prepare();
+  launch_xi_oz(W, N, p->LinvH, N, p->ld, p->ng, Xi_out, true, scratch, p->status, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return fail(ACE_ERR_CUDA, std::string("ace_debug_xi_product: ") + cudaGetErrorString(e));
+  return cuda_check("ace_debug_xi_product");
 }
 
 ace_status ace_status_sync(ace_plan* p, void* stream, int* info) {

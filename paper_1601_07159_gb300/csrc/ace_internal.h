@@ -67,7 +67,12 @@ struct EngineInfo {
   int threads = 0;
   int blocks = 0;    // co-resident blocks on the device (0: the engine does not fit)
 };
+// A persistent-engine wait gives up after this many polls (each sleeps >= 256
+// ns: about a second or more) unless a plan sets another limit.
+constexpr unsigned kEngineSpinDefault = 1u << 22;
 struct EngineLaunch {
+  unsigned spin_limit = kEngineSpinDefault;   // polls before a dependent wait gives up
+  unsigned wait_bias = 0;                     // added to every awaited count (test hook)
   const TileDesc* dtiles;
   const EngineBatch* batches;
   int nbatches;
@@ -111,6 +116,16 @@ void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, 
                     int splits, int* status, cudaStream_t st);
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
                      void* Out, int* status, cudaStream_t st);
+// Xi = W L^{-*} with FP64 arithmetic from complex FP32 W (dense.cu): C upper
+// triangular FP64 [nk][nb]; Out complex FP32 or FP64 [nb][ld].
+void launch_outer_f64acc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,
+                         bool out_f64, cudaStream_t st);
+// The same product to FP64 accuracy on the FP16 tensor cores (xi_oz.cu), with
+// `scratch` of xi_oz_scratch_bytes(); returns the kernel count.
+bool xi_oz_prepare();
+size_t xi_oz_scratch_bytes(long long ng, int nk, int nb, bool out_f64);
+int launch_xi_oz(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,
+                 bool out_f64, void* scratch, int* status, cudaStream_t st);
 // Diagonal of dV A^* B recomputed with FP64 accumulation into Mc (after the
 // tensor-core gram): keeps 1/2 tr M = E_x at FP32 accuracy. part: scratch.
 size_t diag_dot_part_doubles(int na);
@@ -121,7 +136,9 @@ int launch_cholesky_inv(const double* M, int n, double* work, double* LinvH, int
                         cudaStream_t st);
 size_t cholesky_work_doubles(int n);
 void prepare_cholesky(int n);
-void launch_scale(bool f64, bool real, void* X, long long count, double s, cudaStream_t st);
+// X *= s over the first ng elements of each of `count` vectors (stride ld).
+void launch_scale(bool f64, bool real, void* X, long long count, long long ng, long long ld, double s,
+                  cudaStream_t st);
 void launch_energy_reduce(const double* part, int count, double factor, double* out, cudaStream_t st);
 void launch_zero(void* p, size_t bytes, cudaStream_t st);
 // count values (reals) uniform in [-1, 1) from a hash of (seed, index).

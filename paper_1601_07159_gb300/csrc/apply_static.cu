@@ -32,17 +32,17 @@ void* g_addr[kMaxDevices] = {};
 }  // namespace
 
 // Accessors the plan layer uses (defined in ace_api.cu).
-ace_status ace_internal_plan_info(const ace_plan* p, int* device, int* n_occ, long long* ng,
+ace_status ace_internal_plan_info(const ace_plan* p, int* device, int* n_occ, long long* ng, long long* ld,
                                   double* dv, int* f64, int* real);
 ace_status ace_internal_set_error(ace_status s, const char* msg);
 
 extern "C" ace_status ace_apply_static(ace_plan* p, const void* Xi, const void* Psi, int nb, void* Y,
                                        void* stream) {
   int device = 0, N = 0, f64 = 0, real = 0;
-  long long ng = 0;
+  long long ng = 0, ld = 0;
   double dv = 0.0;
   if (!p) return ace_internal_set_error(ACE_ERR_ARG, "plan is NULL");
-  ace_internal_plan_info(p, &device, &N, &ng, &dv, &f64, &real);
+  ace_internal_plan_info(p, &device, &N, &ng, &ld, &dv, &f64, &real);
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != device)
     return ace_internal_set_error(ACE_ERR_ARG, "current device differs from the plan's device");
@@ -80,9 +80,9 @@ extern "C" ace_status ace_apply_static(ace_plan* p, const void* Xi, const void* 
   double* part = static_cast<double*>(base);
   double* Cm = part + (size_t)splits * N * nb * 2;
   cudaStream_t st = (cudaStream_t)stream;
-  ace::launch_gram(f64 != 0, real != 0, Xi, N, Psi, nb, ng, ng, part, splits, st);
+  ace::launch_gram(f64 != 0, real != 0, Xi, N, Psi, nb, ld, ng, part, splits, st);
   ace::launch_gram_reduce(part, splits, N, nb, dv, false, false, Cm, nullptr, st);
-  ace::launch_outer(f64 != 0, real != 0, Xi, N, Cm, nb, ng, ng, -1.0, Y, st);
+  ace::launch_outer(f64 != 0, real != 0, Xi, N, Cm, nb, ld, ng, -1.0, Y, st);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return ace_internal_set_error(ACE_ERR_CUDA, (std::string("ace_apply_static: ") + cudaGetErrorString(e)).c_str());

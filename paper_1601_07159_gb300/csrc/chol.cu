@@ -326,12 +326,17 @@ __global__ void scale_kernel_d(double* x, long long count, double s) {
     x[i] *= s;
 }
 
-// X *= s over `count` stored vector elements (real and imaginary parts alike).
-void launch_scale(bool f64, bool real, void* X, long long count, double s, cudaStream_t st) {
-  const long long nreal = real ? count : 2 * count;
-  const unsigned grid = (unsigned)((nreal + 255) / 256 < 152 * 16 ? (nreal + 255) / 256 : 152 * 16);
-  if (f64) scale_kernel_d<<<grid, 256, 0, st>>>(static_cast<double*>(X), nreal, s);
-  else scale_kernel_f<<<grid, 256, 0, st>>>(static_cast<float*>(X), nreal, (float)s);
+// X *= s over the first ng elements of each of `count` vectors of stride ld
+// (real and imaginary parts alike): one packed run when ld == ng.
+void launch_scale(bool f64, bool real, void* X, long long count, long long ng, long long ld, double s,
+                  cudaStream_t st) {
+  const long long per = real ? 1 : 2;   // reals per element
+  const long long runs = ld == ng ? 1 : count, run = (ld == ng ? count * ng : ng) * per;
+  const unsigned grid = (unsigned)((run + 255) / 256 < 152 * 16 ? (run + 255) / 256 : 152 * 16);
+  for (long long v = 0; v < runs; ++v) {
+    if (f64) scale_kernel_d<<<grid, 256, 0, st>>>(static_cast<double*>(X) + v * ld * per, run, s);
+    else scale_kernel_f<<<grid, 256, 0, st>>>(static_cast<float*>(X) + v * ld * per, run, (float)s);
+  }
 }
 
 }  // namespace ace

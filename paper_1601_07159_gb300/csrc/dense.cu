@@ -332,6 +332,92 @@ void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C
   }
 }
 
+// Xi = W L^{-*} with FP64 arithmetic from FP32 vectors (the plain FP64 form
+// of Eq. Wtilde for FP32 storage): A is complex FP32 [nk][ld], promoted
+// exactly; C = L^{-*} is upper triangular, so the block of columns
+// [b0, b0 + OB) takes k < b0 + OB only; Out is complex FP32 (rounded once) or
+// FP64 [nb][ld].
+template <typename OUT>
+__global__ void __launch_bounds__(256)
+outer_f64acc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
+                    long long ng, OUT* __restrict__ Out) {
+  __shared__ double2 As[OK][OG];
+  __shared__ double2 Cs[OK][OB];
+  const int tg = threadIdx.x & 63, tb = threadIdx.x >> 6;
+  const long long g0 = (long long)blockIdx.x * OG;
+  const int b0 = blockIdx.y * OB;
+  const int rbb = nb - b0 - 4 * tb;
+  const int nj = rbb <= 0 ? 0 : (rbb < 4 ? rbb : 4);
+  const int kend = b0 + OB < nk ? b0 + OB : nk;   // C[k][b] = 0 for k > b
+  double2 acc[2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < kend; k0 += OK) {
+    const int kmax = kend - k0 < OK ? kend - k0 : OK;
+#pragma unroll
+    for (int e = 0; e < (OK * OG) / 256; ++e) {
+      const int idx = threadIdx.x + 256 * e;
+      const int kk = idx / OG, gg = idx % OG;
+      const long long g = g0 + gg;
+      double2 v = make_double2(0.0, 0.0);
+      if (k0 + kk < kend && g < ng) {
+        const float2 t = A[(long long)(k0 + kk) * ld + g];
+        v = make_double2((double)t.x, (double)t.y);
+      }
+      As[kk][gg] = v;
+    }
+    {
+      const int kk = threadIdx.x / OB, bb = threadIdx.x % OB;
+      double2 c = make_double2(0.0, 0.0);
+      if (k0 + kk < kend && b0 + bb < nb) {
+        const long long o = 2 * ((long long)(k0 + kk) * nb + b0 + bb);
+        c = make_double2(C[o], C[o + 1]);
+      }
+      Cs[kk][bb] = c;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < OK; ++k) {
+      if (k >= kmax) break;
+      double2 av[2], cv[4];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) av[i] = As[k][tg + 64 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cv[j] = Cs[k][tb * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (j < nj) acc[i][j] = cadd(acc[i][j], cmul(av[i], cv[j]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const long long g = g0 + tg + 64 * i;
+    if (g >= ng) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + tb * 4 + j;
+      if (b >= nb) continue;
+      OUT o;
+      o.x = acc[i][j].x;
+      o.y = acc[i][j].y;
+      Out[(long long)b * ld + g] = o;
+    }
+  }
+}
+
+void launch_outer_f64acc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,
+                         bool out_f64, cudaStream_t st) {
+  const dim3 grid((unsigned)((ng + OG - 1) / OG), (nb + OB - 1) / OB);
+  const float2* a = static_cast<const float2*>(A);
+  if (out_f64) outer_f64acc_kernel<double2><<<grid, 256, 0, st>>>(a, nk, C, nb, ld, ng, static_cast<double2*>(Out));
+  else outer_f64acc_kernel<float2><<<grid, 256, 0, st>>>(a, nk, C, nb, ld, ng, static_cast<float2*>(Out));
+}
+
 // Cholesky + inverse (FP64): chol.cu
 
 // ---------------------------------------------------------------- reductions

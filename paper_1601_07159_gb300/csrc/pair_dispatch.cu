@@ -3,7 +3,7 @@
 
 // Keep in step with EDGES_F32 / EDGES_F64 in build_lib.py.
 #define ACE_EDGES_F32(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(64) X(96)
-#define ACE_EDGES_F64(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48)
+#define ACE_EDGES_F64(X) X(8) X(12) X(16) X(20) X(24) X(32) X(36) X(40) X(48) X(64) X(96)
 
 namespace ace {
 

@@ -505,8 +505,11 @@ template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
 }
 constexpr int kBSplitPencils = 128;   // pencils per 256-thread block of the split pass B
 
+// FP64 pencils of 64+ points need the whole register file of a thread: one block per SM.
+template <typename R, int N> constexpr int kBSplitBlocks = sizeof(R) == 8 ? 1 : 2;
+
 template <typename R, int N>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, kBSplitBlocks<R, N>)
 pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
   using C = cplx<R>;
   constexpr int N2 = N * N, M = N / 2, H = N / 4;
@@ -613,10 +616,14 @@ __device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)
 // fit an SM where the one-thread-per-line form runs 15 warps at 117-128.
 // Below 48 the whole-line form is as fast (several planes per block). Pass A
 // at 48^3 is held to 80 registers (eight blocks, 24 warps): 1.3 % faster steps.
+// FP64 lines take the two-lane form from n = 64 (a whole FP64 line of 64 would
+// not fit a thread's registers), with one or two blocks per SM.
 constexpr int kSplitMinEdge = 48;
-template <typename R, int N> constexpr bool kSplitPlanes = sizeof(R) == 4 && N >= kSplitMinEdge && N % 4 == 0;
-template <int N> constexpr int kSplitBlocks = N >= 96 ? 2 : 6;
-template <int N> constexpr int kSplitBlocksA = N == 48 ? 8 : kSplitBlocks<N>;
+constexpr int kSplitMinEdgeF64 = 64;
+template <typename R, int N> constexpr bool kSplitPlanes =
+    N % 4 == 0 && (sizeof(R) == 4 ? N >= kSplitMinEdge : N >= kSplitMinEdgeF64);
+template <typename R, int N> constexpr int kSplitBlocks = sizeof(R) == 8 ? (N >= 96 ? 1 : 2) : (N >= 96 ? 2 : 6);
+template <typename R, int N> constexpr int kSplitBlocksA = sizeof(R) == 4 && N == 48 ? 8 : kSplitBlocks<R, N>;
 template <typename R, int N> constexpr size_t kSplitSmem = (size_t)N * (N + 1) * sizeof(cplx<R>);
 
 // frequency index held in y[j] by lane h
@@ -630,7 +637,7 @@ template <int N> __device__ __forceinline__ int split_index(int j, int h) {
 // registers of a whole line per thread (which at 96^3 would need over 200), so
 // more warps per SM hide the latency of the plane loads and stores.
 template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(2 * N, kSplitBlocksA<N>)
+__global__ void __launch_bounds__(2 * N, kSplitBlocksA<R, N>)
 pass_a_split_kernel(const __grid_constant__ PairParams<R, N> P) {
   using C = cplx<R>;
   constexpr int M = N / 2;
@@ -668,7 +675,7 @@ pass_a_split_kernel(const __grid_constant__ PairParams<R, N> P) {
 }
 
 template <typename R, int N>
-__global__ void __launch_bounds__(2 * N, kSplitBlocks<N>)
+__global__ void __launch_bounds__(2 * N, kSplitBlocks<R, N>)
 pass_c_split_kernel(const __grid_constant__ PairParams<R, N> P) {
   using C = cplx<R>;
   constexpr int M = N / 2;
@@ -749,6 +756,8 @@ template <typename R, int N> struct EngineParams {
   unsigned* done;               // done[4 k + p]: finished tasks of pass p of batch k
   int* status;                  // plan status word: timeout -> ACE_ERR_TIMEOUT
   int mode;                     // 0: Poisson + accumulate; 1: energy only; 2: both
+  unsigned spin_limit;          // polls before a dependent wait gives up
+  unsigned wait_bias;           // added to every awaited count (0; a test hook)
 };
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
@@ -757,10 +766,12 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   return v;
 }
 
-// A wait gives up after ~2^22 sleeps of >= 256 ns (about a second or more);
-// the block then records ACE_ERR_TIMEOUT and leaves, and so do the blocks that
-// wait on it, so the launch always ends.
-constexpr unsigned kSpinLimit = 1u << 22;
+// A wait gives up after E.spin_limit polls (by default 2^22 sleeps of >= 256
+// ns, about a second or more); the block then records ACE_ERR_TIMEOUT and
+// leaves, and so do the blocks that wait on it, so the launch always ends. A
+// block only ever waits before it starts a task, with nothing of its own in
+// flight, so leaving is always safe. E.wait_bias > 0 (a test hook) asks for
+// more finished tasks than a pass has, so that every dependent wait runs out.
 
 template <typename R, int N, bool REAL>
 __global__ void __launch_bounds__(kEngineThreads, 2)
@@ -794,16 +805,16 @@ pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
         unsigned target = 0;
         if (pass > 0) {
           want = E.done + kCtrStride * (4 * k + pass - 1);
-          target = (unsigned)b.n[pass - 1];
+          target = (unsigned)b.n[pass - 1] + E.wait_bias;
         } else if (k > 0) {
           want = E.done + kCtrStride * (4 * (k - 1) + E.npasses - 1);
-          target = (unsigned)E.batches[k - 1].n[E.npasses - 1];
+          target = (unsigned)E.batches[k - 1].n[E.npasses - 1] + E.wait_bias;
         }
         if (want) {
           unsigned it = 0;
           while (ld_acquire(want) < target) {
             __nanosleep(it < 64 ? 32 : 256);
-            if (++it > kSpinLimit) {
+            if (++it > E.spin_limit) {
               E.status[0] = -6;   // ACE_ERR_TIMEOUT
               E.status[1] = (int)(t & 0x7fffffff);
               stop = 1;
@@ -874,8 +885,17 @@ void engine_tasks(const Batch& b, int n[4]) {
   n[3] = (int)((((long long)N * N * N + kEngineThreads - 1) / kEngineThreads) * b.ntiles);
 }
 
+// The persistent engine holds whole lines per thread; FP64 lines of 64 or more
+// points do not fit, so those edges have no engine (plans fall back to the four
+// kernels per batch).
+template <typename R, int N> constexpr bool kEngineBuilt = !(sizeof(R) == 8 && N >= kSplitMinEdgeF64);
+
 template <typename R, int N>
 void engine_prepare(EngineInfo& info) {
+  if constexpr (!kEngineBuilt<R, N>) {
+    info = EngineInfo{};
+    return;
+  } else {
   constexpr int IPB = engine_items<R, N>();
   constexpr size_t smem = (size_t)IPB * N * (N + 1) * sizeof(cplx<R>);
   info.smem = smem;
@@ -893,10 +913,14 @@ void engine_prepare(EngineInfo& info) {
   one(pair_engine_kernel<R, N, false>);
   if constexpr (sizeof(R) == 8) one(pair_engine_kernel<R, N, true>);
   info.blocks = occ > 0 ? occ * sms : 0;
+  }
 }
 
 template <typename R, int N>
 bool launch_engine(const PairLaunch& L, const EngineLaunch& EL, cudaStream_t st) {
+  if constexpr (!kEngineBuilt<R, N>) {
+    return false;
+  } else {
   EngineParams<R, N> E;
   Batch none{};
   fill_params<R, N>(E.P, L, none);
@@ -909,6 +933,8 @@ bool launch_engine(const PairLaunch& L, const EngineLaunch& EL, cudaStream_t st)
   E.done = EL.done;
   E.status = EL.status;
   E.mode = L.mode;
+  E.spin_limit = EL.spin_limit;
+  E.wait_bias = EL.wait_bias;
   cudaLaunchConfig_t cfg{};
   long long blocks = EL.blocks;
   if (blocks > EL.ntasks) blocks = EL.ntasks;
@@ -931,6 +957,7 @@ bool launch_engine(const PairLaunch& L, const EngineLaunch& EL, cudaStream_t st)
   if (L.real_io) return false;
   cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, false>, E);
   return true;
+  }
 }
 
 template <typename R, int N>
@@ -940,16 +967,21 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   if (L.prepare_only) {
     // opt in to > 48 KB of dynamic shared memory and the largest carveout; done
     // once at plan creation on the plan's device, never during stream capture
-    if constexpr (sizeof(R) == 8) {
-      cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    }
-    cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if constexpr (kSplitPlanes<R, N>) {
+    if constexpr (!kSplitPlanes<R, N>) {   // whole lines per thread
+      if constexpr (sizeof(R) == 8) {
+        cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
+      cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    } else {
       constexpr int s1 = (int)kSplitSmem<R, N>;
+      if constexpr (sizeof(R) == 8) {
+        cudaFuncSetAttribute(pass_a_split_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+        cudaFuncSetAttribute(pass_a_split_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
       cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
       cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
       cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -972,7 +1004,12 @@ bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
   mark(0);
   if (mask & 1) {
     if constexpr (kSplitPlanes<R, N>) {
-      launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, false>, dim3((unsigned)items), dim3(2 * N), kSplitSmem<R, N>, st, P);
+      if (sizeof(R) == 8 && L.real_io)
+        launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, sizeof(R) == 8>, dim3((unsigned)items), dim3(2 * N),
+                   kSplitSmem<R, N>, st, P);
+      else
+        launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, false>, dim3((unsigned)items), dim3(2 * N), kSplitSmem<R, N>,
+                   st, P);
     } else if constexpr (sizeof(R) == 8) {
       if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
       else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);

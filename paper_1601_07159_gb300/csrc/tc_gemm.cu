@@ -41,10 +41,15 @@
 #include <cstdint>
 
 #include "ace_internal.h"
+#include "tcgen05.cuh"
 
 namespace ace {
 
 namespace {
+
+using tc::smem_u32;
+using tc::mbar_init;
+using tc::mma_commit;
 
 constexpr int THREADS = 512;
 constexpr int TM = 128;                    // rows per CTA (M of the MMA)
@@ -68,15 +73,8 @@ template <int TN> struct Tile {
                                     ((uint32_t)(TM >> 4) << 24);
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// shared-memory matrix descriptor: start, LBO = 128 B, SBO, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t mat_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) |
-         ((uint64_t)(SBO >> 4) << 32) | (1ull << 46);
-}
+// shared-memory matrix descriptor of an operand tile (K-major, no swizzle)
+__device__ __forceinline__ uint64_t mat_desc(uint32_t addr) { return tc::kmajor_desc(addr, SBO); }
 
 // byte offset of element (row r, real k) in an operand tile
 __device__ __forceinline__ int tile_off(int r, int k) {
@@ -91,25 +89,9 @@ __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo
   *reinterpret_cast<float4*>(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
 // bounded wait for the phase with parity `parity`; false on timeout
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-  const uint32_t a = smem_u32(bar);
-  for (unsigned it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return tc::mbar_wait(bar, parity, kWaitLimit);
 }
 
 template <int TN>
@@ -120,11 +102,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(Tile<TN>::IDESC), "r"(accumulate)
       : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
 }
 
 // 32 consecutive accumulator columns of this thread's lane, added into acc[o .. o + 31]

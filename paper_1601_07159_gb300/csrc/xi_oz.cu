@@ -1,0 +1,400 @@
+// Xi = W L^{-*} (Eq. Wtilde) to FP64 accuracy on the FP16 tensor cores, for
+// FP32 vectors W: an error-free splitting of both operands into small-integer
+// slices (the Ozaki scheme), exact integer products on tcgen05 (kind::f16),
+// exact accumulation, and a single scaling to FP64 at the end.
+//
+// As in the tensor-core GEMMs of tc_gemm.cu the complex product is a real GEMM
+// on interleaved data: rows are grid points g, K' = 2 nk real terms (Re, Im of
+// W_k(g)), and a tile of BB complex output columns b is TN = 2 BB real columns
+// (j < BB: (Re C_kb, -Im C_kb) -> Re Xi_b; BB + j: (Im C_kb, Re C_kb) -> Im Xi_b).
+//
+// Splitting (beta = 8 bits per slice):
+//   row g of A is scaled by 2^-e_g, e_g the smallest exponent with |A_gk| < 2^e_g
+//   for every k; column b of C by 2^-f_b likewise. The scaled value x in (-1, 1)
+//   is peeled into signed digits d_1 = rint(2^8 x), d_s = rint(2^8 r_{s-1})
+//   with r the remainders (|d_1| <= 256, |d_s| <= 128), so that
+//   x = sum_s d_s 2^{-8 s} + O(2^{-8 S}); every step is exact in FP32 (A) or
+//   FP64 (C) arithmetic, and every digit is an integer that FP16 holds exactly.
+// Products:
+//   Xi_gb = 2^{e_g + f_b} sum_{s,t} 2^{-8 (s+t)} P_st,  P_st = sum_k a^(s)_gk c^(t)_kb,
+//   keeping the slice pairs with s + t <= T (T = 5 for FP32 output: truncation
+//   about 2^-40 of |A||C|; T = 6 for FP64 output). The products of one weight
+//   w = s + t share a tensor-memory accumulator. Over a group of 128 real K
+//   terms every partial sum is an integer below 2^24 in magnitude (at most 1.5
+//   2^16 per term and weight), so the FP32 accumulation is exact whatever its
+//   rounding; after each group the accumulators are read back (tcgen05.ld),
+//   converted to int32 exactly and added into per-thread int64 sums shifted by
+//   8 (T - w) bits (below 2^60: no overflow). The final value is
+//   ldexp((double)sum, e_g + f_b - 8 T), rounded once to the output type.
+//
+// Per CTA (512 threads, one per SM): T - 1 accumulators of TN columns in TMEM;
+// K runs in chunks of 32 real terms (16 orbitals) through three shared-memory
+// stages, each holding 4 A slices (split on the fly from the FP32 loads) and
+// the chunk's B slices (split once per call by oz_slice_b_kernel into the
+// stage layout, copied in with 16-byte loads). One thread issues the MMAs of a
+// chunk (2 K-steps per slice pair) and commits them to the stage's mbarrier;
+// the threads drain the accumulators after the last chunk of each group.
+// L^{-*} is upper triangular, so tile [b0, b0 + BB) runs k < b0 + BB only.
+// Every mbarrier wait is bounded: on timeout the CTA records ACE_ERR_TIMEOUT,
+// stops issuing, waits (bounded) for what it issued and frees its TMEM.
+#include <cstdint>
+#include <cuda_fp16.h>
+
+#include "ace_internal.h"
+#include "tcgen05.cuh"
+
+namespace ace {
+
+namespace {
+
+constexpr int OZ_THREADS = 512;
+constexpr int OZ_TM = 128;                     // rows per CTA (M of the MMA)
+constexpr int OZ_KC = 32;                      // real K terms per chunk
+constexpr int OZ_SBO = (OZ_KC / 8) * 128;      // bytes between 8-row groups of 16-bit elements = 512
+constexpr int OZ_BETA = 8;                     // bits per slice
+constexpr int OZ_GROUP = 4;                    // chunks per exact accumulation group (128 real K)
+constexpr int OZ_NSTAGE = 3;
+constexpr unsigned kOzWaitLimit = 1u << 24;
+
+template <int T> struct Oz {
+  static_assert(T == 5 || T == 6, "slice depth");
+  static constexpr int SA = 4;                 // A slices: 32 bits below the row maximum
+  static constexpr int SB = T - 1;             // C slices
+  static constexpr int NW = T - 1;             // accumulators, weights w = 2 .. T
+  static constexpr int TN = T == 5 ? 128 : 96; // NW x TN <= 512 TMEM columns
+  static constexpr int BB = TN / 2;
+  static constexpr int NACC = TN / 4;          // columns per thread (4 column groups of warps)
+  static constexpr int A_SLICE = OZ_TM * OZ_KC * 2;
+  static constexpr int B_SLICE = TN * OZ_KC * 2;
+  static constexpr int STAGE = SA * A_SLICE + SB * B_SLICE;
+  static constexpr int SMEM = OZ_NSTAGE * STAGE + 1024 + 64;
+  // instruction descriptor: D = F32, A = B = F16, both K-major, N = TN, M = 128
+  static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(OZ_TM >> 4) << 24);
+};
+
+// byte offset of (row r, real k) in a 16-bit operand tile of one chunk
+__device__ __forceinline__ int oz_off(int r, int k) {
+  return (r >> 3) * OZ_SBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ unsigned short f16_bits(float d) { return __half_as_ushort(__float2half_rn(d)); }
+
+template <int T>
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(Oz<T>::IDESC), "r"(accumulate)
+      : "memory");
+}
+
+// smallest e with |x| < 2^e (0 for x == 0)
+__device__ __forceinline__ int exp_above(double m) {
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  return e;
+}
+
+// e_g for every grid point: the row maximum of |Re W_k(g)|, |Im W_k(g)| over k.
+__global__ void oz_row_exp_kernel(const float2* __restrict__ A, int nk, long long ld, long long ng,
+                                  int* __restrict__ erow) {
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += (long long)gridDim.x * blockDim.x) {
+    float m = 0.f;
+    for (int k = 0; k < nk; ++k) {
+      const float2 v = A[(long long)k * ld + g];
+      m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    erow[g] = exp_above((double)m);
+  }
+}
+
+// One block per complex column b of C (FP64 [nk][nb], upper triangular): f_b,
+// then the SB digits of the column's real entries, written into the stage
+// layout of chunk c = k / 16, tile bt = b / BB: Bsl[((bt * nch + c) * SB + t)]
+// holds a TN x 32 16-bit operand tile. Bsl must be zero beforehand (padding).
+template <int T>
+__global__ void __launch_bounds__(256)
+oz_slice_b_kernel(const double* __restrict__ C, int nk, int nb, int nch, unsigned short* __restrict__ Bsl,
+                  int* __restrict__ fcol) {
+  using O = Oz<T>;
+  __shared__ double red[256];
+  const int b = blockIdx.x;
+  const int kend = b + 1 < nk ? b + 1 : nk;          // C[k][b] = 0 for k > b
+  double m = 0.0;
+  for (int k = threadIdx.x; k < kend; k += blockDim.x) {
+    const long long o = 2 * ((long long)k * nb + b);
+    m = fmax(m, fmax(fabs(C[o]), fabs(C[o + 1])));
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  const int f = exp_above(red[0]);
+  if (threadIdx.x == 0) fcol[b] = f;
+  const int bt = b / O::BB, j = b % O::BB;
+  for (int k = threadIdx.x; k < kend; k += blockDim.x) {
+    const long long o = 2 * ((long long)k * nb + b);
+    const double re = C[o], im = C[o + 1];
+    const int c = k / 16, kk = 2 * (k % 16);          // real rows kk (Re A) and kk + 1 (Im A)
+    unsigned short* tile = Bsl + (size_t)(bt * nch + c) * O::SB * (O::TN * OZ_KC);
+    // (row j: Re C, -Im C), (row BB + j: Im C, Re C)
+    const double v[4] = {re, -im, im, re};
+    const int rr[4] = {j, j, O::BB + j, O::BB + j}, kr[4] = {kk, kk + 1, kk, kk + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double x = ldexp(v[q], OZ_BETA - f);
+#pragma unroll
+      for (int t = 0; t < O::SB; ++t) {
+        const double d = rint(x);
+        x = (x - d) * (double)(1 << OZ_BETA);
+        tile[(size_t)t * (O::TN * OZ_KC) + oz_off(rr[q], kr[q]) / 2] = f16_bits((float)d);
+      }
+    }
+  }
+}
+
+// Grid: (ceil(nb / BB), ceil(ng / 128)). A: complex FP32 [nk][ld]; Out: complex
+// FP32 or FP64 [nb][ld].
+template <int T, typename OUT>
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long long ng,
+                const int* __restrict__ erow, const unsigned short* __restrict__ Bsl, const int* __restrict__ fcol,
+                int nch, OUT* __restrict__ Out, int* status) {
+  using O = Oz<T>;
+  constexpr int NACC = O::NACC;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + OZ_NSTAGE * O::STAGE);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + OZ_NSTAGE * O::STAGE + 32);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int i = 0; i < OZ_NSTAGE; ++i) tc::mbar_init(&bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  if (tid < 32) tc::tmem_alloc_warp(tmem_slot, 512);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+
+  const int bt = blockIdx.x, b0 = bt * O::BB;
+  const long long g0 = (long long)blockIdx.y * OZ_TM;
+  const int kend = b0 + O::BB < nk ? b0 + O::BB : nk;
+  const int nchunks = (kend + 15) / 16;
+  // this thread's A elements: row r = tid % 128, real K 4q .. 4q + 3 with q = tid / 128 and q + 4
+  const int r = tid & 127, q = tid >> 7;
+  const long long g = g0 + r;
+  const int er = g < ng ? erow[g] : 0;
+  const float sa = ldexpf(1.0f, OZ_BETA - er);       // exact power of two
+  const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(NACC * (w >> 2));
+
+  long long acc[NACC];
+#pragma unroll
+  for (int j = 0; j < NACC; ++j) acc[j] = 0;
+
+  auto load_a = [&](int c, float4 (&v)[2]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int k = c * 16 + 2 * (q + 4 * i);
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (g < ng) {
+        if (k < kend) { const float2 x = A[(long long)k * ld + g]; t.x = x.x; t.y = x.y; }
+        if (k + 1 < kend) { const float2 x = A[(long long)(k + 1) * ld + g]; t.z = x.x; t.w = x.y; }
+      }
+      v[i] = t;
+    }
+  };
+  // the 4 A slices of this thread's 8 values into stage `st`
+  auto store_a = [&](unsigned char* st, const float4 (&v)[2]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      float x[4] = {v[i].x * sa, v[i].y * sa, v[i].z * sa, v[i].w * sa};
+      const int off = oz_off(r, 4 * (q + 4 * i));
+#pragma unroll
+      for (int s = 0; s < O::SA; ++s) {
+        unsigned short h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float d = rintf(x[e]);
+          x[e] = (x[e] - d) * (float)(1 << OZ_BETA);
+          h[e] = f16_bits(d);
+        }
+        uint2 u;
+        u.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
+        u.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+        *reinterpret_cast<uint2*>(st + s * O::A_SLICE + off) = u;
+      }
+    }
+  };
+  auto copy_b = [&](unsigned char* st, int c) {
+    const uint4* src = reinterpret_cast<const uint4*>(Bsl + (size_t)(bt * nch + c) * O::SB * (O::TN * OZ_KC));
+    uint4* dst = reinterpret_cast<uint4*>(st + O::SA * O::A_SLICE);
+    constexpr int N16 = O::SB * O::B_SLICE / 16;
+    for (int i = tid; i < N16; i += OZ_THREADS) dst[i] = src[i];
+  };
+  auto issue = [&](const unsigned char* st, bool group_first) {
+    const uint32_t a0 = tc::smem_u32(st), bb0 = a0 + O::SA * O::A_SLICE;
+    bool first[O::NW];
+#pragma unroll
+    for (int i = 0; i < O::NW; ++i) first[i] = group_first;
+#pragma unroll
+    for (int wt = 2; wt <= T; ++wt) {
+#pragma unroll
+      for (int s = 1; s <= O::SA; ++s) {
+        const int t = wt - s;
+        if (t < 1 || t > O::SB) continue;
+#pragma unroll
+        for (int ks = 0; ks < OZ_KC / 16; ++ks) {
+          const uint32_t o = ks * 256;    // two core matrices of 16 B along K per K-step of 16
+          mma_f16<T>(tmem + (uint32_t)((wt - 2) * O::TN), tc::kmajor_desc(a0 + (s - 1) * O::A_SLICE + o, OZ_SBO),
+                     tc::kmajor_desc(bb0 + (t - 1) * O::B_SLICE + o, OZ_SBO), first[wt - 2] ? 0u : 1u);
+          first[wt - 2] = false;
+        }
+      }
+    }
+  };
+  auto drain = [&]() {
+    tc::fence_after_sync();
+#pragma unroll
+    for (int wt = 2; wt <= T; ++wt) {
+      const uint32_t ta = tmem + lane_col + (uint32_t)((wt - 2) * O::TN);
+      const int sh = OZ_BETA * (T - wt);
+      uint32_t v[32];
+      if constexpr (NACC == 32) {
+        tc::tmem_ld32(ta, v);
+      } else {
+        tc::tmem_ld16(ta, v);
+        tc::tmem_ld8(ta + 16, v + 16);
+      }
+      tc::tmem_wait_ld();
+#pragma unroll
+      for (int j = 0; j < NACC; ++j) acc[j] += (long long)__float2int_rn(__uint_as_float(v[j])) << sh;
+    }
+    tc::fence_before_sync();
+  };
+
+  unsigned phase = 0, issued = 0;
+  bool ok = true;
+  auto settle = [&](int s) -> bool {
+    if (!tc::mbar_wait(&bar[s], (phase >> s) & 1u, kOzWaitLimit)) return false;
+    phase ^= 1u << s;
+    issued &= ~(1u << s);
+    return true;
+  };
+  float4 cur[2], nxt[2];
+  if (nchunks > 0) load_a(0, cur);
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c % OZ_NSTAGE;
+    unsigned char* st = base + s * O::STAGE;
+    if (c + 1 < nchunks) load_a(c + 1, nxt);
+    if (((issued >> s) & 1u) && !settle(s)) s_fail = 1;   // chunk c - NSTAGE read this stage
+    store_a(st, cur);
+    copy_b(st, c);
+    tc::fence_async_smem();
+    __syncthreads();
+    if (s_fail) { ok = false; break; }
+    if (tid == 0) {
+      tc::fence_after_sync();
+      issue(st, (c % OZ_GROUP) == 0);
+      tc::mma_commit(&bar[s]);
+    }
+    issued |= 1u << s;
+    if ((c % OZ_GROUP) == OZ_GROUP - 1 || c == nchunks - 1) {
+      if (!settle(s)) { s_fail = 1; }                     // every MMA so far has completed
+      else drain();
+      __syncthreads();
+      if (s_fail) { ok = false; break; }
+    }
+    cur[0] = nxt[0];
+    cur[1] = nxt[1];
+  }
+  // commits still outstanding (bounded; also after a lost wait)
+  for (int i = 0; i < OZ_NSTAGE; ++i)
+    if (((issued >> i) & 1u) && !settle(i)) ok = false;
+  __syncthreads();
+  if ((!ok || s_fail) && tid == 0) {
+    status[0] = -6;   // ACE_ERR_TIMEOUT
+    status[1] = -3;
+  }
+  if (ok && !s_fail) {
+    const int row = 32 * (w & 3) + lane;
+    const long long gg = g0 + row;
+    const int ergg = gg < ng ? erow[gg] : 0;
+    const int ri = (w >> 2) >= 2 ? 1 : 0;                 // column groups 0-1 real, 2-3 imaginary
+    const int jq = ((w >> 2) & 1) * NACC;
+    if (gg < ng) {
+#pragma unroll
+      for (int j = 0; j < NACC; ++j) {
+        const int b = b0 + jq + j;
+        if (b < nb) {
+          const double val = ldexp((double)acc[j], ergg + fcol[b] - OZ_BETA * T);
+          if constexpr (sizeof(OUT) == 8) reinterpret_cast<float*>(Out)[2 * ((long long)b * ld + gg) + ri] = (float)val;
+          else reinterpret_cast<double*>(Out)[2 * ((long long)b * ld + gg) + ri] = val;
+        }
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (tid < 32) tc::tmem_dealloc_warp(tmem, 512);
+}
+
+template <int T> size_t oz_bsl_bytes(int nk, int nb) {
+  using O = Oz<T>;
+  const size_t ntiles = (size_t)(nb + O::BB - 1) / O::BB;
+  const size_t nch = (size_t)(nk + 15) / 16;
+  return ntiles * nch * O::SB * O::TN * OZ_KC * 2;
+}
+
+size_t align256_(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+bool xi_oz_prepare() {
+  cudaFuncSetAttribute(oz_outer_kernel<5, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Oz<5>::SMEM);
+  cudaFuncSetAttribute(oz_outer_kernel<6, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Oz<6>::SMEM);
+  return cudaGetLastError() == cudaSuccess;
+}
+
+size_t xi_oz_scratch_bytes(long long ng, int nk, int nb, bool out_f64) {
+  const size_t bsl = out_f64 ? oz_bsl_bytes<6>(nk, nb) : oz_bsl_bytes<5>(nk, nb);
+  return align256_((size_t)ng * sizeof(int)) + align256_((size_t)nb * sizeof(int)) + align256_(bsl);
+}
+
+int launch_xi_oz(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,
+                 bool out_f64, void* scratch, int* status, cudaStream_t st) {
+  char* p = static_cast<char*>(scratch);
+  int* erow = reinterpret_cast<int*>(p);
+  p += align256_((size_t)ng * sizeof(int));
+  int* fcol = reinterpret_cast<int*>(p);
+  p += align256_((size_t)nb * sizeof(int));
+  unsigned short* bsl = reinterpret_cast<unsigned short*>(p);
+  const float2* a = static_cast<const float2*>(A);
+  const int nch = (nk + 15) / 16;
+  const unsigned rgrid = (unsigned)((ng + 255) / 256 < 152 * 8 ? (ng + 255) / 256 : 152 * 8);
+  oz_row_exp_kernel<<<rgrid, 256, 0, st>>>(a, nk, ld, ng, erow);
+  if (out_f64) {
+    using O = Oz<6>;
+    cudaMemsetAsync(bsl, 0, oz_bsl_bytes<6>(nk, nb), st);
+    oz_slice_b_kernel<6><<<nb, 256, 0, st>>>(C, nk, nb, nch, bsl, fcol);
+    const dim3 grid((nb + O::BB - 1) / O::BB, (unsigned)((ng + OZ_TM - 1) / OZ_TM));
+    oz_outer_kernel<6, double2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
+                                                                    static_cast<double2*>(Out), status);
+  } else {
+    using O = Oz<5>;
+    cudaMemsetAsync(bsl, 0, oz_bsl_bytes<5>(nk, nb), st);
+    oz_slice_b_kernel<5><<<nb, 256, 0, st>>>(C, nk, nb, nch, bsl, fcol);
+    const dim3 grid((nb + O::BB - 1) / O::BB, (unsigned)((ng + OZ_TM - 1) / OZ_TM));
+    oz_outer_kernel<5, float2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
+                                                                   static_cast<float2*>(Out), status);
+  }
+  return 3;
+}
+
+}  // namespace ace

@@ -174,3 +174,50 @@ def directions(shape, count: int, seed: int, dv: float) -> np.ndarray:
     d = rng.standard_normal((count,) + tuple(shape)) + 1j * rng.standard_normal((count,) + tuple(shape))
     nrm = np.sqrt(dv * np.sum(np.abs(d) ** 2, axis=tuple(range(1, d.ndim))))
     return d / nrm.reshape((count,) + (1,) * len(shape))
+
+
+# --------------------------------------------------------------------------
+# The same recipe on a CUDA device (torch), for workloads whose host QR and
+# host arrays are too large to build per run (96^3 x 1024 orbitals: 14.5 GB in
+# FP64, a 884736 x 1024 QR). The random stream is torch's, so these arrays are
+# not the host ones above; the distribution and structure are the same.
+# --------------------------------------------------------------------------
+def _device_coefficients(sysm: System, count: int, gen, ecut: float, device):
+    import torch
+    n = sysm.n
+    m = torch.fft.fftfreq(n, d=1.0 / n, device=device, dtype=torch.float64) * (2 * math.pi / sysm.L)
+    g2 = m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2
+    decay = torch.where(0.5 * g2 <= ecut, torch.exp(-g2 / (2 * ecut)), torch.zeros_like(g2)).to(torch.float32)
+    out = torch.empty((count, n, n, n), dtype=torch.complex64, device=device)
+    for i in range(0, count, 64):
+        k = min(64, count - i)
+        c = torch.complex(torch.randn((k, n, n, n), generator=gen, device=device),
+                          torch.randn((k, n, n, n), generator=gen, device=device)) / math.sqrt(2.0)
+        out[i:i + k] = torch.fft.ifftn(c * decay, dim=(1, 2, 3)) * n ** 3
+    return out
+
+
+def orbitals_device(sysm: System, seed: int, device="cuda", ecut: float = ECUT_HA):
+    """Orthonormal complex orbitals (N, n, n, n) complex64 on `device`: the
+    recipe of orbitals() with torch's generator and a QR on the device."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(seed)
+    phi = _device_coefficients(sysm, sysm.n_occ, gen, ecut, device)
+    q, r = torch.linalg.qr(math.sqrt(sysm.dv) * phi.reshape(sysm.n_occ, -1).T)
+    q = q * torch.sgn(torch.diagonal(r).real)[None, :]
+    del phi, r
+    return (q.T / math.sqrt(sysm.dv)).contiguous().reshape(sysm.n_occ, sysm.n, sysm.n, sysm.n)
+
+
+def targets_device(sysm: System, seed: int, count: int | None = None, device="cuda", ecut: float = ECUT_HA):
+    """Target vectors (count, n, n, n) complex64 on `device`, each normalised,
+    not orthogonalised: the recipe of targets() with torch's generator."""
+    import torch
+    count = sysm.n_bands if count is None else count
+    gen = torch.Generator(device=device).manual_seed(seed + 500)
+    psi = _device_coefficients(sysm, count, gen, ecut, device)
+    for i in range(0, count, 64):
+        blk = psi[i:i + 64]
+        nrm = torch.sqrt(sysm.dv * torch.sum(torch.abs(blk) ** 2, dim=(1, 2, 3)))
+        blk /= nrm[:, None, None, None]
+    return psi

@@ -52,11 +52,16 @@ def test_validation_without_gpu(lib):
 
     def make(**kw):
         d = Desc()
-        d.n, d.n_occ, d.dtype, d.kernel = 24, 8, 2, 0
+        d.n_occ, d.dtype, d.kernel = 8, 2, 0
+        d.n[0] = d.n[1] = d.n[2] = 24
         d.L[0] = d.L[1] = d.L[2] = 10.0
         d.omega, d.g0_value, d.alpha, d.max_pairs, d.tile = 0.0, math.nan, 1.0, 0, 0
         for k, v in kw.items():
-            setattr(d, k, v)
+            if k == "n":
+                v = (v,) * 3 if isinstance(v, int) else v
+                d.n[0], d.n[1], d.n[2] = v
+            else:
+                setattr(d, k, v)
         return d
 
     h = ctypes.c_void_p()
@@ -68,8 +73,15 @@ def test_validation_without_gpu(lib):
     assert lib.ace_plan_create(ctypes.byref(make(tile=9)), ctypes.byref(h)) == ACE_ERR_ARG
     assert lib.ace_plan_create(ctypes.byref(make(n=50)), ctypes.byref(h)) == ACE_ERR_UNSUPPORTED
     assert b"50" in lib.ace_last_error()
+    assert lib.ace_plan_create(ctypes.byref(make(n=(24, 24, 0))), ctypes.byref(h)) == ACE_ERR_ARG
+    assert lib.ace_plan_create(ctypes.byref(make(ld=24 ** 3 - 2)), ctypes.byref(h)) == ACE_ERR_ARG
+    assert lib.ace_plan_create(ctypes.byref(make(ld=24 ** 3 + 1)), ctypes.byref(h)) == ACE_ERR_ARG
+    assert lib.ace_plan_create(ctypes.byref(make(prec=9)), ctypes.byref(h)) == ACE_ERR_ARG
+    assert lib.ace_plan_create(ctypes.byref(make(dtype=1, prec=3)), ctypes.byref(h)) == ACE_ERR_UNSUPPORTED
+    assert h.value is None
     assert lib.ace_supported_edge(48, 2) == 1 and lib.ace_supported_edge(64, 2) == 1
-    assert lib.ace_supported_edge(7, 2) == 0 and lib.ace_supported_edge(64, 1) == 0
+    assert lib.ace_supported_edge(7, 2) == 0 and lib.ace_supported_edge(50, 1) == 0
+    assert lib.ace_supported_edge(64, 1) == 1 and lib.ace_supported_edge(96, 0) == 1
     assert lib.ace_workspace_size(None, 0, 4) == 0
 
 
@@ -91,3 +103,32 @@ def test_batched_and_autotune_validation_without_gpu(lib):
     assert lib.ace_build_batched(None, None, None, None, 1, -2, None, 0, None) == ACE_ERR_ARG
     assert lib.ace_workspace_size_batched(None, 3) == 0
     assert lib.ace_autotune(None, 3, None, None) == ACE_ERR_ARG
+
+
+def test_allocation_failure_hook_without_gpu(lib):
+    """ace_debug_fail_alloc makes the library's k-th device allocation fail as
+    if the device were out of memory: plan creation then returns ACE_ERR_CUDA
+    with that reason (here before any device is touched), leaves no plan, and
+    the hook reports how many allocations it counted. NULL plans are refused
+    by ace_debug_engine_wait."""
+    from paper_1601_07159_gb300.ace import Desc, ACE_ERR_ARG, ACE_ERR_CUDA
+    lib.ace_plan_create.restype = ctypes.c_int
+    lib.ace_last_error.restype = ctypes.c_char_p
+    lib.ace_debug_fail_alloc.restype = ctypes.c_longlong
+    lib.ace_debug_fail_alloc.argtypes = [ctypes.c_longlong]
+    lib.ace_debug_engine_wait.restype = ctypes.c_int
+    lib.ace_debug_engine_wait.argtypes = [ctypes.c_void_p, ctypes.c_uint, ctypes.c_int]
+    d = Desc()
+    d.n_occ, d.dtype, d.kernel = 4, 2, 0
+    d.n[0] = d.n[1] = d.n[2] = 16
+    d.L[0] = d.L[1] = d.L[2] = 8.0
+    d.omega, d.g0_value, d.alpha = 0.0, math.nan, 1.0
+    h = ctypes.c_void_p()
+    lib.ace_debug_fail_alloc(1)
+    try:
+        assert lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)) == ACE_ERR_CUDA
+        assert h.value is None
+        assert b"out of memory" in lib.ace_last_error()
+    finally:
+        assert lib.ace_debug_fail_alloc(0) == 1
+    assert lib.ace_debug_engine_wait(None, 0, 0) == ACE_ERR_ARG

@@ -68,6 +68,9 @@ CASES = [
     (48, 20.5, 17, 5, "c64", "erfc", 0.106),     # the 48^3 edge, ragged N
     (64, 27.3, 12, 4, "c64", "bare", 0.0),
     (96, 41.0, 5, 3, "c64", "erfc", 0.106),      # the 96^3 edge (Si512-like cell, h = 0.427)
+    (64, 27.3, 6, 3, "c128", "bare", 0.0),       # FP64 two-lane line transforms
+    (64, 27.3, 5, 2, "r64", "bare", 0.0),
+    (96, 41.0, 3, 2, "c128", "erfc", 0.106),
 ]
 
 
@@ -423,26 +426,6 @@ def test_poisson_hartree_parity(ace, n, L, dtype, kernel, omega):
         assert eh > 0
 
 
-def _gpu_orbitals(s, seed, ecut=synth.ECUT_HA):
-    """The synthetic recipe on the GPU for sizes a host QR cannot afford:
-    Gaussian-decaying complex coefficients on the sphere |G|^2/2 <= ecut, to
-    the grid by an inverse FFT, orthonormalised by a QR of sqrt(dV) Phi."""
-    n = s.n
-    g = torch.Generator(device="cuda").manual_seed(seed)
-    m = torch.fft.fftfreq(n, d=1.0 / n, device="cuda", dtype=torch.float64) * (2 * math.pi / s.L)
-    g2 = m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2
-    decay = torch.where(0.5 * g2 <= ecut, torch.exp(-g2 / (2 * ecut)), torch.zeros_like(g2)).to(torch.float32)
-    phi = torch.empty((s.n_occ, n, n, n), dtype=torch.complex64, device="cuda")
-    for i in range(0, s.n_occ, 64):
-        k = min(64, s.n_occ - i)
-        c = torch.complex(torch.randn((k, n, n, n), generator=g, device="cuda"),
-                          torch.randn((k, n, n, n), generator=g, device="cuda")) * decay
-        phi[i:i + k] = torch.fft.ifftn(c, dim=(1, 2, 3)) * n ** 3
-    q, r = torch.linalg.qr(math.sqrt(s.dv) * phi.reshape(s.n_occ, -1).T)
-    q = q * torch.sgn(torch.diagonal(r).real)[None, :]
-    return (q.T / math.sqrt(s.dv)).contiguous().reshape(s.n_occ, n, n, n)
-
-
 def test_si512_full_size(ace):
     """The large workload at full size (96^3, L = 41, N = 1024, screened
     kernel, FP32 pairs, TF32 3-term GEMMs, FP64 Cholesky), default plan:
@@ -451,7 +434,7 @@ def test_si512_full_size(ace):
     (Eq. EX_ACE) -- sampled W and M columns, and sampled single pair solves on
     the full grid, against the FP64 oracle."""
     s = synth.SI512_96
-    phi = _gpu_orbitals(s, synth.seed_for(5))
+    phi = synth.orbitals_device(s, synth.seed_for(5))
     plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega)
     out = plan.build(phi)
     assert plan.status() == (0, 0)
