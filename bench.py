@@ -103,7 +103,8 @@ def workload_config(name, s):
     return {"workload": name, "grid": f"{s.n}^3", "L_bohr": s.L, "n_occ": s.n_occ,
             "n_bands": s.n_bands, "kernel": f"erfc omega={s.omega}" if s.kernel == "erfc" else "bare",
             "orbitals": "seeded Gaussian-decaying plane waves |G|^2/2<=10 Ha, QR-orthonormal",
-            "precision": "fp32 pair/FFT path, TF32 3-term-split GEMMs, fp64 Cholesky and L^-1",
+            "precision": "fp32 pair/FFT path, TF32 3-term-split M and apply, fp64 Cholesky and L^-1, "
+                         "Xi = W L^-* to fp64 accuracy (fp16 tensor-core slices)",
             "l2": "working set > L2 every step (no flush needed)"}
 
 
@@ -563,7 +564,11 @@ def run_single(args):
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": Ke},
                 "gpu_launches": t["prof"]["launches"], "clocks": t["clocks"]}
-    del phi_d, psi_d, xi_d, y_d, plan
+    if rank == 0 and world == 1 and not args.no_extras:
+        del xi_d, y_d, plan
+        torch.cuda.empty_cache()
+        line["xi_variants"] = xi_variants(ace, s, phi_d, reps=1, warm=s.n < 96)
+    del phi_d, psi_d
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_extras:
         if name != SI64:
@@ -576,6 +581,38 @@ def run_single(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def xi_variants(ace, s, phi_d, reps, warm=True):
+    """Xi = W L^{-*} (Eq. Wtilde) three ways on the same W and L^{-*}: the
+    default FP64-accurate FP16-tensor-core slice product, the TF32 3-term-split
+    product and plain FP64 on CUDA cores; ms per whole ace_build with each, and
+    each Xi's relative difference to the plain-FP64 one. Without `warm` the
+    timed build also captures its graphs (a few ms, for seconds-long builds)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out, xis = {}, {}
+    for key, prec in (("fp64_slices", "xi_fp64"), ("tf32_split", "split_tf32"), ("fp64_cuda_cores", "xi_fp64_simt")):
+        plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega, prec=prec)
+        xi = plan.empty(s.n_occ)
+        if warm:
+            plan.build(phi_d, want_w=False, want_m=False, xi=xi)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            plan.build(phi_d, want_w=False, want_m=False, xi=xi)
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[key] = {"prec": prec, "ms_per_build": a.elapsed_time(b) / reps, "status": plan.status()[0]}
+        xis[key] = xi
+        del plan
+    ref = xis["fp64_cuda_cores"]
+    for key in out:
+        out[key]["xi_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(xis[key] - ref) / torch.linalg.vector_norm(ref))
+    del xis, ref
+    torch.cuda.empty_cache()
+    return out
 
 
 def si64_extra(ace, args, K=20):
@@ -606,6 +643,7 @@ def si64_extra(ace, args, K=20):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    out["xi_variants"] = xi_variants(ace, s, phi_d, reps=3)
     if not args.no_fp64:
         # plain-FP64 form of the same build: the denominator of the mixed-vs-FP64 ratio
         plan64 = ace.Plan(s.n, s.L, s.n_occ, dtype="c128", kernel=s.kernel, omega=s.omega)

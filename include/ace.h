@@ -67,21 +67,24 @@ typedef enum { ACE_KERNEL_BARE = 0, ACE_KERNEL_ERFC = 1, ACE_KERNEL_KINETIC = 2 
 typedef enum {
   ACE_OP_EXCHANGE_APPLY = 0, ACE_OP_BUILD = 1, ACE_OP_APPLY = 2, ACE_OP_ENERGY_GRAD = 3,
   ACE_OP_BUILD_OVERSAMPLED = 4,  /* n_b = N_phi */
-  ACE_OP_POISSON = 5             /* n_b = number of densities */
+  ACE_OP_POISSON = 5,            /* n_b = number of densities */
+  ACE_OP_ENERGY_GRAD_STORE = 6   /* ace_exchange_energy_grad with recompute = 0 */
 } ace_op;
 
 /* Arithmetic of the dense steps (M = Phi^* W, Xi = W L^{-*}, the apply) for
  * ACE_DTYPE_C64 plans; FP64 plans (R64, C128) compute everything in FP64 on
  * CUDA cores and accept ACE_PREC_DEFAULT only. The Cholesky factor and
  * L^{-1} are FP64 in every mode.
- *  ACE_PREC_DEFAULT / ACE_PREC_SPLIT_TF32: tcgen05 TF32 tensor cores, each FP32
- *    operand split into two TF32 terms, three products (FP32 accuracy).
- *  ACE_PREC_FP32: FP32 on CUDA cores.
- *  ACE_PREC_XI_FP64: as SPLIT_TF32, except Xi = W L^{-*}, which is computed to
- *    FP64 accuracy from the FP32 W and the FP64 L^{-*} on the FP16 tensor cores
- *    (error-free 8-bit integer slices of both operands, exact integer products,
- *    exact accumulation) and rounded once to FP32.
- *  ACE_PREC_XI_FP64_SIMT: the same Xi with plain FP64 arithmetic on CUDA cores. */
+ *  ACE_PREC_SPLIT_TF32: tcgen05 TF32 tensor cores for all three products, each
+ *    FP32 operand split into two TF32 terms, three products (FP32 accuracy).
+ *  ACE_PREC_XI_FP64 (the C64 default, ACE_PREC_DEFAULT): as SPLIT_TF32, except
+ *    Xi = W L^{-*}, which is computed to FP64 accuracy from the FP32 W and the
+ *    FP64 L^{-*} on the FP16 tensor cores (error-free 8-bit integer slices of
+ *    both operands, exact integer products, exact accumulation) and rounded
+ *    once to FP32: before that rounding the error of Xi_b(g) is below about
+ *    2^-41 max_k |W_k(g)| sum_k |(L^{-*})_kb|.
+ *  ACE_PREC_XI_FP64_SIMT: the same Xi with plain FP64 arithmetic on CUDA cores.
+ *  ACE_PREC_FP32: all three products in FP32 on CUDA cores. */
 typedef enum {
   ACE_PREC_DEFAULT = 0,
   ACE_PREC_SPLIT_TF32 = 1,
@@ -122,7 +125,8 @@ typedef struct {
  * take pass tasks from an ordered queue and wait, with a bounded spin, on
  * per-batch completion counters) instead of the default four kernels per
  * batch (passes A-D chained by programmatic dependent launch). A wait that runs
- * out (about a second) leaves ACE_ERR_TIMEOUT in the status word. */
+ * out (about a second) leaves ACE_ERR_TIMEOUT in the status word. Cubic grids
+ * only (FP64: edges up to 48); elsewhere the flag is ignored. */
 #define ACE_FLAG_ENGINE 2
 /* Launch the four pass kernels without programmatic dependent launch (a
  * tuning and diagnosis switch). With ACE_FLAG_NO_GRAPH and without
@@ -144,7 +148,11 @@ typedef struct ace_plan ace_plan;
  * lengths; radices 2, 3, 4, 5). */
 int ace_supported_edge(int n, int dtype);
 
-/* Nonzero when the n[0] x n[1] x n[2] grid is compiled in for the dtype. */
+/* Nonzero when the n[0] x n[1] x n[2] grid is compiled in for the dtype: its
+ * plane n[0] x n[1] (every square plane of a compiled edge, plus the listed
+ * non-square planes 12x16, 16x12, 16x24, 24x16, 40x48, 48x40) and its pencil
+ * length n[2] (any compiled edge). Compiled edges: 8, 12, 16, 20, 24, 32, 36,
+ * 40, 48, 64, 96 for every dtype. */
 int ace_supported_grid(const int n[3], int dtype);
 
 /* Validate *desc and build a plan on the current device: Coulomb kernel table,
@@ -246,11 +254,26 @@ ace_status ace_apply(ace_plan* plan, const void* Xi, const void* Psi, int n_b, v
                      void* ws, size_t ws_bytes, void* stream);
 
 /* E_x[Phi] (Eq. EX, via Parseval: -1/2 sum_ij Omega sum_G K |rho_hat_ij|^2, FP64
- * accumulation) into device Ex_out[0]; when grad_out is non-NULL also
- * grad_out = grad_scale * 2 dV W (the gradient dE/dRe(phi) + i dE/dIm(phi);
- * W recomputed, pair potentials never stored). */
+ * accumulation) into device Ex_out[0], and the gradient grad_out = grad_scale
+ * * 2 dV W (dE/dRe(phi) + i dE/dIm(phi)) when grad_out is non-NULL.
+ *
+ * recompute != 0: the pair potentials v_ij are formed and consumed batch by
+ * batch and never kept: a call without grad_out runs the forward transforms
+ * and the energy sum only; a call with grad_out solves every pair once and
+ * accumulates the gradient in the same sweep. ws: ACE_OP_ENERGY_GRAD bytes.
+ *
+ * recompute == 0: the workspace keeps every unique pair potential (N(N+1)/2
+ * N_g complex values, ace_workspace_size(plan, ACE_OP_ENERGY_GRAD_STORE, 0)
+ * bytes) between two calls. A call without grad_out computes E_x and stores
+ * the potentials; a later call with grad_out forms the gradient from the
+ * stored potentials alone (the accumulate pass) and, if Ex_out is non-NULL,
+ * writes E_x again from the stored energy sums. Between the two calls the
+ * caller keeps ws and Phi unchanged and makes no other call with that ws; a
+ * gradient call without a preceding energy call on the same ws gives undefined
+ * values. The store trades N(N+1)/2 N_g complex values of memory for the
+ * second sweep of pair solves; the library never picks it by itself. */
 ace_status ace_exchange_energy_grad(ace_plan* plan, const void* Phi, double* Ex_out,
-                                    void* grad_out, double grad_scale, void* ws,
+                                    void* grad_out, double grad_scale, int recompute, void* ws,
                                     size_t ws_bytes, void* stream);
 
 /* Synchronise `stream` and read the plan's device status word: returns ACE_OK,

@@ -237,18 +237,76 @@ def _delta(shape) -> np.ndarray:
     return d
 
 
+def kernel_matrix(kern: np.ndarray) -> np.ndarray:
+    """K_mat[r, r'] = K_r(r - r') over all pairs of grid points (periodic)."""
+    n2, n1, n0 = kern.shape
+    kr = kernel_realspace(kern)
+    iz, iy, ix = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
+    iz, iy, ix = iz.ravel(), iy.ravel(), ix.ravel()
+    return kr[(iz[:, None] - iz[None, :]) % n2,
+              (iy[:, None] - iy[None, :]) % n1,
+              (ix[:, None] - ix[None, :]) % n0]
+
+
 def vx_matrix(phi: np.ndarray, kern: np.ndarray) -> np.ndarray:
     """Dense V_X on the grid from Eq. VXkernel: V_X(r, r') = -Gamma(r, r')
     K_r(r - r'), the Hadamard product of the density matrix
     Gamma(r,r') = sum_j phi_j(r) conj(phi_j(r')) with the Coulomb kernel.
     Acts on grid vectors as (V_X psi)(r) = sum_r' V_X(r, r') psi(r')."""
-    n2, n1, n0 = kern.shape
-    kr = kernel_realspace(kern)
-    iz, iy, ix = np.meshgrid(np.arange(n2), np.arange(n1), np.arange(n0), indexing="ij")
-    iz, iy, ix = iz.ravel(), iy.ravel(), ix.ravel()
-    kmat = kr[(iz[:, None] - iz[None, :]) % n2,
-              (iy[:, None] - iy[None, :]) % n1,
-              (ix[:, None] - ix[None, :]) % n0]
     p = _mat(np.asarray(phi, dtype=np.complex128))
     gamma = p @ p.conj().T
-    return -gamma * kmat
+    return -gamma * kernel_matrix(kern)
+
+
+# --------------------------------------------------------------------------
+# Self-consistent field of a model Hamiltonian (Eq. HF; the loops of Alg. 1/2)
+# --------------------------------------------------------------------------
+def model_scf(v_loc: np.ndarray, lengths, n_occ: int, mix: float = 0.5, tol: float = 1e-11,
+              max_iter: int = 300, real: bool = False) -> dict:
+    """Ground state of the spinless Hartree-Fock model H = -1/2 Laplacian +
+    V_loc + V_H[rho] + V_X[Gamma] (Eq. HF) on the grid of v_loc, by dense
+    diagonalisation: every iteration builds H as a dense N_g x N_g matrix
+    (the kinetic and Hartree parts from the periodic G-space kernels, V_X from
+    Eq. VXkernel with the current density matrix Gamma), takes its n_occ
+    lowest eigenvectors, and mixes Gamma linearly with the new one, until the
+    new Gamma equals the old to `tol`. The fixed point is the self-consistent
+    solution that Alg. 1 and Alg. 2 reach by their inner and outer loops.
+    Returns the orbitals [n_occ][grid] (dV sum |phi|^2 = 1), the n_occ lowest
+    eigenvalues of the final H, E_x = 1/2 dV sum_i <phi_i, V_X phi_i> and the
+    iteration count. Small grids only (N_g^2 dense matrices)."""
+    shape = v_loc.shape
+    ng = v_loc.size
+    vol = float(np.prod(lengths))
+    dv = vol / ng
+    kin = kinetic_kernel(shape, lengths)
+    bare = coulomb_kernel(shape, lengths, "bare")
+    unit = np.eye(ng).reshape((ng,) + shape)
+    t_mat = _mat(poisson(unit, kin))                 # column j = T e_j
+    k_mat = kernel_matrix(bare)
+    dtype = np.float64 if real else np.complex128
+
+    def hamiltonian(gamma):
+        rho = np.real(np.diag(gamma))
+        v_h = np.real(poisson(rho.reshape(shape), bare)).ravel()
+        h = t_mat + np.diag(v_loc.ravel() + v_h) - gamma * k_mat
+        h = 0.5 * (h + h.conj().T)
+        return (h.real if real else h).astype(dtype)
+
+    def occupied(h):
+        w, u = scipy.linalg.eigh(h)
+        phi = u[:, :n_occ] / math.sqrt(dv)           # dV sum |phi|^2 = 1
+        return w, phi, phi @ phi.conj().T
+
+    w, phi, gamma = occupied((t_mat + np.diag(v_loc.ravel())).real if real else t_mat + np.diag(v_loc.ravel()))
+    it = 0
+    for it in range(1, max_iter + 1):
+        w, phi, g_out = occupied(hamiltonian(gamma))
+        change = np.linalg.norm(g_out - gamma) / np.linalg.norm(g_out)
+        gamma = (1.0 - mix) * gamma + mix * g_out
+        if change < tol:
+            break
+    w, phi, gamma = occupied(hamiltonian(g_out))
+    vx_phi = -(gamma * k_mat) @ phi
+    ex = 0.5 * dv * float(np.real(np.sum(np.conj(phi) * vx_phi)))
+    orbitals = np.ascontiguousarray(phi.T).reshape((n_occ,) + shape)
+    return {"psi": orbitals, "eigenvalues": w[:n_occ], "ex": ex, "iterations": it}

@@ -34,6 +34,7 @@ DTYPES = {"r64": 0, "c128": 1, "c64": 2}
 TORCH_DTYPES = {"r64": torch.float64, "c128": torch.complex128, "c64": torch.complex64}
 KERNELS = {"bare": 0, "erfc": 1, "kinetic": 2}
 OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED, OP_POISSON = 0, 1, 2, 3, 4, 5
+OP_ENERGY_GRAD_STORE = 6
 
 
 PRECS = {"default": 0, "split_tf32": 1, "fp32": 2, "xi_fp64": 3, "xi_fp64_simt": 4}
@@ -87,7 +88,8 @@ _lib.ace_build.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _
 _lib.ace_build.restype = ctypes.c_int
 _lib.ace_apply.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_size_t, _vp]
 _lib.ace_apply.restype = ctypes.c_int
-_lib.ace_exchange_energy_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, _vp, ctypes.c_size_t, _vp]
+_lib.ace_exchange_energy_grad.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_int, _vp, ctypes.c_size_t,
+                                          _vp]
 _lib.ace_exchange_energy_grad.restype = ctypes.c_int
 _lib.ace_status_sync.argtypes = [_vp, _vp, ctypes.POINTER(ctypes.c_int)]
 _lib.ace_status_sync.restype = ctypes.c_int
@@ -325,16 +327,18 @@ class Plan:
         _check(_lib.ace_apply_static(self._h, _ptr(xi), _ptr(psi), psi.shape[0], _ptr(out), _stream()))
         return out
 
-    def energy_grad(self, phi, grad: bool = False, grad_scale: float = 1.0, out=None):
-        """E_x (Eq. EX) and optionally grad_scale * 2 dV W."""
+    def energy_grad(self, phi, grad: bool = False, grad_scale: float = 1.0, out=None, recompute: bool = True):
+        """E_x (Eq. EX) and optionally grad_scale * 2 dV W. With recompute=False
+        the plan's store workspace keeps the pair potentials: a call without
+        grad stores them, a later call with grad (same phi) uses them."""
         self._vec(phi, "phi")
         ex = torch.empty((), dtype=torch.float64, device=self.device)
         g = None
         if grad:
             g = self.empty(self.n_occ) if out is None else self._vec(out, "out")
-        ws = self.workspace(OP_ENERGY_GRAD)
+        ws = self.workspace(OP_ENERGY_GRAD if recompute else OP_ENERGY_GRAD_STORE)
         _check(_lib.ace_exchange_energy_grad(self._h, _ptr(phi), _ptr(ex), _ptr(g), grad_scale,
-                                             _ptr(ws), ws.numel(), _stream()))
+                                             1 if recompute else 0, _ptr(ws), ws.numel(), _stream()))
         return ex, g
 
     def profile_begin(self, max_events: int = 4096):
@@ -467,14 +471,24 @@ class Batch:
 
 
 class ExchangeEnergy(torch.autograd.Function):
-    """E_x[Phi] with a hand-written adjoint: backward recomputes W through the
-    pair kernels (pair potentials are never stored) and returns
-    grad_output * 2 dV W, the gradient dE/dRe(phi) + i dE/dIm(phi)."""
+    """E_x[Phi] with a hand-written adjoint: backward returns grad_output * 2 dV
+    W, the gradient dE/dRe(phi) + i dE/dIm(phi). When the N(N+1)/2 N_g pair
+    potentials fit in the free device memory (with `store`, by default half of
+    it), forward keeps them in the plan's store workspace and backward only
+    accumulates; otherwise backward recomputes them through the pair kernels."""
 
     @staticmethod
-    def forward(ctx, phi, plan: Plan):
-        ex, _ = plan.energy_grad(phi, grad=False)
+    def forward(ctx, phi, plan: Plan, store=None):
+        if store is None:
+            need = plan.workspace_size(OP_ENERGY_GRAD_STORE)
+            have = plan._ws.get(OP_ENERGY_GRAD_STORE)
+            free = torch.cuda.mem_get_info(plan.device)[0] + (have.numel() if have is not None else 0)
+            store = need <= free // 2
+        ex, _ = plan.energy_grad(phi, grad=False, recompute=not store)
+        plan._store_token = getattr(plan, "_store_token", 0) + 1
         ctx.plan = plan
+        ctx.store = store
+        ctx.token = plan._store_token
         ctx.save_for_backward(phi)
         return ex
 
@@ -483,10 +497,14 @@ class ExchangeEnergy(torch.autograd.Function):
         # the gradient with unit scale from the adjoint kernels, then the chain
         # rule's upstream factor applied on the device (no host synchronisation)
         (phi,) = ctx.saved_tensors
-        _, g = ctx.plan.energy_grad(phi, grad=True)
+        plan = ctx.plan
+        from_store = ctx.store and plan._store_token == ctx.token   # no other forward since
+        _, g = plan.energy_grad(phi, grad=True, recompute=not from_store)
         g.mul_(g_out.to(g.real.dtype))
-        return g, None
+        return g, None, None
 
 
-def exchange_energy(phi: torch.Tensor, plan: Plan) -> torch.Tensor:
-    return ExchangeEnergy.apply(phi, plan)
+def exchange_energy(phi: torch.Tensor, plan: Plan, store=None) -> torch.Tensor:
+    """E_x[phi] as a differentiable scalar; store=None picks storing the pair
+    potentials when they fit, True / False forces one way."""
+    return ExchangeEnergy.apply(phi, plan, store)

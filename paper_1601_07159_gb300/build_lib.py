@@ -1,12 +1,13 @@
 """Build libace.so in-tree: one nvcc process per translation unit (the pair
-kernels once per precision and grid edge), run in parallel, then a shared
-link. sm_103a only (GB300).
+kernels once per precision and plane, pencil length or cubic edge), run in
+parallel, then a shared link. sm_103a only (GB300).
 
     python -m paper_1601_07159_gb300.build_lib [--force]
 """
 from __future__ import annotations
 
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -19,18 +20,36 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libace.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-# keep in step with ACE_EDGES_F32 / ACE_EDGES_F64 in csrc/pair_dispatch.cu
-EDGES_F32 = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 96)
-EDGES_F64 = (8, 12, 16, 20, 24, 32, 36, 40, 48, 64, 96)
-PLAIN = ["pair_dispatch.cu", "dense.cu", "chol.cu", "tc_gemm.cu", "xi_oz.cu", "ace_api.cu", "apply_static.cu"]
+PLAIN = ["pair_dispatch.cu", "pair_point.cu", "dense.cu", "chol.cu", "tc_gemm.cu", "xi_oz.cu", "ace_api.cu",
+         "apply_static.cu"]
+
+
+def shape_lists():
+    """The compiled edges and non-square planes per precision, read from the
+    lists in csrc/pair_dispatch.cu (the one place they are written down)."""
+    text = open(os.path.join(CSRC, "pair_dispatch.cu")).read()
+    out = {}
+    for prec in ("F32", "F64"):
+        edges = re.search(rf"#define ACE_EDGES_{prec}\(X\)(.*)", text).group(1)
+        planes = re.search(rf"#define ACE_PLANES_{prec}\(X\)(.*)", text).group(1)
+        out[prec.lower()] = (tuple(int(v) for v in re.findall(r"X\((\d+)\)", edges)),
+                             tuple((int(a), int(b)) for a, b in re.findall(r"X\((\d+),\s*(\d+)\)", planes)))
+    return out
 
 
 def units():
     """(source, object name, extra flags) for every translation unit."""
     out = [(s, s.replace(".cu", ".o"), []) for s in PLAIN]
-    for prec, typ, edges in (("f32", "float", EDGES_F32), ("f64", "double", EDGES_F64)):
+    for prec, (edges, planes) in shape_lists().items():
+        typ = "float" if prec == "f32" else "double"
+        for nx, ny in [(n, n) for n in edges] + list(planes):
+            tag = f"{prec}_{nx}_{ny}"
+            out.append(("pair_plane.cu", f"pair_plane_{tag}.o",
+                        [f"-DACE_PLANE_R={typ}", f"-DACE_PX={nx}", f"-DACE_PY={ny}", f"-DACE_PLANE_TAG={tag}"]))
         for n in edges:
             tag = f"{prec}_{n}"
+            out.append(("pair_pencil.cu", f"pair_pencil_{tag}.o",
+                        [f"-DACE_PENCIL_R={typ}", f"-DACE_PZ={n}", f"-DACE_PENCIL_TAG={tag}"]))
             out.append(("pair_edge.cu", f"pair_edge_{tag}.o",
                         [f"-DACE_EDGE_R={typ}", f"-DACE_EDGE_N={n}", f"-DACE_EDGE_TAG={tag}"]))
     return out

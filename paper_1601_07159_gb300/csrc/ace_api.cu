@@ -61,6 +61,7 @@ struct Schedule {
   TileDesc* dtiles = nullptr;   // device copy of all tile descriptors
   EngineBatch* deng[2] = {nullptr, nullptr};   // engine task tables: [0] Poisson, [1] energy only
   long long ntasks[2] = {0, 0};
+  std::vector<long long> soff;  // first pair slot of each batch in a store of all pair potentials
 };
 
 void free_schedule(Schedule& sc) {
@@ -88,7 +89,8 @@ struct ProfRec {
 struct ace_plan {
   ace_desc d{};
   int device = 0;
-  int n = 0;                     // grid edge (the pair kernels are compiled per cubic edge)
+  int nx = 0, ny = 0, nz = 0;    // grid points along x, y, z
+  bool cubic = false;            // nx == ny == nz (the persistent engine needs it)
   long long ng = 0;              // grid points N_g
   long long ld = 0;              // elements from one vector to the next
   int xi = 0;                    // Xi = W L^{-*}: 0 the plan's GEMM, 1 FP16 Ozaki slices, 2 FP64 CUDA cores
@@ -106,7 +108,7 @@ struct ace_plan {
   cudaEvent_t ov_ev[2] = {};
 
   EngineInfo einfo;
-  std::vector<double> tw;        // 2n doubles, exp(-2 pi i k / n)
+  std::vector<double> tw[3];     // per axis x, y, z: 2n doubles, exp(-2 pi i k / n)
   Schedule build;                // symmetric schedule of the W build
   std::deque<std::pair<int, Schedule>> rect;   // one-sided schedules by n_b
   std::deque<std::pair<int, Schedule>> pois;   // one-sided schedules of one constant orbital, by n_b
@@ -138,11 +140,16 @@ cudaError_t upload(const ace_plan* p, Schedule& sc) {
   std::vector<TileDesc> all;
   std::vector<EngineBatch> eng[2];
   long long t0[2] = {0, 0};
+  long long slots = 0;
   for (const Batch& b : sc.batches) {
+    sc.soff.push_back(slots);
+    slots += b.npairs;
     sc.toff.push_back((int)all.size());
     int nt[4] = {0, 0, 0, 0};
-    if (p->f64) engine_tasks_f64(p->n, b, nt);
-    else engine_tasks_f32(p->n, b, nt);
+    if (p->cubic) {
+      if (p->f64) engine_tasks_f64(p->nx, b, nt);
+      else engine_tasks_f32(p->nx, b, nt);
+    }
     for (int m = 0; m < 2; ++m) {
       EngineBatch e{};
       e.toff = (int)all.size();
@@ -275,6 +282,7 @@ struct WsLayout {
   double* work = nullptr;       // oversampled build: Cholesky work and L^{-*} of N_phi
   double* LinvH = nullptr;
   char* xis = nullptr;          // FP64-accurate Xi: row/column exponents and C slices
+  char* store = nullptr;        // pair potentials kept between calls (ACE_OP_ENERGY_GRAD_STORE)
   size_t total = 0;
 };
 
@@ -292,7 +300,7 @@ long long rect_batch_bound(const ace_plan* p, int nb) {
   return (long long)((N + lc - 1) / lc) * ((nb + b - 1) / b);
 }
 
-int epart_per_lane(const ace_plan* p) { return energy_blocks(p->n, p->max_pairs, p->f64) + 1; }
+int epart_per_lane(const ace_plan* p) { return energy_blocks(p->nx, p->ny, p->nz, p->max_pairs) + 1; }
 size_t slot_bytes(const ace_plan* p) { return (size_t)p->ng * p->csize; }
 size_t lane_bytes(const ace_plan* p) { return align256((size_t)p->max_pairs * slot_bytes(p)); }
 
@@ -303,7 +311,7 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
   const int N = p->d.n_occ;
   const int splits = op == ACE_OP_BUILD_OVERSAMPLED ? gram_parts(p, nb, nb) : gram_parts(p, N, op == ACE_OP_APPLY ? nb : N);
   if (op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_BUILD || op == ACE_OP_ENERGY_GRAD || op == ACE_OP_BUILD_OVERSAMPLED ||
-      op == ACE_OP_POISSON) {
+      op == ACE_OP_POISSON || op == ACE_OP_ENERGY_GRAD_STORE) {
     L.S = take((size_t)p->lanes * lane_bytes(p));
     long long nbat = op == ACE_OP_EXCHANGE_APPLY ? rect_batch_bound(p, nb) : (long long)p->build.batches.size();
     if (op == ACE_OP_POISSON) nbat = (nb + p->tile - 1) / p->tile;
@@ -319,8 +327,13 @@ WsLayout layout(const ace_plan* p, int op, int nb, char* base) {
     L.work = (double*)take(cholesky_work_doubles(nb) * sizeof(double));
     L.LinvH = (double*)take((size_t)nb * nb * 2 * sizeof(double));
   }
-  if (op == ACE_OP_ENERGY_GRAD)
+  if (op == ACE_OP_ENERGY_GRAD || op == ACE_OP_ENERGY_GRAD_STORE)
     L.Epart = (double*)take((size_t)p->lanes * epart_per_lane(p) * sizeof(double));
+  if (op == ACE_OP_ENERGY_GRAD_STORE) {   // every unique pair potential of the build schedule
+    long long slots = 0;
+    for (const Batch& b : p->build.batches) slots += b.npairs;
+    L.store = take((size_t)slots * slot_bytes(p));
+  }
   if (op == ACE_OP_BUILD) {
     const size_t pd = (size_t)splits * N * N * 2;
     L.part = (double*)take((pd > diag_dot_part_doubles(N) ? pd : diag_dot_part_doubles(N)) * sizeof(double));
@@ -371,12 +384,24 @@ cudaEvent_t* take_events(ace_plan* p, int count, int kind) {
 // pass. Graph mode (called while capturing `cs`): the batches of one round
 // are spread over the plan's lanes (fork/join through events), consecutive
 // rounds are joined. Returns the kernel count, or -1 if the edge is not built.
+//
+// With `store` set, batch k works in its own part of a store of every pair
+// potential (slots sc.soff[k] ..), nothing is reused, and base.pass_mask
+// selects the passes (A-C to fill the store, D to consume it); the persistent
+// engine is not used then.
 long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, char* S0, double* E0,
-                      char* ctr, cudaStream_t cs, bool reset_status = true) {
+                      char* ctr, cudaStream_t cs, bool reset_status = true, char* store = nullptr) {
   long long kernels = 0;
   if (reset_status) cudaMemsetAsync(p->status, 0, 2 * sizeof(int), cs);
   if (sc.batches.empty()) return 0;
-  if (p->engine) {   // one persistent launch for the whole schedule
+  const int gmask = base.pass_mask ? base.pass_mask : 15;
+  auto scratch = [&](size_t k, char* dflt) { return store ? store + (size_t)sc.soff[k] * slot_bytes(p) : dflt; };
+  auto launches = [&](int mask, int mode) {   // kernels one batch issues for a pass mask
+    int c = 0;
+    for (int b = 0; b < 4; ++b) c += (mask >> b) & 1;
+    return mode == 1 ? std::min(c, 2) : c;
+  };
+  if (p->engine && !store) {   // one persistent launch for the whole schedule
     const int m = base.mode == 1 ? 1 : 0;
     cudaMemsetAsync(ctr, 0, engine_ctr_bytes((long long)sc.batches.size()), cs);
     PairLaunch L = base;
@@ -401,12 +426,13 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
   }
   if (!p->graphs) {
     for (const Batch& b : sc.batches) {
+      const size_t k = (size_t)(&b - sc.batches.data());
       PairLaunch L = base;
-      L.S = S0;
+      L.S = scratch(k, S0);
       L.Epart = E0;
       L.ev = take_events(p, 5, 0);
-      L.dtiles = sc.dtiles + sc.toff[&b - sc.batches.data()];
-      kernels += pair_batch_launches(L.mode);
+      L.dtiles = sc.dtiles + sc.toff[k];
+      kernels += launches(gmask, L.mode);
       if (!launch_one(p, L, b, cs)) return -1;
     }
     return kernels;
@@ -424,21 +450,21 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
     bool ok = true;
     for (size_t k = 0; k < sc.batches.size(); ++k) {
       PairLaunch L = base;
-      L.S = S0 + (k & 1) * lane_bytes(p);
+      L.S = scratch(k, S0 + (k & 1) * lane_bytes(p));
       L.Epart = E0;
       L.ev = nullptr;
       L.dtiles = sc.dtiles + sc.toff[k];
-      L.pass_mask = 1;
-      ok = ok && launch_one(p, L, sc.batches[k], la);
+      L.pass_mask = 1 & gmask;
+      if (L.pass_mask) ok = ok && launch_one(p, L, sc.batches[k], la);
       cudaEventRecord(p->ov_ev[0], la);
       cudaStreamWaitEvent(lb, p->ov_ev[0], 0);
-      L.pass_mask = 2 | 4;
-      ok = ok && launch_one(p, L, sc.batches[k], lb);
+      L.pass_mask = (2 | 4) & gmask;
+      if (L.pass_mask) ok = ok && launch_one(p, L, sc.batches[k], lb);
       cudaEventRecord(p->ov_ev[1], lb);
       cudaStreamWaitEvent(la, p->ov_ev[1], 0);
-      L.pass_mask = 8;
-      ok = ok && launch_one(p, L, sc.batches[k], lb);
-      kernels += 4;
+      L.pass_mask = 8 & gmask;
+      if (L.pass_mask) ok = ok && launch_one(p, L, sc.batches[k], lb);
+      kernels += launches(gmask, L.mode);
     }
     cudaEventRecord(p->join_ev[0], la);
     cudaStreamWaitEvent(cs, p->join_ev[0], 0);
@@ -469,11 +495,11 @@ long long issue_pairs(ace_plan* p, const PairLaunch& base, const Schedule& sc, c
     }
     const int ln = k_in_round++ % nl;
     PairLaunch L = base;
-    L.S = S0 + (size_t)ln * lane_bytes(p);
+    L.S = scratch(k, S0 + (size_t)ln * lane_bytes(p));
     L.Epart = E0 ? E0 + (size_t)ln * epart_per_lane(p) : nullptr;
     L.ev = nullptr;
     L.dtiles = sc.dtiles + sc.toff[k];
-    kernels += pair_batch_launches(L.mode);
+    kernels += launches(gmask, L.mode);
     ok = ok && launch_one(p, L, sc.batches[k], p->lane[ln]);
   }
   join();
@@ -535,10 +561,14 @@ ace_status run_graph(ace_plan* p, const uintptr_t key[8], cudaStream_t st, bool 
 
 PairLaunch base_launch(const ace_plan* p) {
   PairLaunch L{};
-  L.n = p->n;
+  L.nx = p->nx;
+  L.ny = p->ny;
+  L.nz = p->nz;
   L.ld = p->ld;
   L.Kt = p->Kt;
-  L.tw = p->tw.data();
+  L.twx = p->tw[0].data();
+  L.twy = p->tw[1].data();
+  L.twz = p->tw[2].data();
   L.real_io = p->real;
   L.scale = 1.0;
   L.prepare_only = false;
@@ -678,15 +708,14 @@ ace_status ace_internal_set_error(ace_status s, const char* msg) { return fail(s
 
 extern "C" {
 
-int ace_supported_edge(int n, int dtype) {
-  if (dtype == ACE_DTYPE_C64) return pair_edge_supported_f32(n) ? 1 : 0;
-  if (dtype == ACE_DTYPE_C128 || dtype == ACE_DTYPE_R64) return pair_edge_supported_f64(n) ? 1 : 0;
-  return 0;
+int ace_supported_grid(const int n[3], int dtype) {
+  if (!n || dtype < ACE_DTYPE_R64 || dtype > ACE_DTYPE_C64) return 0;
+  return pair_grid_supported(dtype != ACE_DTYPE_C64, n[0], n[1], n[2]) ? 1 : 0;
 }
 
-int ace_supported_grid(const int n[3], int dtype) {
-  if (!n || n[0] != n[1] || n[1] != n[2]) return 0;
-  return ace_supported_edge(n[0], dtype);
+int ace_supported_edge(int n, int dtype) {
+  const int g[3] = {n, n, n};
+  return ace_supported_grid(g, dtype);
 }
 
 const char* ace_last_error(void) { return g_last_error.c_str(); }
@@ -722,7 +751,10 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   ace_plan* p = new ace_plan();
   p->d = *d;
   cudaGetDevice(&p->device);
-  p->n = d->n[0];
+  p->nx = d->n[0];
+  p->ny = d->n[1];
+  p->nz = d->n[2];
+  p->cubic = p->nx == p->ny && p->ny == p->nz;
   p->ng = ng_;
   p->ld = d->ld ? d->ld : ng_;
   p->vol = d->L[0] * d->L[1] * d->L[2];
@@ -734,9 +766,12 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->tile = d->tile ? d->tile : kTileMax;
   p->lanes = d->lanes ? d->lanes : 2;
   p->graphs = !(d->flags & ACE_FLAG_NO_GRAPH);
-  p->engine = (d->flags & ACE_FLAG_ENGINE) != 0;
+  p->engine = (d->flags & ACE_FLAG_ENGINE) != 0 && p->cubic;
   p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM) && d->prec != ACE_PREC_FP32;
-  p->xi = d->prec == ACE_PREC_XI_FP64 ? 1 : (d->prec == ACE_PREC_XI_FP64_SIMT ? 2 : 0);
+  // C64 default: Xi to FP64 accuracy on the FP16 tensor cores (the triangular
+  // product stays FP64-accurate, as the Cholesky factor it applies)
+  const bool xi_slices = d->prec == ACE_PREC_XI_FP64 || (d->prec == ACE_PREC_DEFAULT && p->tc);
+  p->xi = xi_slices ? 1 : (d->prec == ACE_PREC_XI_FP64_SIMT ? 2 : 0);
   p->overlap = p->graphs && !p->engine && !(d->flags & ACE_FLAG_NO_OVERLAP);
   if (p->overlap && p->lanes < 2) p->lanes = 2;
   const size_t slot = (size_t)p->ng * p->csize;
@@ -752,25 +787,28 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   }
   if (p->max_pairs < tt) p->max_pairs = tt;
 
-  // twiddles exp(-2 pi i k/n) in FP64
-  const int n = p->n;
-  p->tw.resize(2 * n);
-  for (int k = 0; k < n; ++k) {
-    const double a = 2.0 * M_PI * (double)k / (double)n;
-    p->tw[2 * k] = std::cos(a);
-    p->tw[2 * k + 1] = -std::sin(a);
+  // twiddles exp(-2 pi i k/n) in FP64, per axis
+  const int nax[3] = {p->nx, p->ny, p->nz};
+  for (int a = 0; a < 3; ++a) {
+    p->tw[a].resize(2 * nax[a]);
+    for (int k = 0; k < nax[a]; ++k) {
+      const double t = 2.0 * M_PI * (double)k / (double)nax[a];
+      p->tw[a][2 * k] = std::cos(t);
+      p->tw[a][2 * k + 1] = -std::sin(t);
+    }
   }
   // kernel table K(G) alpha / N_g, folded: every kernel depends on |G|^2 only,
   // and |G|^2 at index n - k equals that at k on each axis (the wrapped
   // frequency k - n = -k), so the table holds indices 0..n/2 per axis,
-  // [kz][kx][ky] with (n/2 + 1)^3 entries (62.5 KB at 48^3 FP32, L1-sized)
+  // [kz][kx][ky] with (n_z/2 + 1)(n_x/2 + 1)(n_y/2 + 1) entries (62.5 KB at 48^3
+  // FP32, L1-sized)
   const double g0_default = d->kernel == ACE_KERNEL_ERFC ? M_PI / (d->omega * d->omega) : 0.0;
   const double g0 = std::isnan(d->g0_value) ? g0_default : d->g0_value;
-  const int nh = n / 2 + 1;
-  std::vector<double> kt((size_t)nh * nh * nh);
-  for (int kz = 0; kz < nh; ++kz)
-    for (int kx = 0; kx < nh; ++kx)
-      for (int ky = 0; ky < nh; ++ky) {
+  const int nhx = p->nx / 2 + 1, nhy = p->ny / 2 + 1, nhz = p->nz / 2 + 1;
+  std::vector<double> kt((size_t)nhz * nhx * nhy);
+  for (int kz = 0; kz < nhz; ++kz)
+    for (int kx = 0; kx < nhx; ++kx)
+      for (int ky = 0; ky < nhy; ++ky) {
         const double gx = 2.0 * M_PI * kx / d->L[0];
         const double gy = 2.0 * M_PI * ky / d->L[1];
         const double gz = 2.0 * M_PI * kz / d->L[2];
@@ -780,7 +818,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
         else if (d->kernel == ACE_KERNEL_BARE) k = 4.0 * M_PI / g2;
         else if (d->kernel == ACE_KERNEL_KINETIC) k = 0.5 * g2;
         else k = 4.0 * M_PI / g2 * (1.0 - std::exp(-g2 / (4.0 * d->omega * d->omega)));
-        kt[((size_t)kz * nh + kx) * nh + ky] = d->alpha * k / (double)p->ng;
+        kt[((size_t)kz * nhx + kx) * nhy + ky] = d->alpha * k / (double)p->ng;
       }
   const int N = d->n_occ;
   cudaError_t e = cudaSuccess;
@@ -825,8 +863,8 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     if (p->tc) tc_gemm_prepare();
     if (p->xi == 1) xi_oz_prepare();
     if (p->engine) {
-      if (p->f64) engine_prepare_f64(p->n, p->einfo);
-      else engine_prepare_f32(p->n, p->einfo);
+      if (p->f64) engine_prepare_f64(p->nx, p->einfo);
+      else engine_prepare_f32(p->nx, p->einfo);
       if (p->einfo.blocks <= 0) p->engine = false;   // does not fit: four kernels per batch
     }
     e = cudaGetLastError();
@@ -875,7 +913,7 @@ ace_status ace_plan_destroy(ace_plan* p) {
 }
 
 size_t ace_workspace_size(const ace_plan* p, int op, int nb) {
-  if (!p || op < ACE_OP_EXCHANGE_APPLY || op > ACE_OP_POISSON) return 0;
+  if (!p || op < ACE_OP_EXCHANGE_APPLY || op > ACE_OP_ENERGY_GRAD_STORE) return 0;
   if ((op == ACE_OP_EXCHANGE_APPLY || op == ACE_OP_APPLY || op == ACE_OP_POISSON) && nb < 0) return 0;
   if (op == ACE_OP_BUILD_OVERSAMPLED && (nb < p->d.n_occ || nb > 1024)) return 0;
   return layout(p, op, nb, nullptr).total;
@@ -1273,33 +1311,60 @@ ace_status ace_apply(ace_plan* p, const void* Xi, const void* Psi, int nb, void*
 }
 
 ace_status ace_exchange_energy_grad(ace_plan* p, const void* Phi, double* Ex_out, void* grad_out,
-                                    double grad_scale, void* ws, size_t ws_bytes, void* stream) {
-  ace_status s = check_common(p, ws, ws_bytes, ACE_OP_ENERGY_GRAD, 0);
+                                    double grad_scale, int recompute, void* ws, size_t ws_bytes, void* stream) {
+  const int op = recompute ? ACE_OP_ENERGY_GRAD : ACE_OP_ENERGY_GRAD_STORE;
+  ace_status s = check_common(p, ws, ws_bytes, op, 0);
   if (s != ACE_OK) return s;
-  if (!Phi || !Ex_out) return fail(ACE_ERR_ARG, "Phi and Ex_out are required");
+  if (!Phi || (!Ex_out && (recompute || !grad_out))) return fail(ACE_ERR_ARG, "Phi and Ex_out are required");
   if (!aligned16(Phi) || (grad_out && !aligned16(grad_out))) return fail(ACE_ERR_ARG, "vectors must be 16-byte aligned");
   if (grad_out == Phi) return fail(ACE_ERR_ARG, "grad_out must not alias Phi");
   if (!std::isfinite(grad_scale)) return fail(ACE_ERR_ARG, "grad_scale must be finite");
   cudaStream_t st = (cudaStream_t)stream;
   const int N = p->d.n_occ;
-  const WsLayout Wl = layout(p, ACE_OP_ENERGY_GRAD, 0, (char*)ws);
+  const WsLayout Wl = layout(p, op, 0, (char*)ws);
   const int ecount = p->lanes * epart_per_lane(p);
+  const double efac = -0.5 * p->vol / (double)p->ng;   // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2
   PairLaunch L = base_launch(p);
   L.X = Phi;
   L.Y = Phi;
   L.OutX = grad_out;
   L.OutY = grad_out;
-  L.mode = grad_out ? 2 : 1;
   L.scale = 2.0 * p->dv;                   // grad = 2 dV W, then * grad_scale
-  const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)Ex_out, (uintptr_t)ws, 0, 3, 0, 0};
-  s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
-    cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), cs);
-    if (grad_out) zero_vectors(p, grad_out, N, cs);
-    const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, Wl.ctr, cs);
-    // E = -1/2 Omega/N_g sum_pairs w_p sum_G Kt |F rho|^2  (Kt = alpha K / N_g)
-    launch_energy_reduce(Wl.Epart, ecount, -0.5 * p->vol / (double)p->ng, Ex_out, cs);
-    return k < 0 ? k : k + 1;
-  });
+  if (recompute) {
+    // one sweep: energy (and, with grad_out, the potentials consumed batch by batch)
+    L.mode = grad_out ? 2 : 1;
+    const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)Ex_out, (uintptr_t)ws, 0, 3, 0, 0};
+    s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
+      cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), cs);
+      if (grad_out) zero_vectors(p, grad_out, N, cs);
+      const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, Wl.ctr, cs);
+      launch_energy_reduce(Wl.Epart, ecount, efac, Ex_out, cs);
+      return k < 0 ? k : k + 1;
+    });
+  } else if (!grad_out) {
+    // the energy, and every unique pair potential into the workspace's store
+    L.mode = 2;
+    L.pass_mask = 1 | 2 | 4;
+    const uintptr_t key[8] = {(uintptr_t)Phi, 0, (uintptr_t)Ex_out, (uintptr_t)ws, 0, 3, 1, 0};
+    s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
+      cudaMemsetAsync(Wl.Epart, 0, (size_t)ecount * sizeof(double), cs);
+      const long long k = issue_pairs(p, L, p->build, Wl.S, Wl.Epart, Wl.ctr, cs, true, Wl.store);
+      launch_energy_reduce(Wl.Epart, ecount, efac, Ex_out, cs);
+      return k < 0 ? k : k + 1;
+    });
+  } else {
+    // the gradient from the stored potentials (pass D only); E_x again from
+    // the stored energy partials
+    L.mode = 0;
+    L.pass_mask = 8;
+    const uintptr_t key[8] = {(uintptr_t)Phi, (uintptr_t)grad_out, (uintptr_t)Ex_out, (uintptr_t)ws, 0, 3, 2, 0};
+    s = run_graph(p, key, st, true, [&](cudaStream_t cs) -> long long {
+      zero_vectors(p, grad_out, N, cs);
+      const long long k = issue_pairs(p, L, p->build, Wl.S, nullptr, Wl.ctr, cs, true, Wl.store);
+      if (Ex_out) launch_energy_reduce(Wl.Epart, ecount, efac, Ex_out, cs);
+      return k < 0 ? k : k + (Ex_out ? 1 : 0);
+    });
+  }
   if (s != ACE_OK) return s;
   if (grad_out && grad_scale != 1.0) {   // outside the graph: the scale varies per call
     launch_scale(p->f64, p->real, grad_out, N, p->ng, p->ld, grad_scale, st);

@@ -31,17 +31,19 @@ __host__ __device__ inline int tile_pairs(const TileDesc& d) {
 
 // Launchers (pair_f32.cu / pair_f64.cu). Return false if edge n is not compiled.
 struct PairLaunch {
-  int n;                 // grid edge
-  long long ld;          // elements per vector (n^3)
+  int nx, ny, nz;        // grid points along x, y, z
+  long long ld;          // elements from one vector to the next (>= n_x n_y n_z)
   const void* X;         // l-side vectors (phi)
   const void* Y;         // r-side vectors (phi or psi)
   void* OutX;            // accumulators for the l side (symmetric tiles)
   void* OutY;            // accumulators for the r side
-  void* S;               // spectrum scratch, max_pairs * n^3 complex
-  const void* Kt;        // kernel table K(G) alpha / N_g, folded [kz][kx][ky] over 0..n/2 each
+  void* S;               // spectrum scratch, max_pairs * N_g complex
+  const void* Kt;        // kernel table K(G) alpha / N_g, folded [kz][kx][ky] over 0..n/2 per axis
   double* Epart;         // per-block energy partials (nullable)
   double scale;          // Out -= scale * sum
-  const double* tw;      // host FP64 twiddles exp(-2 pi i k/n), 2n doubles
+  const double* twx;     // host FP64 twiddles exp(-2 pi i k/n) per axis, 2n doubles each
+  const double* twy;
+  const double* twz;
   bool real_io;          // R64 vectors
   int mode;              // 0: W / Y accumulate; 1: energy only; 2: energy + accumulate
   cudaEvent_t* ev;       // nullable: 5 events recorded around passes A, B, C, D
@@ -90,13 +92,12 @@ bool engine_tasks_f64(int n, const Batch& b, int nt[4]);
 bool launch_engine_f32(const PairLaunch& L, const EngineLaunch& E, cudaStream_t st);
 bool launch_engine_f64(const PairLaunch& L, const EngineLaunch& E, cudaStream_t st);
 
-// Kernel launches issued by one pair batch for a mode (4, or 2 for energy only).
-inline int pair_batch_launches(int mode) { return mode == 1 ? 2 : 4; }
 bool launch_pair_batch_f32(const PairLaunch& L, const Batch& b, cudaStream_t st);
 bool launch_pair_batch_f64(const PairLaunch& L, const Batch& b, cudaStream_t st);
-bool pair_edge_supported_f32(int n);
-bool pair_edge_supported_f64(int n);
-int energy_blocks(int n, int npairs, bool f64);
+// The grid's plane (n_x, n_y) and pencil length n_z are compiled in.
+bool pair_grid_supported(bool f64, int nx, int ny, int nz);
+// Energy partials one pair batch of npairs writes (one per pass-B block).
+int energy_blocks(int nx, int ny, int nz, int npairs);
 
 // Dense kernels (dense.cu).
 void launch_gram(bool f64, bool real_in, const void* A, int na, const void* B, int nb, long long ld,

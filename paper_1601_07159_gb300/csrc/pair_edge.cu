@@ -1,7 +1,7 @@
-// One (precision, grid edge) instance of the pair passes and the persistent
-// engine. The build compiles this file once per supported edge with
-// -DACE_EDGE_R=<float|double> -DACE_EDGE_N=<n> -DACE_EDGE_TAG=<f32_n|f64_n>,
-// so the instances compile in parallel; pair_dispatch.cu maps n to them.
+// One (precision, cubic edge) instance of the persistent pair engine. The
+// build compiles this file once per compiled edge with
+// -DACE_EDGE_R=<float|double> -DACE_EDGE_N=<n> -DACE_EDGE_TAG=<f32_n|f64_n>, so
+// the instances compile in parallel; pair_dispatch.cu maps n to them.
 #include "pair_kernels.cuh"
 
 #if !defined(ACE_EDGE_R) || !defined(ACE_EDGE_N) || !defined(ACE_EDGE_TAG)
@@ -12,9 +12,6 @@
 
 namespace ace {
 
-bool ACE_CAT(edge_launch_, ACE_EDGE_TAG)(const PairLaunch& L, const Batch& b, cudaStream_t st) {
-  return launch_edge<ACE_EDGE_R, ACE_EDGE_N>(L, b, st);
-}
 void ACE_CAT(edge_prepare_, ACE_EDGE_TAG)(EngineInfo& info) { engine_prepare<ACE_EDGE_R, ACE_EDGE_N>(info); }
 void ACE_CAT(edge_tasks_, ACE_EDGE_TAG)(const Batch& b, int nt[4]) { engine_tasks<ACE_EDGE_R, ACE_EDGE_N>(b, nt); }
 bool ACE_CAT(edge_engine_, ACE_EDGE_TAG)(const PairLaunch& L, const EngineLaunch& E, cudaStream_t st) {

@@ -1,8 +1,9 @@
 // Pair FFT-Poisson solves: the hot loop of Eq. applyVX / Eq. W.
 //
-// For a batch of pairs (l, r) the 3-D solve v = F^-1[ K F[conj(x_l) y_r] ] is
-// split into three passes over the batch's spectrum scratch S, each a set of
-// register-resident line FFTs (fft_reg.cuh), plus one accumulate pass:
+// For a batch of pairs (l, r) the 3-D solve v = F^-1[ K F[conj(x_l) y_r] ] on an
+// n_x x n_y x n_z grid is split into three passes over the batch's spectrum
+// scratch S, each a set of register-resident line FFTs (fft_reg.cuh), plus one
+// accumulate pass:
 //
 //   pass A  (per z-plane)   rho = conj(x_l) y_r; FFT along y (thread = column x,
 //                           coalesced loads), transpose through shared memory,
@@ -19,20 +20,26 @@
 //                           orbitals and accumulators, one read-modify-write of
 //                           each output per tile, fixed summation order (full
 //                           off-diagonal tiles: two threads per point).
-// In FP32 at the larger edges a line is held by two lanes instead of one
-// thread (split_line_dft): passes A and C from n = 48, pass B from n = 64.
+// The plane passes are compiled per (n_x, n_y), the pencil pass per n_z (the
+// pencil's (kx, ky) position is a run-time index), the accumulate pass once per
+// precision; a grid n_x x n_y x n_z runs when its plane and its pencil length
+// are compiled in. On cubic grids passes B and D use instances with the grid
+// compiled in (strides and offsets folded into the instructions). At the larger edges a line is held by two lanes instead of
+// one thread (split_line_dft): the plane passes when the longer plane edge is
+// >= 48 (FP64: >= 64), pass B from n_z = 64.
 //
 // Two ways to run a schedule of batches:
 //  * four kernels per batch (pass_*_kernel), chained with programmatic
 //    dependent launch, replayed from a CUDA graph (the default) or launched
 //    eagerly (per-pass timing);
-//  * one persistent launch (pair_engine_kernel): co-resident blocks take
-//    tasks (one pass-A/C block of planes, one pass-B block of pencils, one
-//    pass-D block of points) in schedule order from an atomic queue and wait,
-//    with a bounded spin, on per-batch completion counters: pass p of batch k
-//    needs all of pass p-1 of batch k, pass A of batch k needs the last pass of
-//    batch k-1 (the scratch is reused). Tasks are taken in increasing order by
-//    resident blocks, so every awaited task is already running: no deadlock.
+//  * one persistent launch (pair_engine_kernel, cubic grids): co-resident
+//    blocks take tasks (one pass-A/C block of planes, one pass-B block of
+//    pencils, one pass-D block of points) in schedule order from an atomic
+//    queue and wait, with a bounded spin, on per-batch completion counters:
+//    pass p of batch k needs all of pass p-1 of batch k, pass A of batch k
+//    needs the last pass of batch k-1 (the scratch is reused). Tasks are taken
+//    in increasing order by resident blocks, so every awaited task is already
+//    running: no deadlock.
 //
 // Tiles within a batch touch disjoint outputs (the schedule guarantees it) and
 // batches run in order, so the accumulation needs no atomics and the result is
@@ -44,20 +51,63 @@
 
 namespace ace {
 
-template <typename R, int N> struct PairParams {
+// Twiddle tables of a plane: one per axis, shared when the plane is square.
+template <typename R, int NX, int NY> struct PlaneTw {
+  TwTable<R, NX> x;
+  TwTable<R, NY> y;
+  __device__ __forceinline__ const TwTable<R, NX>& tx() const { return x; }
+  __device__ __forceinline__ const TwTable<R, NY>& ty() const { return y; }
+  void fill(const double* twx, const double* twy) {
+    for (int k = 0; k < NX; ++k) { x.w[k].x = (R)twx[2 * k]; x.w[k].y = (R)twx[2 * k + 1]; }
+    for (int k = 0; k < NY; ++k) { y.w[k].x = (R)twy[2 * k]; y.w[k].y = (R)twy[2 * k + 1]; }
+  }
+};
+template <typename R, int N> struct PlaneTw<R, N, N> {
+  TwTable<R, N> x;
+  __device__ __forceinline__ const TwTable<R, N>& tx() const { return x; }
+  __device__ __forceinline__ const TwTable<R, N>& ty() const { return x; }
+  void fill(const double* twx, const double*) {
+    for (int k = 0; k < N; ++k) { x.w[k].x = (R)twx[2 * k]; x.w[k].y = (R)twx[2 * k + 1]; }
+  }
+};
+
+// Passes A and C: the pair's vectors (pass A), the scratch, nz z-planes per pair.
+template <typename R, int NX, int NY> struct PlaneParams {
+  const void* X;
+  const void* Y;
+  cplx<R>* S;
+  long long ld;
+  int nz;
+  int npairs;
+  const TileDesc* tiles;   // device table of the batch's tiles
+  int ntiles;
+  PlaneTw<R, NX, NY> tw;
+};
+
+// Pass B: pencils of NZ points at the nxy = n_x n_y positions (kx, ky) of a plane.
+template <typename R, int NZ> struct PencilParams {
+  cplx<R>* S;
+  const R* Kt;             // K(G) alpha / N_g, folded [kz][kx][ky] over 0..n/2 per axis
+  double* Epart;
+  int npairs;
+  int nx, ny, nxy;
+  int khy, kzs;            // folded table: row length n_y/2 + 1, kz stride (n_x/2 + 1)(n_y/2 + 1)
+  const TileDesc* tiles;
+  int ntiles;
+  TwTable<R, NZ> tw;
+};
+
+// Pass D: the tile's vectors and outputs, the pair potentials in S.
+template <typename R> struct PointParams {
   const void* X;
   const void* Y;
   void* OutX;
   void* OutY;
-  cplx<R>* S;
-  const R* Kt;
-  double* Epart;
+  const cplx<R>* S;
   long long ld;
+  long long ng;
   R scale;
-  int npairs;
-  const TileDesc* tiles;   // device table of the batch's tiles
-  int ntiles;
-  TwTable<R, N> tw;
+  const TileDesc* tiles;
 };
 
 // Programmatic dependent launch (four-kernel mode): every pass is launched with
@@ -122,21 +172,36 @@ __device__ __forceinline__ cplx<R> load_vec(const void* base, long long idx) {
   }
 }
 
-// The kernel table is folded (K depends on |G|^2 only): index k of an axis and
-// n - k share an entry. kfold(k) = min(k, N - k); the table is [kz][kx][ky] over
-// 0..N/2 each.
+// The kernel table is folded (K depends on |G|^2 only): index k of an axis of
+// n points and n - k share an entry. kfold(k) = min(k, n - k).
 template <int N> __host__ __device__ __forceinline__ constexpr int kfold(int k) { return k <= N / 2 ? k : N - k; }
-template <int N> constexpr int kKH = N / 2 + 1;
-// offset of the (kx, ky) pencil f = kx N + ky in the folded table
-template <int N> __device__ __forceinline__ int kt_pencil(int f) {
-  const int kx = f / N, ky = f - kx * N;
-  return kfold<N>(kx) * kKH<N> + kfold<N>(ky);
-}
+__host__ __device__ __forceinline__ int kfold_rt(int k, int n) { return k <= n / 2 ? k : n - k; }
+// Plane geometry seen by the pencil pass: compile-time for cubic grids
+// (CUBE: n_x = n_y = n_z, so strides and table offsets fold into the
+// instructions), read from the parameters otherwise.
+template <typename R, int NZ, bool CUBE> struct PencilGeom {
+  int nx, ny, nxy, khy, kzs;
+  __device__ __forceinline__ explicit PencilGeom(const PencilParams<R, NZ>& P) {
+    if constexpr (CUBE) {
+      nx = NZ; ny = NZ; nxy = NZ * NZ; khy = NZ / 2 + 1; kzs = (NZ / 2 + 1) * (NZ / 2 + 1);
+    } else {
+      nx = P.nx; ny = P.ny; nxy = P.nxy; khy = P.khy; kzs = P.kzs;
+    }
+  }
+  // offset of the (kx, ky) pencil f = kx n_y + ky in the folded table
+  __device__ __forceinline__ int kt_pencil(int f) const {
+    const int kx = f / ny, ky = f - kx * ny;
+    return kfold_rt(kx, nx) * khy + kfold_rt(ky, ny);
+  }
+};
 
-template <typename R, int N> __host__ __device__ constexpr int plane_items() {
+template <int NX, int NY> constexpr int kMaxLine = NX > NY ? NX : NY;
+
+template <typename R, int NX, int NY> __host__ __device__ constexpr int plane_items() {
   // items (pair, z-plane) per CTA of the plane kernels: ~256 threads, <= 96 KB
-  constexpr int by_threads = (256 / N) > 0 ? (256 / N) : 1;
-  constexpr int by_smem = (96 * 1024) / (N * (N + 1) * (int)sizeof(cplx<R>));
+  constexpr int ML = kMaxLine<NX, NY>;
+  constexpr int by_threads = (256 / ML) > 0 ? (256 / ML) : 1;
+  constexpr int by_smem = (96 * 1024) / (NY * (NX + 1) * (int)sizeof(cplx<R>));
   constexpr int v = by_threads < by_smem ? by_threads : by_smem;
   return v > 0 ? v : 1;
 }
@@ -150,68 +215,72 @@ template <typename R, int N> __host__ __device__ constexpr int engine_items() {
 }
 
 // ---------------------------------------------------------------- pass bodies
-// Pass A on virtual block `vb` (IPB plane items, thread tid = ty * N + tx).
-template <typename R, int N, bool REAL, bool COH, int IPB, bool PDL>
-__device__ __forceinline__ void body_a(const PairParams<R, N>& P, const TileDesc* tiles, int ntiles, int npairs,
-                                       cplx<R>* smem, long long vb, int tid) {
-  const int tx = tid % N, ty = tid / N;
-  cplx<R>* buf = smem + ty * N * (N + 1);
+// Pass A on virtual block `vb` (IPB plane items, thread tid = ty * max(NX, NY) + tx).
+template <typename R, int NX, int NY, bool REAL, bool COH, int IPB, bool PDL>
+__device__ __forceinline__ void body_a(const PlaneParams<R, NX, NY>& P, const TileDesc* tiles, int ntiles,
+                                       int npairs, cplx<R>* smem, long long vb, int tid) {
+  constexpr int ML = kMaxLine<NX, NY>;
+  const int tx = tid % ML, ty = tid / ML;
+  cplx<R>* buf = smem + ty * NY * (NX + 1);
   const long long item = vb * IPB + ty;
-  const bool active = ty < IPB && item < (long long)npairs * N;
+  const bool active = ty < IPB && item < (long long)npairs * P.nz;
   int p = 0, z = 0, l = 0, r = 0;
   if (active) {
-    p = (int)(item / N);
-    z = (int)(item % N);
+    p = (int)(item / P.nz);
+    z = (int)(item % P.nz);
     decode_pair(tiles, ntiles, p, l, r);
-    cplx<R> a[N];
-    const long long xo = (long long)l * P.ld + (long long)z * N * N + tx;
-    const long long yo = (long long)r * P.ld + (long long)z * N * N + tx;
+  }
+  if (active && tx < NX) {
+    cplx<R> a[NY];
+    const long long xo = (long long)l * P.ld + (long long)z * NX * NY + tx;
+    const long long yo = (long long)r * P.ld + (long long)z * NX * NY + tx;
 #pragma unroll
-    for (int y = 0; y < N; ++y) {
-      const cplx<R> xv = load_vec<R, REAL>(P.X, xo + y * N);
-      const cplx<R> yv = load_vec<R, REAL>(P.Y, yo + y * N);
+    for (int y = 0; y < NY; ++y) {
+      const cplx<R> xv = load_vec<R, REAL>(P.X, xo + y * NX);
+      const cplx<R> yv = load_vec<R, REAL>(P.Y, yo + y * NX);
       a[y] = cmulc(xv, yv);                   // conj(x_l) * y_r
     }
-    dft<N, N, false, R>(a, P.tw);             // along y
+    dft<NY, NY, false, R>(a, P.tw.ty());      // along y, column x = tx
 #pragma unroll
-    for (int k = 0; k < N; ++k) buf[k * (N + 1) + tx] = a[k];
+    for (int k = 0; k < NY; ++k) buf[k * (NX + 1) + tx] = a[k];
   }
   __syncthreads();
-  if (active) {
-    cplx<R> b[N];
+  if (active && tx < NY) {
+    cplx<R> b[NX];
 #pragma unroll
-    for (int x = 0; x < N; ++x) b[x] = buf[tx * (N + 1) + x];
-    dft<N, N, false, R>(b, P.tw);             // along x, row ky = tx
+    for (int x = 0; x < NX; ++x) b[x] = buf[tx * (NX + 1) + x];
+    dft<NX, NX, false, R>(b, P.tw.tx());      // along x, row ky = tx
     if constexpr (PDL) griddep_wait();        // the previous batch's pass D still reads S
-    cplx<R>* out = P.S + ((long long)p * N + z) * N * N + tx;
+    cplx<R>* out = P.S + ((long long)p * P.nz + z) * NX * NY + tx;
 #pragma unroll
-    for (int kx = 0; kx < N; ++kx) stx<COH>(out + kx * N, b[kx]);
+    for (int kx = 0; kx < NX; ++kx) stx<COH>(out + kx * NY, b[kx]);
   }
 }
 
 // Pass B on virtual block `vb` of `nthr` pencils. mode 0: Poisson (forward z,
 // K, inverse z); 1: energy only; 2: both. The energy partial of the block
 // (mode != 0) is added to *eslot by thread 0 (one owner per slot).
-template <typename R, int N, bool COH>
-__device__ __forceinline__ void body_b(const PairParams<R, N>& P, const TileDesc* tiles, int ntiles, int npairs,
+template <typename R, int NZ, bool COH, bool CUBE>
+__device__ __forceinline__ void body_b(const PencilParams<R, NZ>& P, const TileDesc* tiles, int ntiles, int npairs,
                                        int mode, long long vb, int tid, int nthr, double* red, double* eslot) {
-  constexpr int N2 = N * N;
+  const PencilGeom<R, NZ, CUBE> G(P);
+  const int nxy = G.nxy;
   const long long gid = vb * nthr + tid;
-  const bool active = gid < (long long)npairs * N2;
+  const bool active = gid < (long long)npairs * nxy;
   double e = 0.0;
   if (active) {
-    const int p = (int)(gid / N2);
-    const int f = (int)(gid % N2);
-    cplx<R>* s = P.S + (long long)p * N * N2 + f;
-    cplx<R> a[N];
+    const int p = (int)(gid / nxy);
+    const int f = (int)(gid % nxy);
+    cplx<R>* s = P.S + (long long)p * NZ * nxy + f;
+    cplx<R> a[NZ];
 #pragma unroll
-    for (int zz = 0; zz < N; ++zz) a[zz] = ldx<COH>(s + (long long)zz * N2);
-    dft<N, N, false, R>(a, P.tw);
+    for (int zz = 0; zz < NZ; ++zz) a[zz] = ldx<COH>(s + (long long)zz * nxy);
+    dft<NZ, NZ, false, R>(a, P.tw);
     R acc = R(0);
-    const R* kt = P.Kt + kt_pencil<N>(f);
+    const R* kt = P.Kt + G.kt_pencil(f);
 #pragma unroll
-    for (int kz = 0; kz < N; ++kz) {
-      const R k = kt[kfold<N>(kz) * (kKH<N> * kKH<N>)];
+    for (int kz = 0; kz < NZ; ++kz) {
+      const R k = kt[kfold<NZ>(kz) * G.kzs];
       if (mode != 0) acc += k * (a[kz].x * a[kz].x + a[kz].y * a[kz].y);
       a[kz] = cscale(a[kz], k);
     }
@@ -221,9 +290,9 @@ __device__ __forceinline__ void body_b(const PairParams<R, N>& P, const TileDesc
       e = (l == r ? 1.0 : 2.0) * (double)acc;
     }
     if (mode != 1) {
-      dft<N, N, true, R>(a, P.tw);
+      dft<NZ, NZ, true, R>(a, P.tw);
 #pragma unroll
-      for (int zz = 0; zz < N; ++zz) stx<COH>(s + (long long)zz * N2, a[zz]);
+      for (int zz = 0; zz < NZ; ++zz) stx<COH>(s + (long long)zz * nxy, a[zz]);
     }
   }
   if (mode != 0) {
@@ -240,32 +309,36 @@ __device__ __forceinline__ void body_b(const PairParams<R, N>& P, const TileDesc
 }
 
 // Pass C on virtual block `vb` (IPB plane items).
-template <typename R, int N, bool COH, int IPB>
-__device__ __forceinline__ void body_c(const PairParams<R, N>& P, int npairs, cplx<R>* smem, long long vb, int tid) {
-  const int tx = tid % N, ty = tid / N;
-  cplx<R>* buf = smem + ty * N * (N + 1);
+template <typename R, int NX, int NY, bool COH, int IPB>
+__device__ __forceinline__ void body_c(const PlaneParams<R, NX, NY>& P, int npairs, cplx<R>* smem, long long vb,
+                                       int tid) {
+  constexpr int ML = kMaxLine<NX, NY>;
+  const int tx = tid % ML, ty = tid / ML;
+  cplx<R>* buf = smem + ty * NY * (NX + 1);
   const long long item = vb * IPB + ty;
-  const bool active = ty < IPB && item < (long long)npairs * N;
+  const bool active = ty < IPB && item < (long long)npairs * P.nz;
   cplx<R>* plane = nullptr;
   if (active) {
-    const int p = (int)(item / N);
-    const int z = (int)(item % N);
-    plane = P.S + ((long long)p * N + z) * N * N;
-    cplx<R> b[N];
+    const int p = (int)(item / P.nz);
+    const int z = (int)(item % P.nz);
+    plane = P.S + ((long long)p * P.nz + z) * NX * NY;
+  }
+  if (active && tx < NY) {
+    cplx<R> b[NX];
 #pragma unroll
-    for (int kx = 0; kx < N; ++kx) b[kx] = ldx<COH>(plane + kx * N + tx);   // row ky = tx
-    dft<N, N, true, R>(b, P.tw);                                            // inverse along x
+    for (int kx = 0; kx < NX; ++kx) b[kx] = ldx<COH>(plane + kx * NY + tx);   // row ky = tx
+    dft<NX, NX, true, R>(b, P.tw.tx());                                      // inverse along x
 #pragma unroll
-    for (int x = 0; x < N; ++x) buf[tx * (N + 1) + x] = b[x];
+    for (int x = 0; x < NX; ++x) buf[tx * (NX + 1) + x] = b[x];
   }
   __syncthreads();
-  if (active) {
-    cplx<R> a[N];
+  if (active && tx < NX) {
+    cplx<R> a[NY];
 #pragma unroll
-    for (int ky = 0; ky < N; ++ky) a[ky] = buf[ky * (N + 1) + tx];  // column x = tx
-    dft<N, N, true, R>(a, P.tw);                                    // inverse along y
+    for (int ky = 0; ky < NY; ++ky) a[ky] = buf[ky * (NX + 1) + tx];  // column x = tx
+    dft<NY, NY, true, R>(a, P.tw.ty());                               // inverse along y
 #pragma unroll
-    for (int y = 0; y < N; ++y) stx<COH>(plane + y * N + tx, a[y]);
+    for (int y = 0; y < NY; ++y) stx<COH>(plane + y * NX + tx, a[y]);
   }
 }
 
@@ -284,10 +357,10 @@ __device__ __forceinline__ void rmw_out(void* base, long long idx, cplx<R> acc, 
 // Full tiles (kTileMax orbitals per side): no runtime guards, so all loads of
 // the tile's pair potentials can be issued back to back. v is read once, so it
 // is loaded with the streaming (evict-first) hint.
-template <typename R, int N, bool REAL, bool COH>
-__device__ __forceinline__ void d_full_diag(const PairParams<R, N>& P, const TileDesc& d,
+template <typename R, bool REAL, bool COH, long long NGC>
+__device__ __forceinline__ void d_full_diag(const PointParams<R>& P, const TileDesc& d,
                                             const cplx<R>* __restrict__ V, long long g) {
-  constexpr long long NG = (long long)N * N * N;
+  const long long NG = NGC ? NGC : P.ng;
   constexpr int B = kTileMax;
   cplx<R> x[B], acc[B];
 #pragma unroll
@@ -309,10 +382,10 @@ __device__ __forceinline__ void d_full_diag(const PairParams<R, N>& P, const Til
   for (int o = 0; o < B; ++o) rmw_out<R, REAL, COH>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
 }
 
-template <typename R, int N, bool REAL, bool COH>
-__device__ __forceinline__ void d_full_off(const PairParams<R, N>& P, const TileDesc& d,
+template <typename R, bool REAL, bool COH, long long NGC>
+__device__ __forceinline__ void d_full_off(const PointParams<R>& P, const TileDesc& d,
                                            const cplx<R>* __restrict__ V, long long g) {
-  constexpr long long NG = (long long)N * N * N;
+  const long long NG = NGC ? NGC : P.ng;
   constexpr int B = kTileMax;
   cplx<R> xl[B], yr[B], al[B], ar[B];
 #pragma unroll
@@ -346,10 +419,10 @@ __device__ __forceinline__ void d_full_off(const PairParams<R, N>& P, const Tile
 // halves of r) meet through shared memory and are added in a fixed order;
 // thread h then updates Out_l for l0 + 4h .. l0 + 4h + 3 and Out_r for its r.
 constexpr int kDSplitPts = 128;   // points per 256-thread block
-template <typename R, int N, bool REAL>
-__device__ __forceinline__ void d_split_off(const PairParams<R, N>& P, const TileDesc& d, long long vbx, int tid,
+template <typename R, bool REAL, long long NGC>
+__device__ __forceinline__ void d_split_off(const PointParams<R>& P, const TileDesc& d, long long vbx, int tid,
                                             cplx<R>* xch) {
-  constexpr long long NG = (long long)N * N * N;
+  const long long NG = NGC ? NGC : P.ng;
   constexpr int B = kTileMax, H = kTileMax / 2;
   const int h = (tid >> 5) & 1;
   const int pt = ((tid >> 6) << 5) | (tid & 31);
@@ -393,18 +466,19 @@ __device__ __forceinline__ void d_split_off(const PairParams<R, N>& P, const Til
   }
 }
 
-// Pass D for point block `vbx` (nthr points) of tile `d`.
-template <typename R, int N, bool REAL, bool COH, bool FULL_OFF = true>
-__device__ __forceinline__ void body_d(const PairParams<R, N>& P, const TileDesc& d, long long vbx, int tid,
+// Pass D for point block `vbx` (nthr points) of tile `d`; NGC = N_g at compile
+// time (cubic grids) or 0 (read from the parameters).
+template <typename R, bool REAL, bool COH, bool FULL_OFF, long long NGC>
+__device__ __forceinline__ void body_d(const PointParams<R>& P, const TileDesc& d, long long vbx, int tid,
                                        int nthr) {
-  constexpr long long NG = (long long)N * N * N;
+  const long long NG = NGC ? NGC : P.ng;
   const long long g = vbx * nthr + tid;
   if (g >= NG) return;
   const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
   if (d.kind == 1 && d.nl == kTileMax) {
-    d_full_diag<R, N, REAL, COH>(P, d, V, g);
+    d_full_diag<R, REAL, COH, NGC>(P, d, V, g);
   } else if (FULL_OFF && d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
-    d_full_off<R, N, REAL, COH>(P, d, V, g);
+    d_full_off<R, REAL, COH, NGC>(P, d, V, g);
   } else if (d.kind == 1) {
     cplx<R> x[kTileMax], acc[kTileMax];
 #pragma unroll
@@ -474,18 +548,26 @@ __device__ __forceinline__ void body_d(const PairParams<R, N>& P, const TileDesc
 }
 
 // ---------------------------------------------------------------- four-kernel mode
-template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
-pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
+template <typename R, int NX, int NY, bool REAL>
+__global__ void __launch_bounds__(kMaxLine<NX, NY> * plane_items<R, NX, NY>(), 2)
+pass_a_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   griddep_launch();
-  body_a<R, N, REAL, false, plane_items<R, N>(), true>(P, P.tiles, P.ntiles, P.npairs,
-                                                       reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
+  body_a<R, NX, NY, REAL, false, plane_items<R, NX, NY>(), true>(
+      P, P.tiles, P.ntiles, P.npairs, reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
 }
 
-// Pass B for the large edges (n >= 64), whose whole pencil per thread spills:
-// two lanes per z-pencil (lanes 2q, 2q+1 of a warp; 128 pencils per block).
-// Lane h holds the samples z = 2m + h and transforms them with a DFT of N/2:
+template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
+  T r;
+  r.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
+  r.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
+  return r;
+}
+
+// Pass B for the large pencils (n_z >= 64), whose whole pencil per thread
+// spills: two lanes per z-pencil (lanes 2q, 2q+1 of a warp; 128 pencils per
+// block). Lane h holds the samples z = 2m + h and transforms them with a DFT of
+// N/2:
 //   forward  Y[k] = E[k] + w^k O[k], Y[k + N/2] = E[k] - w^k O[k]
 //            (E, O the half-length transforms of the even / odd samples,
 //            w = exp(-2 pi i / N)); lane h keeps k in [hN/4, (h+1)N/4) and gets
@@ -494,39 +576,35 @@ pass_a_kernel(const __grid_constant__ PairParams<R, N> P) {
 //            over k < N/2; each lane forms its quarter of both sequences and
 //            swaps the other lane's by shuffle; lane 0 transforms the first,
 //            lane 1 the second.
-// Lane roles are selected arithmetically (no divergent branches). At n = 48 the
-// shuffles cost more than the occupancy gains, so smaller edges keep one
+// Lane roles are selected arithmetically (no divergent branches). At n_z = 48
+// the shuffles cost more than the occupancy gains, so shorter pencils keep one
 // thread per pencil.
-template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
-  T r;
-  r.x = __shfl_xor_sync(0xffffffffu, v.x, 1);
-  r.y = __shfl_xor_sync(0xffffffffu, v.y, 1);
-  return r;
-}
 constexpr int kBSplitPencils = 128;   // pencils per 256-thread block of the split pass B
-
 // FP64 pencils of 64+ points need the whole register file of a thread: one block per SM.
 template <typename R, int N> constexpr int kBSplitBlocks = sizeof(R) == 8 ? 1 : 2;
+template <int NZ> constexpr bool kSplitPencil = NZ >= 64 && NZ % 4 == 0;
 
-template <typename R, int N>
-__global__ void __launch_bounds__(256, kBSplitBlocks<R, N>)
-pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
+template <typename R, int NZ, bool CUBE>
+__global__ void __launch_bounds__(256, kBSplitBlocks<R, NZ>)
+pass_b_split_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
   using C = cplx<R>;
-  constexpr int N2 = N * N, M = N / 2, H = N / 4;
+  constexpr int N = NZ, M = N / 2, H = N / 4;
   static_assert(N % 4 == 0, "the split pass B halves a pencil twice");
   __shared__ double red[8];
   griddep_launch();
   griddep_wait();
+  const PencilGeom<R, NZ, CUBE> G(P);
+  const int nxy = G.nxy;
   const int tid = threadIdx.x, h = tid & 1;
   const long long gid = (long long)blockIdx.x * kBSplitPencils + (tid >> 1);
-  const bool active = gid < (long long)P.npairs * N2;     // same for both lanes of a pencil
-  const int p = active ? (int)(gid / N2) : 0;
-  const int f = active ? (int)(gid % N2) : 0;
-  C* s = P.S + (long long)p * N * N2 + f;
+  const bool active = gid < (long long)P.npairs * nxy;    // same for both lanes of a pencil
+  const int p = active ? (int)(gid / nxy) : 0;
+  const int f = active ? (int)(gid % nxy) : 0;
+  C* s = P.S + (long long)p * N * nxy + f;
   const C zero = cmk<C>(R(0), R(0));
   C a[M];
 #pragma unroll
-  for (int m = 0; m < M; ++m) a[m] = active ? s[(long long)(2 * m + h) * N2] : zero;
+  for (int m = 0; m < M; ++m) a[m] = active ? s[(long long)(2 * m + h) * nxy] : zero;
   dft<M, N, false, R>(a, P.tw);                            // E (lane 0) or O (lane 1)
 #pragma unroll
   for (int k = 0; k < M; ++k) {                            // lane 1: w^k O[k]
@@ -543,11 +621,11 @@ pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
     y[H + j] = csub(ev, od);
   }
   R acc = R(0);
-  const R* kt = P.Kt + kt_pencil<N>(f);
+  const R* kt = P.Kt + G.kt_pencil(f);
 #pragma unroll
   for (int j = 0; j < M; ++j) {
     const int kz = h * H + (j < H ? j : j - H + M);
-    const R k = kt[kfold<N>(kz) * (kKH<N> * kKH<N>)];
+    const R k = kt[kfold<N>(kz) * G.kzs];
     if (mode != 0) acc += k * (y[j].x * y[j].x + y[j].y * y[j].y);
     y[j] = cscale(y[j], k);
   }
@@ -569,7 +647,7 @@ pass_b_split_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
     dft<M, N, true, R>(a, P.tw);                           // x[2m + h] = a[m]
     if (active) {
 #pragma unroll
-      for (int m = 0; m < M; ++m) s[(long long)(2 * m + h) * N2] = a[m];
+      for (int m = 0; m < M; ++m) s[(long long)(2 * m + h) * nxy] = a[m];
     }
   }
   if (mode != 0) {
@@ -610,144 +688,170 @@ __device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)
     y[H + j] = csub(ev, od);
   }
 }
-// FP32 edges whose plane passes use the two-lane line transforms (one plane
-// per block), and the blocks per SM their launch bounds ask for: at 48^3 the
-// half-length lines need 72-95 registers, so six 96-thread blocks (18-27 warps)
-// fit an SM where the one-thread-per-line form runs 15 warps at 117-128.
-// Below 48 the whole-line form is as fast (several planes per block). Pass A
-// at 48^3 is held to 80 registers (eight blocks, 24 warps): 1.3 % faster steps.
-// FP64 lines take the two-lane form from n = 64 (a whole FP64 line of 64 would
-// not fit a thread's registers), with one or two blocks per SM.
+// Planes whose passes use the two-lane line transforms (one plane per block),
+// and the blocks per SM their launch bounds ask for: at 48^3 the half-length
+// lines need 72-95 registers, so six 96-thread blocks (18-27 warps) fit an SM
+// where the one-thread-per-line form runs 15 warps at 117-128. Below 48 the
+// whole-line form is as fast (several planes per block). Pass A at 48^3 is held
+// to 80 registers (eight blocks, 24 warps): 1.3 % faster steps. FP64 lines take
+// the two-lane form from 64 (a whole FP64 line of 64 would not fit a thread's
+// registers), with one or two blocks per SM.
 constexpr int kSplitMinEdge = 48;
 constexpr int kSplitMinEdgeF64 = 64;
-template <typename R, int N> constexpr bool kSplitPlanes =
-    N % 4 == 0 && (sizeof(R) == 4 ? N >= kSplitMinEdge : N >= kSplitMinEdgeF64);
-template <typename R, int N> constexpr int kSplitBlocks = sizeof(R) == 8 ? (N >= 96 ? 1 : 2) : (N >= 96 ? 2 : 6);
-template <typename R, int N> constexpr int kSplitBlocksA = sizeof(R) == 4 && N == 48 ? 8 : kSplitBlocks<R, N>;
-template <typename R, int N> constexpr size_t kSplitSmem = (size_t)N * (N + 1) * sizeof(cplx<R>);
+template <typename R, int NX, int NY> constexpr bool kSplitPlanes =
+    NX % 4 == 0 && NY % 4 == 0 &&
+    (sizeof(R) == 4 ? kMaxLine<NX, NY> >= kSplitMinEdge : kMaxLine<NX, NY> >= kSplitMinEdgeF64);
+template <typename R, int NX, int NY> constexpr int kSplitBlocks =
+    sizeof(R) == 8 ? (kMaxLine<NX, NY> >= 96 ? 1 : 2) : (kMaxLine<NX, NY> >= 96 ? 2 : 6);
+template <typename R, int NX, int NY> constexpr int kSplitBlocksA =
+    sizeof(R) == 4 && NX == 48 && NY == 48 ? 8 : kSplitBlocks<R, NX, NY>;
+template <typename R, int NX, int NY> constexpr size_t kSplitSmem = (size_t)NY * (NX + 1) * sizeof(cplx<R>);
 
 // frequency index held in y[j] by lane h
 template <int N> __device__ __forceinline__ int split_index(int j, int h) {
   return h * (N / 4) + (j < N / 4 ? j : j - N / 4 + N / 2);
 }
 
-// Passes A and C with two lanes per line (FP32, n >= 48): one plane per block
-// (2n threads), each pass's two line transforms by split_line_dft, the
-// transpose through shared memory as in the one-thread-per-line form. Half the
-// registers of a whole line per thread (which at 96^3 would need over 200), so
-// more warps per SM hide the latency of the plane loads and stores.
-template <typename R, int N, bool REAL>
-__global__ void __launch_bounds__(2 * N, kSplitBlocksA<R, N>)
-pass_a_split_kernel(const __grid_constant__ PairParams<R, N> P) {
+// Passes A and C with two lanes per line: one plane per block (2 max(n_x, n_y)
+// threads), each pass's two line transforms by split_line_dft, the transpose
+// through shared memory as in the one-thread-per-line form. Half the registers
+// of a whole line per thread (which at 96^3 would need over 200), so more
+// warps per SM hide the latency of the plane loads and stores. On a
+// non-square plane the lanes past the shorter edge compute on zeros and store
+// nothing, so every lane of a warp takes part in the shuffles.
+template <typename R, int NX, int NY, bool REAL>
+__global__ void __launch_bounds__(2 * kMaxLine<NX, NY>, kSplitBlocksA<R, NX, NY>)
+pass_a_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   using C = cplx<R>;
-  constexpr int M = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   griddep_launch();
   const int tid = threadIdx.x, q = tid >> 1, h = tid & 1;
   const long long item = blockIdx.x;                      // one (pair, z) plane per block
-  const int p = (int)(item / N), z = (int)(item % N);
+  const int p = (int)(item / P.nz), z = (int)(item % P.nz);
   int l, r;
   decode_pair(P.tiles, P.ntiles, p, l, r);
-  C a[M], y[M];
+  const C zero = cmk<C>(R(0), R(0));
   {   // column x = q: samples y = 2m + h
-    const long long xo = (long long)l * P.ld + (long long)z * N * N + q;
-    const long long yo = (long long)r * P.ld + (long long)z * N * N + q;
+    constexpr int M = NY / 2;
+    const bool act = q < NX;
+    C a[M], y[M];
+    const long long xo = (long long)l * P.ld + (long long)z * NX * NY + q;
+    const long long yo = (long long)r * P.ld + (long long)z * NX * NY + q;
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const int yy = 2 * m + h;
-      a[m] = cmulc(load_vec<R, REAL>(P.X, xo + yy * N), load_vec<R, REAL>(P.Y, yo + yy * N));
+      a[m] = act ? cmulc(load_vec<R, REAL>(P.X, xo + yy * NX), load_vec<R, REAL>(P.Y, yo + yy * NX)) : zero;
     }
-    split_line_dft<N, false, R>(a, y, h, P.tw);          // along y
+    split_line_dft<NY, false, R>(a, y, h, P.tw.ty());     // along y
+    if (act) {
 #pragma unroll
-    for (int j = 0; j < M; ++j) buf[split_index<N>(j, h) * (N + 1) + q] = y[j];
+      for (int j = 0; j < M; ++j) buf[split_index<NY>(j, h) * (NX + 1) + q] = y[j];
+    }
   }
   __syncthreads();
   {   // row ky = q: samples x = 2m + h
+    constexpr int M = NX / 2;
+    const bool act = q < NY;
+    C a[M], y[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) a[m] = buf[q * (N + 1) + 2 * m + h];
-    split_line_dft<N, false, R>(a, y, h, P.tw);          // along x
+    for (int m = 0; m < M; ++m) a[m] = act ? buf[q * (NX + 1) + 2 * m + h] : zero;
+    split_line_dft<NX, false, R>(a, y, h, P.tw.tx());     // along x
     griddep_wait();                                        // the previous batch's pass D still reads S
-    C* out = P.S + ((long long)p * N + z) * N * N + q;
+    if (act) {
+      C* out = P.S + ((long long)p * P.nz + z) * NX * NY + q;
 #pragma unroll
-    for (int j = 0; j < M; ++j) out[(long long)split_index<N>(j, h) * N] = y[j];
+      for (int j = 0; j < M; ++j) out[(long long)split_index<NX>(j, h) * NY] = y[j];
+    }
   }
 }
 
-template <typename R, int N>
-__global__ void __launch_bounds__(2 * N, kSplitBlocks<R, N>)
-pass_c_split_kernel(const __grid_constant__ PairParams<R, N> P) {
+template <typename R, int NX, int NY>
+__global__ void __launch_bounds__(2 * kMaxLine<NX, NY>, kSplitBlocks<R, NX, NY>)
+pass_c_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   using C = cplx<R>;
-  constexpr int M = N / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   griddep_launch();
   griddep_wait();
   const int tid = threadIdx.x, q = tid >> 1, h = tid & 1;
   const long long item = blockIdx.x;
-  const int p = (int)(item / N), z = (int)(item % N);
-  C* plane = P.S + ((long long)p * N + z) * N * N;
-  C a[M], y[M];
+  const int p = (int)(item / P.nz), z = (int)(item % P.nz);
+  C* plane = P.S + ((long long)p * P.nz + z) * NX * NY;
+  const C zero = cmk<C>(R(0), R(0));
   {   // row ky = q of the spectrum: samples kx = 2m + h, inverse along x
+    constexpr int M = NX / 2;
+    const bool act = q < NY;
+    C a[M], y[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) a[m] = plane[(long long)(2 * m + h) * N + q];
-    split_line_dft<N, true, R>(a, y, h, P.tw);
+    for (int m = 0; m < M; ++m) a[m] = act ? plane[(long long)(2 * m + h) * NY + q] : zero;
+    split_line_dft<NX, true, R>(a, y, h, P.tw.tx());
+    if (act) {
 #pragma unroll
-    for (int j = 0; j < M; ++j) buf[q * (N + 1) + split_index<N>(j, h)] = y[j];   // row ky, column x
+      for (int j = 0; j < M; ++j) buf[q * (NX + 1) + split_index<NX>(j, h)] = y[j];   // row ky, column x
+    }
   }
   __syncthreads();
   {   // column x = q: samples ky = 2m + h, inverse along y
+    constexpr int M = NY / 2;
+    const bool act = q < NX;
+    C a[M], y[M];
 #pragma unroll
-    for (int m = 0; m < M; ++m) a[m] = buf[(2 * m + h) * (N + 1) + q];
-    split_line_dft<N, true, R>(a, y, h, P.tw);
+    for (int m = 0; m < M; ++m) a[m] = act ? buf[(2 * m + h) * (NX + 1) + q] : zero;
+    split_line_dft<NY, true, R>(a, y, h, P.tw.ty());
+    if (act) {
 #pragma unroll
-    for (int j = 0; j < M; ++j) plane[(long long)split_index<N>(j, h) * N + q] = y[j];
+      for (int j = 0; j < M; ++j) plane[(long long)split_index<NY>(j, h) * NX + q] = y[j];
+    }
   }
 }
 
-template <typename R, int N>
+template <typename R, int NZ, bool CUBE>
 __global__ void __launch_bounds__(256, 2)
-pass_b_kernel(const __grid_constant__ PairParams<R, N> P, int mode) {
+pass_b_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
   __shared__ double red[32];
   griddep_launch();
   griddep_wait();
-  body_b<R, N, false>(P, P.tiles, P.ntiles, P.npairs, mode, blockIdx.x, threadIdx.x, blockDim.x, red,
-                      mode != 0 ? P.Epart + blockIdx.x : nullptr);
+  body_b<R, NZ, false, CUBE>(P, P.tiles, P.ntiles, P.npairs, mode, blockIdx.x, threadIdx.x, blockDim.x, red,
+                             mode != 0 ? P.Epart + blockIdx.x : nullptr);
 }
 
-template <typename R, int N>
-__global__ void __launch_bounds__(N * plane_items<R, N>(), 2)
-pass_c_kernel(const __grid_constant__ PairParams<R, N> P) {
+template <typename R, int NX, int NY>
+__global__ void __launch_bounds__(kMaxLine<NX, NY> * plane_items<R, NX, NY>(), 2)
+pass_c_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   griddep_launch();
   griddep_wait();
-  body_c<R, N, false, plane_items<R, N>()>(P, P.npairs, reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x, threadIdx.x);
+  body_c<R, NX, NY, false, plane_items<R, NX, NY>()>(P, P.npairs, reinterpret_cast<cplx<R>*>(smem_raw), blockIdx.x,
+                                                     threadIdx.x);
 }
 
 // Full off-diagonal tiles take two threads per grid point (d_split_off) at
 // four blocks per SM (64 registers): more warps and loads in flight per SM,
 // which measured faster than one thread per point at 2 or 3 blocks per SM
 // (and than streaming the potentials through shared memory with bulk copies).
-template <typename R, int N, bool REAL>
+template <typename R, bool REAL, long long NGC>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2)
-pass_d_kernel(const __grid_constant__ PairParams<R, N> P) {
+pass_d_kernel(const __grid_constant__ PointParams<R> P) {
   __shared__ cplx<R> xch[(kTileMax / 2) * 256];
   griddep_launch();
   griddep_wait();
   const TileDesc d = P.tiles[blockIdx.y];
   if (d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
-    d_split_off<R, N, REAL>(P, d, blockIdx.x, threadIdx.x, xch);
+    d_split_off<R, REAL, NGC>(P, d, blockIdx.x, threadIdx.x, xch);
     return;
   }
   // other tiles: one thread per point, 256 points per block (the grid is
   // sized for 128-point blocks, so the upper half of the blocks has no work)
-  if ((long long)blockIdx.x * 256 >= (long long)N * N * N) return;
-  body_d<R, N, REAL, false, false>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
+  if ((long long)blockIdx.x * 256 >= (NGC ? NGC : P.ng)) return;
+  body_d<R, REAL, false, false, NGC>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
 }
 
 // ---------------------------------------------------------------- persistent engine
 template <typename R, int N> struct EngineParams {
-  PairParams<R, N> P;           // npairs / ntiles unused: per batch from the table
+  PlaneParams<R, N, N> pl;      // npairs / ntiles unused: per batch from the table
+  PencilParams<R, N> pe;
+  PointParams<R> pt;
   const EngineBatch* batches;   // per batch: tiles, pairs, first task, tasks per pass
   int nbatches;
   int npasses;                  // 4 (Poisson) or 2 (energy only: A, B)
@@ -772,7 +876,6 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 // block only ever waits before it starts a task, with nothing of its own in
 // flight, so leaving is always safe. E.wait_bias > 0 (a test hook) asks for
 // more finished tasks than a pass has, so that every dependent wait runs out.
-
 template <typename R, int N, bool REAL>
 __global__ void __launch_bounds__(kEngineThreads, 2)
 pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
@@ -833,18 +936,18 @@ pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
     const int k = s_batch, pass = s_pass;
     const long long loc = s_loc;
     const EngineBatch& b = E.batches[k];
-    const TileDesc* tiles = E.P.tiles + b.toff;
+    const TileDesc* tiles = E.pl.tiles + b.toff;
     if (pass == 0) {
-      body_a<R, N, REAL, true, IPB, false>(E.P, tiles, b.ntiles, b.npairs, smem, loc, tid);
+      body_a<R, N, N, REAL, true, IPB, false>(E.pl, tiles, b.ntiles, b.npairs, smem, loc, tid);
     } else if (pass == 1) {
-      body_b<R, N, true>(E.P, tiles, b.ntiles, b.npairs, E.mode, loc, tid, kEngineThreads, red,
-                         E.mode != 0 ? E.P.Epart + loc : nullptr);
+      body_b<R, N, true, true>(E.pe, tiles, b.ntiles, b.npairs, E.mode, loc, tid, kEngineThreads, red,
+                               E.mode != 0 ? E.pe.Epart + loc : nullptr);
     } else if (pass == 2) {
-      body_c<R, N, true, IPB>(E.P, b.npairs, smem, loc, tid);
+      body_c<R, N, N, true, IPB>(E.pl, b.npairs, smem, loc, tid);
     } else {
       const long long nvb = ((long long)N * N * N + kEngineThreads - 1) / kEngineThreads;
       const TileDesc d = tiles[loc / nvb];
-      body_d<R, N, REAL, true>(E.P, d, loc % nvb, tid, kEngineThreads);
+      body_d<R, REAL, true, true, (long long)N * N * N>(E.pt, d, loc % nvb, tid, kEngineThreads);
     }
     __syncthreads();
     if (tid == 0) {
@@ -855,25 +958,159 @@ pair_engine_kernel(const __grid_constant__ EngineParams<R, N> E) {
 }
 
 // ---------------------------------------------------------------- host side
-template <typename R, int N>
-void fill_params(PairParams<R, N>& P, const PairLaunch& L, const Batch& b) {
+template <typename R, int NX, int NY>
+void fill_plane(PlaneParams<R, NX, NY>& P, const PairLaunch& L, const Batch& b) {
+  P.X = L.X;
+  P.Y = L.Y;
+  P.S = static_cast<cplx<R>*>(L.S);
+  P.ld = L.ld;
+  P.nz = L.nz;
+  P.npairs = b.npairs;
+  P.tiles = L.dtiles;
+  P.ntiles = b.ntiles;
+  P.tw.fill(L.twx, L.twy);
+}
+
+template <typename R, int NZ>
+void fill_pencil(PencilParams<R, NZ>& P, const PairLaunch& L, const Batch& b) {
+  P.S = static_cast<cplx<R>*>(L.S);
+  P.Kt = static_cast<const R*>(L.Kt);
+  P.Epart = L.Epart;
+  P.npairs = b.npairs;
+  P.nx = L.nx;
+  P.ny = L.ny;
+  P.nxy = L.nx * L.ny;
+  P.khy = L.ny / 2 + 1;
+  P.kzs = (L.nx / 2 + 1) * (L.ny / 2 + 1);
+  P.tiles = L.dtiles;
+  P.ntiles = b.ntiles;
+  for (int k = 0; k < NZ; ++k) {
+    P.tw.w[k].x = (R)L.twz[2 * k];
+    P.tw.w[k].y = (R)L.twz[2 * k + 1];
+  }
+}
+
+template <typename R>
+void fill_point(PointParams<R>& P, const PairLaunch& L) {
   P.X = L.X;
   P.Y = L.Y;
   P.OutX = L.OutX;
   P.OutY = L.OutY;
-  P.S = static_cast<cplx<R>*>(L.S);
-  P.Kt = static_cast<const R*>(L.Kt);
-  P.Epart = L.Epart;
+  P.S = static_cast<const cplx<R>*>(L.S);
   P.ld = L.ld;
+  P.ng = (long long)L.nx * L.ny * L.nz;
   P.scale = (R)L.scale;
-  P.npairs = b.npairs;
   P.tiles = L.dtiles;
-  P.ntiles = b.ntiles;
-  for (int k = 0; k < N; ++k) {
-    P.tw.w[k].x = (R)L.tw[2 * k];
-    P.tw.w[k].y = (R)L.tw[2 * k + 1];
+}
+
+// Pass A (pass == 0) or C (pass == 2) of one batch, or (prepare_only) the
+// kernels' shared-memory attributes, set once at plan creation on the plan's
+// device, never during stream capture.
+template <typename R, int NX, int NY>
+bool launch_plane(const PairLaunch& L, const Batch& b, int pass, cudaStream_t st) {
+  constexpr int IPB = plane_items<R, NX, NY>();
+  constexpr int ML = kMaxLine<NX, NY>;
+  constexpr size_t smem = (size_t)IPB * NY * (NX + 1) * sizeof(cplx<R>);
+  if constexpr (sizeof(R) != 8) {
+    if (L.real_io) return false;
+  }
+  if (L.prepare_only) {
+    if constexpr (!kSplitPlanes<R, NX, NY>) {   // whole lines per thread
+      if constexpr (sizeof(R) == 8) {
+        cudaFuncSetAttribute(pass_a_kernel<R, NX, NY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(pass_a_kernel<R, NX, NY, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
+      cudaFuncSetAttribute(pass_a_kernel<R, NX, NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_c_kernel<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(pass_a_kernel<R, NX, NY, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(pass_c_kernel<R, NX, NY>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    } else {
+      constexpr int s1 = (int)kSplitSmem<R, NX, NY>;
+      if constexpr (sizeof(R) == 8) {
+        cudaFuncSetAttribute(pass_a_split_kernel<R, NX, NY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+        cudaFuncSetAttribute(pass_a_split_kernel<R, NX, NY, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      }
+      cudaFuncSetAttribute(pass_a_split_kernel<R, NX, NY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+      cudaFuncSetAttribute(pass_c_split_kernel<R, NX, NY>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
+      cudaFuncSetAttribute(pass_a_split_kernel<R, NX, NY, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      cudaFuncSetAttribute(pass_c_split_kernel<R, NX, NY>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    }
+    return true;
+  }
+  PlaneParams<R, NX, NY> P;
+  fill_plane<R, NX, NY>(P, L, b);
+  const long long items = (long long)b.npairs * L.nz;
+  const bool pdl = !L.no_pdl;
+  if constexpr (kSplitPlanes<R, NX, NY>) {
+    const dim3 grid((unsigned)items), blk(2 * ML);
+    if (pass == 0) {
+      if (sizeof(R) == 8 && L.real_io)
+        launch_pdl(pdl, pass_a_split_kernel<R, NX, NY, sizeof(R) == 8>, grid, blk, kSplitSmem<R, NX, NY>, st, P);
+      else
+        launch_pdl(pdl, pass_a_split_kernel<R, NX, NY, false>, grid, blk, kSplitSmem<R, NX, NY>, st, P);
+    } else {
+      launch_pdl(pdl, pass_c_split_kernel<R, NX, NY>, grid, blk, kSplitSmem<R, NX, NY>, st, P);
+    }
+  } else {
+    const dim3 grid((unsigned)((items + IPB - 1) / IPB)), blk(ML * IPB);
+    if (pass == 0) {
+      if (sizeof(R) == 8 && L.real_io)
+        launch_pdl(pdl, pass_a_kernel<R, NX, NY, sizeof(R) == 8>, grid, blk, smem, st, P);
+      else
+        launch_pdl(pdl, pass_a_kernel<R, NX, NY, false>, grid, blk, smem, st, P);
+    } else {
+      launch_pdl(pdl, pass_c_kernel<R, NX, NY>, grid, blk, smem, st, P);
+    }
+  }
+  return true;
+}
+
+// Pass B of one batch (the compile-time geometry on cubic grids).
+template <typename R, int NZ, bool CUBE>
+void launch_pencil_as(const PencilParams<R, NZ>& P, const PairLaunch& L, long long pencils, cudaStream_t st) {
+  if constexpr (kSplitPencil<NZ>) {
+    const unsigned grid = (unsigned)((pencils + kBSplitPencils - 1) / kBSplitPencils);
+    launch_pdl(!L.no_pdl, pass_b_split_kernel<R, NZ, CUBE>, dim3(grid), dim3(256), 0, st, P, L.mode);
+  } else {
+    const unsigned grid = (unsigned)((pencils + 255) / 256);
+    launch_pdl(!L.no_pdl, pass_b_kernel<R, NZ, CUBE>, dim3(grid), dim3(256), 0, st, P, L.mode);
   }
 }
+template <typename R, int NZ>
+bool launch_pencil(const PairLaunch& L, const Batch& b, cudaStream_t st) {
+  if (L.prepare_only) return true;
+  PencilParams<R, NZ> P;
+  fill_pencil<R, NZ>(P, L, b);
+  const long long pencils = (long long)b.npairs * L.nx * L.ny;
+  if (L.nx == NZ && L.ny == NZ) launch_pencil_as<R, NZ, true>(P, L, pencils, st);
+  else launch_pencil_as<R, NZ, false>(P, L, pencils, st);
+  return true;
+}
+
+// Pass D of one batch: NGC = N_g of a cubic grid compiled in, or 0 (any grid).
+template <typename R, long long NGC>
+bool launch_point(const PairLaunch& L, const Batch& b, cudaStream_t st) {
+  if (L.prepare_only) return true;
+  PointParams<R> P;
+  fill_point<R>(P, L);
+  if (NGC && P.ng != NGC) return false;
+  const dim3 grid((unsigned)((P.ng + kDSplitPts - 1) / kDSplitPts), (unsigned)b.ntiles);
+  if constexpr (sizeof(R) == 8) {
+    if (L.real_io) {
+      launch_pdl(!L.no_pdl, pass_d_kernel<R, true, NGC>, grid, dim3(256), 0, st, P);
+      return true;
+    }
+  } else {
+    if (L.real_io) return false;
+  }
+  launch_pdl(!L.no_pdl, pass_d_kernel<R, false, NGC>, grid, dim3(256), 0, st, P);
+  return true;
+}
+
+// The persistent engine holds whole lines per thread; FP64 lines of 64 or more
+// points do not fit, so those edges have no engine (plans fall back to the four
+// kernels per batch).
+template <typename R, int N> constexpr bool kEngineBuilt = !(sizeof(R) == 8 && N >= kSplitMinEdgeF64);
 
 // Tasks per pass of a batch in the engine (A, B, C, D).
 template <typename R, int N>
@@ -885,34 +1122,29 @@ void engine_tasks(const Batch& b, int n[4]) {
   n[3] = (int)((((long long)N * N * N + kEngineThreads - 1) / kEngineThreads) * b.ntiles);
 }
 
-// The persistent engine holds whole lines per thread; FP64 lines of 64 or more
-// points do not fit, so those edges have no engine (plans fall back to the four
-// kernels per batch).
-template <typename R, int N> constexpr bool kEngineBuilt = !(sizeof(R) == 8 && N >= kSplitMinEdgeF64);
-
 template <typename R, int N>
 void engine_prepare(EngineInfo& info) {
   if constexpr (!kEngineBuilt<R, N>) {
     info = EngineInfo{};
     return;
   } else {
-  constexpr int IPB = engine_items<R, N>();
-  constexpr size_t smem = (size_t)IPB * N * (N + 1) * sizeof(cplx<R>);
-  info.smem = smem;
-  info.threads = kEngineThreads;
-  int dev = 0, sms = 0, per = 0, occ = 1 << 30;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto one = [&](auto kern) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kEngineThreads, smem);
-    if (per < occ) occ = per;
-  };
-  one(pair_engine_kernel<R, N, false>);
-  if constexpr (sizeof(R) == 8) one(pair_engine_kernel<R, N, true>);
-  info.blocks = occ > 0 ? occ * sms : 0;
+    constexpr int IPB = engine_items<R, N>();
+    constexpr size_t smem = (size_t)IPB * N * (N + 1) * sizeof(cplx<R>);
+    info.smem = smem;
+    info.threads = kEngineThreads;
+    int dev = 0, sms = 0, per = 0, occ = 1 << 30;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    auto one = [&](auto kern) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      per = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, kEngineThreads, smem);
+      if (per < occ) occ = per;
+    };
+    one(pair_engine_kernel<R, N, false>);
+    if constexpr (sizeof(R) == 8) one(pair_engine_kernel<R, N, true>);
+    info.blocks = occ > 0 ? occ * sms : 0;
   }
 }
 
@@ -921,134 +1153,48 @@ bool launch_engine(const PairLaunch& L, const EngineLaunch& EL, cudaStream_t st)
   if constexpr (!kEngineBuilt<R, N>) {
     return false;
   } else {
-  EngineParams<R, N> E;
-  Batch none{};
-  fill_params<R, N>(E.P, L, none);
-  E.P.tiles = EL.dtiles;
-  E.batches = EL.batches;
-  E.nbatches = EL.nbatches;
-  E.npasses = L.mode == 1 ? 2 : 4;
-  E.ntasks = EL.ntasks;
-  E.head = EL.head;
-  E.done = EL.done;
-  E.status = EL.status;
-  E.mode = L.mode;
-  E.spin_limit = EL.spin_limit;
-  E.wait_bias = EL.wait_bias;
-  cudaLaunchConfig_t cfg{};
-  long long blocks = EL.blocks;
-  if (blocks > EL.ntasks) blocks = EL.ntasks;
-  if (blocks < 1) return true;
-  cfg.gridDim = dim3((unsigned)blocks);
-  cfg.blockDim = dim3(kEngineThreads);
-  cfg.dynamicSmemBytes = EL.smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident (required by the waits)
-  at[0].val.cooperative = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  if constexpr (sizeof(R) == 8) {
-    if (L.real_io) {
-      cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, true>, E);
-      return true;
-    }
-  }
-  if (L.real_io) return false;
-  cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, false>, E);
-  return true;
-  }
-}
-
-template <typename R, int N>
-bool launch_edge(const PairLaunch& L, const Batch& b, cudaStream_t st) {
-  constexpr int IPB = plane_items<R, N>();
-  constexpr size_t smem = (size_t)IPB * N * (N + 1) * sizeof(cplx<R>);
-  if (L.prepare_only) {
-    // opt in to > 48 KB of dynamic shared memory and the largest carveout; done
-    // once at plan creation on the plan's device, never during stream capture
-    if constexpr (!kSplitPlanes<R, N>) {   // whole lines per thread
-      if constexpr (sizeof(R) == 8) {
-        cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(pass_a_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      }
-      cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      cudaFuncSetAttribute(pass_a_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      cudaFuncSetAttribute(pass_c_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    } else {
-      constexpr int s1 = (int)kSplitSmem<R, N>;
-      if constexpr (sizeof(R) == 8) {
-        cudaFuncSetAttribute(pass_a_split_kernel<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-        cudaFuncSetAttribute(pass_a_split_kernel<R, N, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      }
-      cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-      cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, s1);
-      cudaFuncSetAttribute(pass_a_split_kernel<R, N, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-      cudaFuncSetAttribute(pass_c_split_kernel<R, N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    }
-    return true;
-  }
-  PairParams<R, N> P;
-  fill_params<R, N>(P, L, b);
-  auto mark = [&](int k) { if (L.ev) cudaEventRecord(L.ev[k], st); };
-  const long long items = (long long)b.npairs * N;
-  const dim3 pblk(N * IPB);
-  const unsigned pgrid = (unsigned)((items + IPB - 1) / IPB);
-  const unsigned bgrid = (unsigned)(((long long)b.npairs * N * N + 255) / 256);
-  const dim3 dgrid((unsigned)(((long long)N * N * N + kDSplitPts - 1) / kDSplitPts), (unsigned)b.ntiles);
-  if constexpr (sizeof(R) != 8) {
-    if (L.real_io) return false;
-  }
-  const int mask = L.pass_mask ? L.pass_mask : 15;
-  mark(0);
-  if (mask & 1) {
-    if constexpr (kSplitPlanes<R, N>) {
-      if (sizeof(R) == 8 && L.real_io)
-        launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, sizeof(R) == 8>, dim3((unsigned)items), dim3(2 * N),
-                   kSplitSmem<R, N>, st, P);
-      else
-        launch_pdl(!L.no_pdl, pass_a_split_kernel<R, N, false>, dim3((unsigned)items), dim3(2 * N), kSplitSmem<R, N>,
-                   st, P);
-    } else if constexpr (sizeof(R) == 8) {
-      if (L.real_io) launch_pdl(!L.no_pdl, pass_a_kernel<R, N, true>, dim3(pgrid), pblk, smem, st, P);
-      else launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
-    } else {
-      launch_pdl(!L.no_pdl, pass_a_kernel<R, N, false>, dim3(pgrid), pblk, smem, st, P);
-    }
-  }
-  mark(1);
-  if (mask & 2) {
-    if constexpr (N >= 64) {
-      const unsigned sgrid = (unsigned)(((long long)b.npairs * N * N + kBSplitPencils - 1) / kBSplitPencils);
-      launch_pdl(!L.no_pdl, pass_b_split_kernel<R, N>, dim3(sgrid), dim3(256), 0, st, P, L.mode);
-    } else {
-      launch_pdl(!L.no_pdl, pass_b_kernel<R, N>, dim3(bgrid), dim3(256), 0, st, P, L.mode);
-    }
-  }
-  mark(2);
-  if (L.mode == 1) {
-    mark(3);
-    mark(4);
-    return true;
-  }
-  if (mask & 4) {
-    if constexpr (kSplitPlanes<R, N>)
-      launch_pdl(!L.no_pdl, pass_c_split_kernel<R, N>, dim3((unsigned)items), dim3(2 * N), kSplitSmem<R, N>, st, P);
-    else
-      launch_pdl(!L.no_pdl, pass_c_kernel<R, N>, dim3(pgrid), pblk, smem, st, P);
-  }
-  mark(3);
-  if (mask & 8) {
+    if (L.nx != N || L.ny != N || L.nz != N) return false;
+    EngineParams<R, N> E;
+    Batch none{};
+    fill_plane<R, N, N>(E.pl, L, none);
+    fill_pencil<R, N>(E.pe, L, none);
+    fill_point<R>(E.pt, L);
+    E.pl.tiles = EL.dtiles;
+    E.pe.tiles = EL.dtiles;
+    E.pt.tiles = EL.dtiles;
+    E.batches = EL.batches;
+    E.nbatches = EL.nbatches;
+    E.npasses = L.mode == 1 ? 2 : 4;
+    E.ntasks = EL.ntasks;
+    E.head = EL.head;
+    E.done = EL.done;
+    E.status = EL.status;
+    E.mode = L.mode;
+    E.spin_limit = EL.spin_limit;
+    E.wait_bias = EL.wait_bias;
+    cudaLaunchConfig_t cfg{};
+    long long blocks = EL.blocks;
+    if (blocks > EL.ntasks) blocks = EL.ntasks;
+    if (blocks < 1) return true;
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(kEngineThreads);
+    cfg.dynamicSmemBytes = EL.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;   // all blocks co-resident (required by the waits)
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
     if constexpr (sizeof(R) == 8) {
-      if (L.real_io) launch_pdl(!L.no_pdl, pass_d_kernel<R, N, true>, dgrid, dim3(256), 0, st, P);
-      else launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
-    } else {
-      launch_pdl(!L.no_pdl, pass_d_kernel<R, N, false>, dgrid, dim3(256), 0, st, P);
+      if (L.real_io) {
+        cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, true>, E);
+        return true;
+      }
     }
+    if (L.real_io) return false;
+    cudaLaunchKernelEx(&cfg, pair_engine_kernel<R, N, false>, E);
+    return true;
   }
-  mark(4);
-  return true;
 }
 
 }  // namespace ace

@@ -17,8 +17,12 @@
 //   FP64 (C) arithmetic, and every digit is an integer that FP16 holds exactly.
 // Products:
 //   Xi_gb = 2^{e_g + f_b} sum_{s,t} 2^{-8 (s+t)} P_st,  P_st = sum_k a^(s)_gk c^(t)_kb,
-//   keeping the slice pairs with s + t <= T (T = 5 for FP32 output: truncation
-//   about 2^-40 of |A||C|; T = 6 for FP64 output). The products of one weight
+//   keeping the slice pairs with s + t <= T = 6 and 5 slices per operand. The
+//   error before the final rounding is then below about 2^-41 max_k |A_gk|
+//   sum_k |C_kb| (the truncated slices and the dropped pairs): FP64 accuracy
+//   relative to the size of the terms of the sum, which an ill-conditioned
+//   L (large entries of L^{-*}) makes much larger than Xi itself; with
+//   T = 5 (2^-33) such cases lost FP32 accuracy. The products of one weight
 //   w = s + t share a tensor-memory accumulator. Over a group of 128 real K
 //   terms every partial sum is an integer below 2^24 in magnitude (at most 1.5
 //   2^16 per term and weight), so the FP32 accumulation is exact whatever its
@@ -29,7 +33,7 @@
 //
 // Per CTA (512 threads, one per SM): T - 1 accumulators of TN columns in TMEM;
 // K runs in chunks of 32 real terms (16 orbitals) through three shared-memory
-// stages, each holding 4 A slices (split on the fly from the FP32 loads) and
+// stages, each holding T - 1 A slices (split on the fly from the FP32 loads) and
 // the chunk's B slices (split once per call by oz_slice_b_kernel into the
 // stage layout, copied in with 16-byte loads). One thread issues the MMAs of a
 // chunk (2 K-steps per slice pair) and commits them to the stage's mbarrier;
@@ -58,7 +62,7 @@ constexpr unsigned kOzWaitLimit = 1u << 24;
 
 template <int T> struct Oz {
   static_assert(T == 5 || T == 6, "slice depth");
-  static constexpr int SA = 4;                 // A slices: 32 bits below the row maximum
+  static constexpr int SA = T - 1;             // A slices: 8 (T - 1) bits below the row maximum
   static constexpr int SB = T - 1;             // C slices
   static constexpr int NW = T - 1;             // accumulators, weights w = 2 .. T
   static constexpr int TN = T == 5 ? 128 : 96; // NW x TN <= 512 TMEM columns
@@ -209,7 +213,7 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
       v[i] = t;
     }
   };
-  // the 4 A slices of this thread's 8 values into stage `st`
+  // the SA slices of this thread's 8 values into stage `st`
   auto store_a = [&](unsigned char* st, const float4 (&v)[2]) {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -305,8 +309,10 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     }
     issued |= 1u << s;
     if ((c % OZ_GROUP) == OZ_GROUP - 1 || c == nchunks - 1) {
-      if (!settle(s)) { s_fail = 1; }                     // every MMA so far has completed
-      else drain();
+      // every MMA so far has completed; the warp drains only if all its threads saw it
+      const bool seen = __all_sync(0xffffffffu, settle(s));
+      if (seen) drain();
+      else s_fail = 1;
       __syncthreads();
       if (s_fail) { ok = false; break; }
     }
@@ -356,15 +362,16 @@ size_t align256_(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+constexpr int kOzT = 6;   // slice depth for both output precisions
+
 bool xi_oz_prepare() {
-  cudaFuncSetAttribute(oz_outer_kernel<5, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Oz<5>::SMEM);
-  cudaFuncSetAttribute(oz_outer_kernel<6, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Oz<6>::SMEM);
+  cudaFuncSetAttribute(oz_outer_kernel<kOzT, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Oz<kOzT>::SMEM);
+  cudaFuncSetAttribute(oz_outer_kernel<kOzT, double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, Oz<kOzT>::SMEM);
   return cudaGetLastError() == cudaSuccess;
 }
 
-size_t xi_oz_scratch_bytes(long long ng, int nk, int nb, bool out_f64) {
-  const size_t bsl = out_f64 ? oz_bsl_bytes<6>(nk, nb) : oz_bsl_bytes<5>(nk, nb);
-  return align256_((size_t)ng * sizeof(int)) + align256_((size_t)nb * sizeof(int)) + align256_(bsl);
+size_t xi_oz_scratch_bytes(long long ng, int nk, int nb, bool) {
+  return align256_((size_t)ng * sizeof(int)) + align256_((size_t)nb * sizeof(int)) + align256_(oz_bsl_bytes<kOzT>(nk, nb));
 }
 
 int launch_xi_oz(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,
@@ -379,21 +386,16 @@ int launch_xi_oz(const void* A, int nk, const double* C, int nb, long long ld, l
   const int nch = (nk + 15) / 16;
   const unsigned rgrid = (unsigned)((ng + 255) / 256 < 152 * 8 ? (ng + 255) / 256 : 152 * 8);
   oz_row_exp_kernel<<<rgrid, 256, 0, st>>>(a, nk, ld, ng, erow);
-  if (out_f64) {
-    using O = Oz<6>;
-    cudaMemsetAsync(bsl, 0, oz_bsl_bytes<6>(nk, nb), st);
-    oz_slice_b_kernel<6><<<nb, 256, 0, st>>>(C, nk, nb, nch, bsl, fcol);
-    const dim3 grid((nb + O::BB - 1) / O::BB, (unsigned)((ng + OZ_TM - 1) / OZ_TM));
-    oz_outer_kernel<6, double2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
-                                                                    static_cast<double2*>(Out), status);
-  } else {
-    using O = Oz<5>;
-    cudaMemsetAsync(bsl, 0, oz_bsl_bytes<5>(nk, nb), st);
-    oz_slice_b_kernel<5><<<nb, 256, 0, st>>>(C, nk, nb, nch, bsl, fcol);
-    const dim3 grid((nb + O::BB - 1) / O::BB, (unsigned)((ng + OZ_TM - 1) / OZ_TM));
-    oz_outer_kernel<5, float2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
-                                                                   static_cast<float2*>(Out), status);
-  }
+  using O = Oz<kOzT>;
+  cudaMemsetAsync(bsl, 0, oz_bsl_bytes<kOzT>(nk, nb), st);
+  oz_slice_b_kernel<kOzT><<<nb, 256, 0, st>>>(C, nk, nb, nch, bsl, fcol);
+  const dim3 grid((nb + O::BB - 1) / O::BB, (unsigned)((ng + OZ_TM - 1) / OZ_TM));
+  if (out_f64)
+    oz_outer_kernel<kOzT, double2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
+                                                                       static_cast<double2*>(Out), status);
+  else
+    oz_outer_kernel<kOzT, float2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
+                                                                      static_cast<float2*>(Out), status);
   return 3;
 }
 

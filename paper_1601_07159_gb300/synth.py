@@ -8,8 +8,9 @@ from it without sharing method code.
 Workloads are shaped like the silicon runs of Sec. 4 (Si8/Si64/Si216/Si512,
 Gamma-point, plane-wave basis):
 
-* cubic cell of edge ``L`` (bohr) sampled on an ``n^3`` grid, x fastest;
-* reciprocal vectors G = 2*pi*m/L with the wrapped FFT index m;
+* cubic cell of edge ``L`` (bohr) sampled on an ``n^3`` grid, x fastest (or an
+  orthorhombic cell L_x x L_y x L_z on an n_x x n_y x n_z grid);
+* reciprocal vectors G = 2*pi*m/L per axis with the wrapped FFT index m;
 * orbital coefficients c(G) = (a + i b)/sqrt(2) * exp(-|G|^2 / (2 E_cut)) on
   the sphere |G|^2/2 <= E_cut (E_cut = 10 Ha), zero outside, a, b ~ N(0, 1);
 * real Gamma-point orbitals enforce c(-G) = conj c(G) and a real c(0);
@@ -19,7 +20,7 @@ Gamma-point, plane-wave basis):
 * target vectors psi use the same recipe with seed + 500, normalised but not
   orthogonalised against Phi.
 
-Arrays are numpy, shape (count, n, n, n) = [orbital][z][y][x], FP64
+Arrays are numpy, shape (count, n_z, n_y, n_x) = [orbital][z][y][x], FP64
 (complex128, or float64 for real Gamma-point systems).
 """
 from __future__ import annotations
@@ -36,7 +37,9 @@ SHAPE_SEED_BATCHED = 1601074590
 
 @dataclasses.dataclass(frozen=True)
 class System:
-    """Shape of one periodic system (one cubic cell)."""
+    """Shape of one periodic system: a cubic cell of edge L on an n^3 grid, or
+    an orthorhombic cell `cell` = (L_x, L_y, L_z) on a `grid` = (n_x, n_y, n_z)
+    grid (then n and L are not used)."""
 
     n: int                 # grid points per edge
     L: float               # cell edge (bohr)
@@ -45,14 +48,32 @@ class System:
     real: bool = False     # real Gamma-point orbitals
     kernel: str = "bare"   # "bare" or "erfc"
     omega: float = 0.0     # screening parameter (bohr^-1) for "erfc"
+    grid: tuple | None = None   # (n_x, n_y, n_z) of a non-cubic grid
+    cell: tuple | None = None   # (L_x, L_y, L_z) of a non-cubic cell
+
+    @property
+    def nxyz(self) -> tuple:
+        return tuple(self.grid) if self.grid else (self.n,) * 3
+
+    @property
+    def lengths(self) -> tuple:
+        return tuple(self.cell) if self.cell else (self.L,) * 3
+
+    @property
+    def shape(self) -> tuple:
+        """Array shape of one vector: (n_z, n_y, n_x)."""
+        nx, ny, nz = self.nxyz
+        return (nz, ny, nx)
 
     @property
     def ng(self) -> int:
-        return self.n ** 3
+        nx, ny, nz = self.nxyz
+        return nx * ny * nz
 
     @property
     def volume(self) -> float:
-        return self.L ** 3
+        lx, ly, lz = self.lengths
+        return lx * ly * lz
 
     @property
     def dv(self) -> float:
@@ -100,18 +121,29 @@ def wavevector_sq(n: int, L: float) -> np.ndarray:
     return gx * gx + gy * gy + gz * gz
 
 
+def wavevector_sq3(shape, lengths) -> np.ndarray:
+    """|G|^2 on the wrapped index grid of shape (n_z, n_y, n_x), cell (L_x, L_y, L_z)."""
+    nz, ny, nx = shape
+    lx, ly, lz = lengths
+    gx = 2.0 * math.pi * np.fft.fftfreq(nx, d=1.0 / nx) / lx
+    gy = 2.0 * math.pi * np.fft.fftfreq(ny, d=1.0 / ny) / ly
+    gz = 2.0 * math.pi * np.fft.fftfreq(nz, d=1.0 / nz) / lz
+    z, y, x = np.meshgrid(gz, gy, gx, indexing="ij")
+    return x * x + y * y + z * z
+
+
 def _coefficients(rng, sysm: System, count: int, ecut: float) -> np.ndarray:
-    n = sysm.n
-    g2 = wavevector_sq(n, sysm.L)
+    shape = sysm.shape
+    g2 = wavevector_sq3(shape, sysm.lengths)
     sphere = 0.5 * g2 <= ecut
     decay = np.where(sphere, np.exp(-g2 / (2.0 * ecut)), 0.0)
-    a = rng.standard_normal((count, n, n, n))
-    b = rng.standard_normal((count, n, n, n))
+    a = rng.standard_normal((count,) + shape)
+    b = rng.standard_normal((count,) + shape)
     c = (a + 1j * b) / math.sqrt(2.0) * decay
     if sysm.real:
         # Hermitian symmetry c(-G) = conj c(G): average with the mirrored conjugate.
-        idx = (-np.arange(n)) % n
-        mirror = np.conj(c[:, idx][:, :, idx][:, :, :, idx])
+        iz, iy, ix = ((-np.arange(m)) % m for m in shape)
+        mirror = np.conj(c[:, iz][:, :, iy][:, :, :, ix])
         c = 0.5 * (c + mirror)
         c[:, 0, 0, 0] = c[:, 0, 0, 0].real
     return c
@@ -133,7 +165,7 @@ def orbitals(sysm: System, seed: int, ecut: float = ECUT_HA) -> np.ndarray:
     sgn = np.sign(np.real(np.diag(r)))
     sgn[sgn == 0] = 1.0
     q = q * sgn[None, :]
-    out = (q.T / math.sqrt(sysm.dv)).reshape(sysm.n_occ, sysm.n, sysm.n, sysm.n)
+    out = (q.T / math.sqrt(sysm.dv)).reshape((sysm.n_occ,) + sysm.shape)
     return np.ascontiguousarray(out)
 
 

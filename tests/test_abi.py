@@ -83,6 +83,15 @@ def test_validation_without_gpu(lib):
     assert lib.ace_supported_edge(7, 2) == 0 and lib.ace_supported_edge(50, 1) == 0
     assert lib.ace_supported_edge(64, 1) == 1 and lib.ace_supported_edge(96, 0) == 1
     assert lib.ace_workspace_size(None, 0, 4) == 0
+    grid = ctypes.c_int * 3
+    lib.ace_supported_grid.restype = ctypes.c_int
+    lib.ace_supported_grid.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+    for n3 in ((12, 16, 20), (48, 40, 36), (16, 16, 64), (96, 96, 8), (40, 48, 96)):
+        for dt in (0, 1, 2):
+            assert lib.ace_supported_grid(grid(*n3), dt) == 1, (n3, dt)
+    for n3 in ((12, 20, 16), (50, 50, 50), (48, 48, 50), (7, 7, 7)):
+        assert lib.ace_supported_grid(grid(*n3), 2) == 0, n3
+    assert lib.ace_plan_create(ctypes.byref(make(n=(12, 20, 16))), ctypes.byref(h)) == ACE_ERR_UNSUPPORTED
 
 
 def test_batched_and_autotune_validation_without_gpu(lib):

@@ -475,3 +475,37 @@ def test_si512_full_size(ace):
         pj = phi[j].cpu().numpy().astype(np.complex128)
         ref = -pi * oracle.poisson((np.conj(pi) * pj)[None], kern)[0]
         assert rel(_host(y)[0], ref) < 1e-6, (i, j)
+
+
+@pytest.mark.parametrize("dtype,graphs,overlap", [("c64", True, True), ("c64", True, False), ("c64", False, True),
+                                                  ("c128", True, True), ("r64", True, True)])
+def test_stored_pair_potentials(ace, dtype, graphs, overlap):
+    """ace_exchange_energy_grad with recompute = 0: the energy call keeps every
+    unique pair potential in the workspace, the gradient call only accumulates
+    (Eq. EX and its gradient 2 dV W); energies and gradients are bitwise those
+    of the recomputing sweep, on every schedule, and through the autograd
+    Function with and without the store."""
+    s, phi, psi, kern = _inputs(24, 10.0, 21, 1, dtype, "erfc", 0.3, seed=61)
+    plan = ace.Plan(24, 10.0, 21, dtype=dtype, kernel="erfc", omega=0.3, tile=4, max_pairs=16,
+                    graphs=graphs, overlap=overlap)
+    phi_d = _dev(phi, dtype, ace)
+    e1, g1 = plan.energy_grad(phi_d, grad=True, grad_scale=0.5)
+    e0, _ = plan.energy_grad(phi_d)
+    for _ in range(2):                                   # capture, then replay
+        e2, none = plan.energy_grad(phi_d, recompute=False)
+        e3, g3 = plan.energy_grad(phi_d, grad=True, grad_scale=0.5, recompute=False)
+        assert none is None and plan.status() == (0, 0)
+        assert e3.item() == e2.item()                    # the stored energy sums, reduced again
+        assert abs(e2.item() - e0.item()) <= 1e-13 * abs(e0.item())
+        assert abs(e1.item() - e0.item()) <= 1e-13 * abs(e0.item())
+        assert torch.equal(g3, g1)
+    assert rel(_host(g3), 0.5 * oracle.energy_grad(phi, kern, s.dv)) < TOL[dtype]["g"]
+    need = plan.workspace_size(ace.OP_ENERGY_GRAD_STORE)
+    assert need >= 21 * 22 // 2 * 24 ** 3 * (8 if dtype == "c64" else 16)
+    grads = []
+    for store in (True, False):
+        p = phi_d.clone().requires_grad_(True)
+        e = ace.exchange_energy(p, plan, store=store)
+        (3.0 * e).backward()
+        grads.append(p.grad)
+    assert torch.equal(grads[0], grads[1]) and torch.equal(grads[0], 6.0 * g1)

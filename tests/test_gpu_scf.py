@@ -88,3 +88,64 @@ def test_ace_scf_reaches_the_direct_fixed_point(ace):
     eps = a["eigenvalues"].to(hpsi.dtype)
     res = hpsi - eps[:, None, None, None] * psi
     assert float(torch.linalg.vector_norm(res) / torch.linalg.vector_norm(hpsi)) < 1e-6
+
+
+def _wells_at(n, L, centres, depth=3.0, width=0.8):
+    x = np.arange(n) * (L / n)
+    z, y, xx = np.meshgrid(x, x, x, indexing="ij")
+    v = np.zeros((n, n, n))
+    for c in centres:
+        dx = (xx - c[0] * L + L / 2) % L - L / 2
+        dy = (y - c[1] * L + L / 2) % L - L / 2
+        dz = (z - c[2] * L + L / 2) % L - L / 2
+        v -= depth * np.exp(-(dx * dx + dy * dy + dz * dz) / (2 * width * width))
+    return v
+
+
+@pytest.mark.parametrize("dtype", ["c128", "r64"])
+def test_ace_scf_matches_the_oracle_scf(ace, dtype):
+    """Alg. 2 on the GPU (ACE built once per outer iteration, V_ACE in every H
+    application of the Chebyshev-filtered inner loop) against the oracle's
+    self-consistent field of the same model Hamiltonian (Eq. HF, dense
+    diagonalisation, pinned on its own): the occupied eigenvalues and E_x agree."""
+    from paper_1601_07159_gb300 import scf
+    n, L, N = 8, 6.0, 4
+    v = _wells(n, L)
+    ref = oracle.model_scf(v, (L, L, L), N, real=(dtype == "r64"))
+    s = synth.System(n=n, L=L, n_occ=N, n_bands=N, real=(dtype == "r64"))
+    psi0 = torch.from_numpy(synth.orbitals(s, 11, ecut=2.0)).cuda()
+    m = scf.ModelHF(n, L, N, torch.from_numpy(v).cuda(), dtype=dtype)
+    r = m.scf(psi0, use_ace=True)
+    assert r["outer"] < 40
+    eps = r["eigenvalues"].cpu().numpy()
+    print(f"8^3 {dtype}: eigenvalues {eps} vs oracle {ref['eigenvalues']}, E_x {r['ex_history'][-1]} vs {ref['ex']}")
+    assert np.max(np.abs(eps - ref["eigenvalues"])) < 1e-8
+    assert abs(r["ex_history"][-1] - ref["ex"]) < 1e-8 * abs(ref["ex"])
+
+
+def test_ace_scf_fp32_against_fp64_at_48():
+    """The 48^3 cell (L = 20.5) with N = 16 electrons in 16 wells: the FP32 loop
+    (FP32 pair path, TF32-split M and apply, FP64-accurate Xi) reaches the FP64
+    loop's fixed point to FP32 accuracy."""
+    pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_07159_gb300 import build_lib, scf
+    build_lib.build()
+    n, L, N = 48, 20.5, 16
+    centres = [((i + 0.5) / 4, (j + 0.5) / 2, (k + 0.5) / 2) for i in range(4) for j in range(2) for k in range(2)]
+    v = torch.from_numpy(_wells_at(n, L, centres, depth=3.0, width=0.8)).cuda()
+    s = synth.System(n=n, L=L, n_occ=N, n_bands=N)
+    psi0 = torch.from_numpy(synth.orbitals(s, 17, ecut=2.0)).cuda()
+    res = {}
+    for dtype in ("c128", "c64"):
+        m = scf.ModelHF(n, L, N, v, dtype=dtype)
+        tol = 1e-10 if dtype == "c128" else 1e-6
+        res[dtype] = m.scf(psi0, use_ace=True, inner_tol=tol, outer_tol=tol)
+        assert res[dtype]["outer"] < 40, dtype
+    e64 = res["c128"]["eigenvalues"].cpu().numpy()
+    e32 = res["c64"]["eigenvalues"].cpu().numpy().astype(np.float64)
+    x64, x32 = res["c128"]["ex_history"][-1], res["c64"]["ex_history"][-1]
+    print(f"48^3 N=16: max eigenvalue diff {np.max(np.abs(e32 - e64)):.2e}, E_x {x32} vs {x64}")
+    assert np.max(np.abs(e32 - e64)) < 1e-5 * np.max(np.abs(e64))
+    assert abs(x32 - x64) < 1e-5 * abs(x64)

@@ -17,7 +17,7 @@ def test_batched_draw_recipe():
         assert s.n_bands == (3 * s.n_occ) // 2
         assert math.isclose(s.L / s.n, 20.5 / 48)                                # the 48^3 cell's spacing
         assert s.kernel == "bare"
-        assert s.n in build_lib.EDGES_F32
+        assert s.n in build_lib.shape_lists()["f32"][0]
     assert len({s.n for s in a}) == 5                                            # every edge drawn
     pairs = sum(s.n_occ * (s.n_occ + 1) // 2 for s in a)
     assert pairs == 207841                                                       # the unique pair solves of one batched build

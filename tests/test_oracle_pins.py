@@ -300,3 +300,73 @@ def test_kernel_tables_reflection_symmetric(shape, lengths):
     # and the folded indices cover every value: min(k, n - k) reaches each class once
     n = shape[0]
     assert sorted({min(i, n - i) for i in range(n)}) == list(range(n // 2 + 1))
+
+
+# ---------------------------------------------------------------- model SCF (Eq. HF, Alg. 1/2)
+def _wells(shape, lengths, depth=3.0, width=0.8):
+    nz, ny, nx = shape
+    lx, ly, lz = lengths
+    z, y, x = np.meshgrid(np.arange(nz) * lz / nz, np.arange(ny) * ly / ny, np.arange(nx) * lx / nx, indexing="ij")
+    v = np.zeros(shape)
+    for c in ((0.25, 0.25, 0.25), (0.75, 0.75, 0.25), (0.75, 0.25, 0.75), (0.25, 0.75, 0.75)):
+        dx = (x - c[0] * lx + lx / 2) % lx - lx / 2
+        dy = (y - c[1] * ly + ly / 2) % ly - ly / 2
+        dz = (z - c[2] * lz + lz / 2) % lz - lz / 2
+        v -= depth * np.exp(-(dx * dx + dy * dy + dz * dz) / (2 * width * width))
+    return v
+
+
+def test_model_scf_free_electron():
+    """No external potential, one electron: the ground state is the constant
+    orbital (G = 0, kinetic energy 0), and its Hartree and exchange potentials
+    cancel exactly (spinless HF is free of self-interaction), so the
+    eigenvalue is 0 and E_x = -E_H of the uniform density (0 with K(0) = 0)."""
+    shape, lengths = (6, 6, 6), (5.0, 5.0, 5.0)
+    r = oracle.model_scf(np.zeros(shape), lengths, 1, real=True)
+    assert abs(r["eigenvalues"][0]) < 1e-10
+    phi = r["psi"][0]
+    assert np.allclose(np.abs(phi), np.abs(phi).mean(), rtol=1e-8)
+    assert abs(r["ex"]) < 1e-10
+
+
+def test_model_scf_one_electron_is_the_bare_ground_state():
+    """One orbital in a potential well: V_H[|phi|^2] phi + V_X[phi] phi = 0
+    exactly, so the self-consistent orbital and eigenvalue are those of
+    T + V_loc alone (the lowest eigenpair, by inverse iteration here) and E_x
+    equals -1/2 <phi, V_H phi>."""
+    shape, lengths = (8, 8, 8), (6.0, 6.0, 6.0)
+    v = _wells(shape, lengths)
+    r = oracle.model_scf(v, lengths, 1, real=True)
+    ng = v.size
+    dv = np.prod(lengths) / ng
+    kin = oracle.kinetic_kernel(shape, lengths)
+    # lowest eigenpair of T + V_loc by inverse iteration with matrix-free solves (CG on H - sigma)
+    import scipy.sparse.linalg as sla
+    h = sla.LinearOperator((ng, ng), matvec=lambda x: np.real(oracle.poisson(x.reshape(shape), kin)).ravel()
+                           + v.ravel() * x, dtype=np.float64)
+    w0, u0 = sla.eigsh(h, k=1, which="SA", tol=1e-13)
+    assert abs(r["eigenvalues"][0] - w0[0]) < 1e-9
+    phi = r["psi"][0].ravel()
+    assert abs(abs(np.dot(phi, u0[:, 0])) * np.sqrt(dv) - 1.0) < 1e-9
+    bare = oracle.coulomb_kernel(shape, lengths, "bare")
+    vh = np.real(oracle.poisson((phi * phi).reshape(shape), bare)).ravel()
+    assert abs(r["ex"] + 0.5 * dv * np.sum(phi * vh * phi)) < 1e-10
+
+
+def test_model_scf_fixed_point_satisfies_hf_equations():
+    """At the returned fixed point the orbitals solve H[rho, phi] phi_i =
+    eps_i phi_i with H applied matrix-free through the pinned Poisson solve and
+    exchange apply (Eq. applyVX2), not the dense matrices the loop used; E_x
+    equals the direct pair sum (Eq. EX)."""
+    shape, lengths = (8, 8, 8), (6.0, 6.0, 6.0)
+    v = _wells(shape, lengths)
+    r = oracle.model_scf(v, lengths, 4)
+    phi = r["psi"]
+    kin = oracle.kinetic_kernel(shape, lengths)
+    bare = oracle.coulomb_kernel(shape, lengths, "bare")
+    rho = np.sum(np.abs(phi) ** 2, axis=0)
+    vh = np.real(oracle.poisson(rho, bare))
+    hphi = oracle.poisson(phi, kin) + (v + vh)[None] * phi + oracle.exchange_apply(phi, phi, kern=bare)
+    res = hphi - r["eigenvalues"][:, None, None, None] * phi
+    assert np.linalg.norm(res) < 1e-8 * np.linalg.norm(hphi)
+    assert abs(r["ex"] - oracle.energy_direct(phi, bare, np.prod(lengths))) < 1e-10 * abs(r["ex"])
