@@ -243,10 +243,22 @@ ace_status ace_build_batched(ace_plan* const* plans, const void* const* Phi, voi
  * pair schedule or two lanes without overlap -- on seeded pseudo-random
  * orbitals, `reps` timed builds each (0 = 3) after one untimed build, and
  * writes the fastest into *best (a copy of *d with tile, max_pairs, lanes and
- * flags set) and its milliseconds per build into *ms_out (nullable).
+ * flags set) and its milliseconds per build into *ms_out (nullable), and
+ * registers it for later plans of the same problem (ace_tuning_register).
  * Allocates its own device buffers (about 2 N N_g vectors plus the largest
  * workspace) and synchronises; call it outside timed or captured regions. */
 ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_out);
+
+/* Tuned schedules, process-wide: ace_autotune registers its result, and
+ * ace_tuning_register adds one found earlier (for instance from a saved
+ * tuning table); ace_plan_create then takes the registered max_pairs, tile,
+ * lanes and ACE_FLAG_NO_OVERLAP for a descriptor with the same grid, n_occ,
+ * dtype, prec and kernel whose max_pairs, tile and lanes are all 0.
+ * ace_tuning_clear forgets every registered schedule. ace_plan_desc writes the
+ * plan's effective descriptor (the schedule it runs, the resolved ld). */
+ace_status ace_tuning_register(const ace_desc* tuned);
+ace_status ace_tuning_clear(void);
+ace_status ace_plan_desc(const ace_plan* plan, ace_desc* out);
 
 /* Y = V_ACE Psi = -Xi (dV Xi^* Psi) (Eq. ACE). Xi: N vectors from ace_build,
  * Psi and Y: n_b vectors; Y must not alias Xi or Psi. No Poisson solves. */

@@ -111,6 +111,12 @@ _lib.ace_build_batched.restype = ctypes.c_int
 _lib.ace_autotune.argtypes = [ctypes.POINTER(Desc), ctypes.c_int, ctypes.POINTER(Desc),
                               ctypes.POINTER(ctypes.c_double)]
 _lib.ace_autotune.restype = ctypes.c_int
+_lib.ace_tuning_register.argtypes = [ctypes.POINTER(Desc)]
+_lib.ace_tuning_register.restype = ctypes.c_int
+_lib.ace_tuning_clear.argtypes = []
+_lib.ace_tuning_clear.restype = ctypes.c_int
+_lib.ace_plan_desc.argtypes = [_vp, ctypes.POINTER(Desc)]
+_lib.ace_plan_desc.restype = ctypes.c_int
 _lib.ace_debug_engine_wait.argtypes = [_vp, ctypes.c_uint, ctypes.c_int]
 _lib.ace_debug_engine_wait.restype = ctypes.c_int
 _lib.ace_debug_xi_product.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp]
@@ -352,6 +358,13 @@ class Plan:
         return {"pass_ms": {"A": ms[0], "B": ms[1], "C": ms[2], "D": ms[3]}, "pair_ms": ms[4],
                 "batches": cnt[0], "launches": cnt[1], "dropped": cnt[2]}
 
+    def effective_schedule(self) -> dict:
+        """The schedule the plan runs (after any registered tuned schedule)."""
+        d = Desc()
+        _check(_lib.ace_plan_desc(self._h, ctypes.byref(d)))
+        return {"tile": d.tile, "max_pairs": d.max_pairs, "lanes": d.lanes, "overlap": not (d.flags & 16),
+                "ld": d.ld}
+
     def debug_engine_wait(self, polls: int = 0, unreachable: bool = False):
         """ace_debug_engine_wait: bound (or make unreachable) the engine's waits."""
         _check(_lib.ace_debug_engine_wait(self._h, polls, 1 if unreachable else 0))
@@ -405,9 +418,26 @@ def autotune(n: int, L, n_occ: int, dtype: str = "c64", kernel: str = "bare", om
             "overlap": not (best.flags & 16), "ms": ms.value}
 
 
+def tuning_register(n, L, n_occ: int, dtype: str, kernel: str, tile: int, max_pairs: int, lanes: int,
+                    overlap: bool, omega: float = 0.0, prec: str = "default"):
+    """ace_tuning_register: later plans of this problem with default schedule
+    knobs run this schedule."""
+    d = _desc(n, L, n_occ, dtype, kernel, omega, None, 1.0)
+    d.prec = PRECS[prec]
+    d.tile, d.max_pairs, d.lanes = tile, max_pairs, lanes
+    d.flags = 0 if overlap else 16
+    _check(_lib.ace_tuning_register(ctypes.byref(d)))
+
+
+def tuning_clear():
+    _check(_lib.ace_tuning_clear())
+
+
 class TuningTable:
     """Autotuner results keyed by problem shape (n, N, dtype, kernel), kept in
-    a JSON file so that a shape is timed once per machine."""
+    a JSON file so that a shape is timed once per machine. Loading a table
+    registers its entries with the library, so plans created with the default
+    schedule knobs run the tuned schedules."""
 
     def __init__(self, path: str | None = None):
         self.path = path
@@ -416,10 +446,15 @@ class TuningTable:
             import json
             with open(path) as f:
                 self.table = json.load(f)
+            for k, t in self.table.items():
+                n, n_occ, dtype, kernel = k.split("|")
+                tuning_register(tuple(int(v) for v in n.split("x")), 1.0, int(n_occ), dtype, kernel,
+                                t["tile"], t["max_pairs"], t["lanes"], t["overlap"])
 
     @staticmethod
     def key(n, n_occ, dtype, kernel) -> str:
-        return f"{n}|{n_occ}|{dtype}|{kernel}"
+        """'n_x x n_y x n_z|N|dtype|kernel', e.g. '48x48x48|128|c64|erfc'."""
+        return "x".join(str(v) for v in _grid(n)) + f"|{n_occ}|{dtype}|{kernel}"
 
     def schedule(self, n, L, n_occ, dtype="c64", kernel="bare", omega=0.0, g0=None, alpha=1.0) -> dict:
         k = self.key(n, n_occ, dtype, kernel)

@@ -656,6 +656,28 @@ long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* X
   return 1 + kr + (p->tc ? 2 : 0) + kc + kx;
 }
 
+// Tuned schedules (ace_autotune, ace_tuning_register), process-wide, keyed by
+// the problem shape; ace_plan_create takes the registered schedule when the
+// descriptor leaves max_pairs, tile and lanes at 0.
+std::mutex g_tune_mu;
+std::vector<ace_desc> g_tuned;
+constexpr int kScheduleFlags = ACE_FLAG_NO_OVERLAP;
+
+bool same_problem(const ace_desc& a, const ace_desc& b) {
+  return a.n[0] == b.n[0] && a.n[1] == b.n[1] && a.n[2] == b.n[2] && a.n_occ == b.n_occ && a.dtype == b.dtype &&
+         a.prec == b.prec && a.kernel == b.kernel;
+}
+
+void register_tuned(const ace_desc& t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& e : g_tuned)
+    if (same_problem(e, t)) {
+      e = t;
+      return;
+    }
+  g_tuned.push_back(t);
+}
+
 // One captured graph per batch of systems (ace_build_batched), shared by all
 // plans of the process and keyed by every pointer the graph bakes in.
 struct BatchGraph {
@@ -748,6 +770,19 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   if (d->max_pairs < 0) return fail(ACE_ERR_ARG, "max_pairs must be >= 0");
   if (d->lanes < 0 || d->lanes > kMaxLanes) return fail(ACE_ERR_ARG, "lanes must be 0..8");
 
+  ace_desc dd = *d;
+  if (dd.max_pairs == 0 && dd.tile == 0 && dd.lanes == 0) {   // a registered tuned schedule, if any
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (const auto& t : g_tuned)
+      if (same_problem(t, dd)) {
+        dd.max_pairs = t.max_pairs;
+        dd.tile = t.tile;
+        dd.lanes = t.lanes;
+        dd.flags = (dd.flags & ~kScheduleFlags) | (t.flags & kScheduleFlags);
+        break;
+      }
+  }
+  d = &dd;
   ace_plan* p = new ace_plan();
   p->d = *d;
   cudaGetDevice(&p->device);
@@ -1284,6 +1319,31 @@ ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_
   if (s != ACE_OK) return s;
   if (best_ms < 0) return fail(ACE_ERR_CUDA, "autotune: no candidate could be timed");
   if (ms_out) *ms_out = best_ms;
+  register_tuned(*best);
+  return ACE_OK;
+}
+
+ace_status ace_tuning_register(const ace_desc* tuned) {
+  if (!tuned) return fail(ACE_ERR_ARG, "tuned is NULL");
+  if (tuned->tile < 1 || tuned->tile > kTileMax || tuned->max_pairs < 1 || tuned->lanes < 0 || tuned->lanes > kMaxLanes)
+    return fail(ACE_ERR_ARG, "a tuned schedule needs tile 1..8, max_pairs >= 1 and lanes 0..8");
+  register_tuned(*tuned);
+  return ACE_OK;
+}
+
+ace_status ace_tuning_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned.clear();
+  return ACE_OK;
+}
+
+ace_status ace_plan_desc(const ace_plan* p, ace_desc* out) {
+  if (!p || !out) return fail(ACE_ERR_ARG, "plan and out are required");
+  *out = p->d;
+  out->max_pairs = p->max_pairs;
+  out->tile = p->tile;
+  out->lanes = p->lanes;
+  out->ld = p->ld;
   return ACE_OK;
 }
 

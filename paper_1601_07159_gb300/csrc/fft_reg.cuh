@@ -58,6 +58,23 @@ __device__ __forceinline__ cplx<R> twiddle(cplx<R> x, int e, const TwTable<R, NT
              : cmul(x, w);
 }
 
+// The twiddle w_N^e (forward sign) or its conjugate as a value: exact for the
+// quarter turns, from the table otherwise. With e a compile-time constant after
+// unrolling this is a pair of constants.
+template <int N, int NTOP, bool INV, typename R>
+__device__ __forceinline__ cplx<R> twiddle_value(int e, const TwTable<R, NTOP>& tw) {
+  e %= N;
+  if (e == 0) return cmk<cplx<R>>(R(1), R(0));
+  if ((4 * e) % N == 0) {
+    const int q = (4 * e) / N;   // forward: -i, -1, +i
+    if (q == 2) return cmk<cplx<R>>(R(-1), R(0));
+    const R s = (q == 1) != INV ? R(-1) : R(1);
+    return cmk<cplx<R>>(R(0), s);
+  }
+  const cplx<R> w = tw.w[e * (NTOP / N)];
+  return INV ? cmk<cplx<R>>(w.x, -w.y) : w;
+}
+
 template <int N> __host__ __device__ constexpr int first_radix() {
   return (N % 4 == 0 && N != 4) ? 4 : (N % 2 == 0 ? 2 : (N % 3 == 0 ? 3 : (N % 5 == 0 ? 5 : N)));
 }

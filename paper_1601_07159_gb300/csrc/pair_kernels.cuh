@@ -8,7 +8,9 @@
 //   pass A  (per z-plane)   rho = conj(x_l) y_r; FFT along y (thread = column x,
 //                           coalesced loads), transpose through shared memory,
 //                           FFT along x (thread = row ky); store S[z][kx][ky]
-//                           (coalesced along ky).
+//                           (coalesced along ky). Blocks run z-plane major, so
+//                           the pairs of a tile that read the same orbital
+//                           plane run together and find it in L2.
 //   pass B  (per pencil)    FFT along z, multiply by K(G)/N_g, inverse FFT along
 //                           z, in place (thread = (kx, ky) pencil, coalesced);
 //                           optionally the Parseval energy sum K |rho_hat|^2.
@@ -48,6 +50,7 @@
 #pragma once
 #include "ace_internal.h"
 #include "fft_reg.cuh"
+
 
 namespace ace {
 
@@ -225,9 +228,9 @@ __device__ __forceinline__ void body_a(const PlaneParams<R, NX, NY>& P, const Ti
   const long long item = vb * IPB + ty;
   const bool active = ty < IPB && item < (long long)npairs * P.nz;
   int p = 0, z = 0, l = 0, r = 0;
-  if (active) {
-    p = (int)(item / P.nz);
-    z = (int)(item % P.nz);
+  if (active) {   // z-plane major: the pairs of a tile that share an orbital plane run together
+    z = (int)(item / npairs);
+    p = (int)(item % npairs);
     decode_pair(tiles, ntiles, p, l, r);
   }
   if (active && tx < NX) {
@@ -564,6 +567,34 @@ template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
   return r;
 }
 
+// A length-N transform of a line held by two lanes (lanes 2q, 2q+1): lane h
+// holds the samples 2m + h in a[], and on return holds y[j] = Y[hN/4 + j] and
+// y[N/4 + j] = Y[hN/4 + j + N/2] (the forward or inverse DFT, unnormalised):
+// a DFT of N/2 per lane, the lane-1 twiddles w^{+-k}, one shuffle per value
+// and the radix-2 combine (decimation in time).
+// The halves are exchanged before the twiddles, so each lane multiplies only
+// the H odd-half values of its own outputs (by w^j on lane 0, w^{H+j} on lane
+// 1: two compile-time constants, selected).
+template <typename R> __device__ __forceinline__ cplx<R> csel(bool c, cplx<R> a, cplx<R> b) {
+  return cmk<cplx<R>>(c ? a.x : b.x, c ? a.y : b.y);
+}
+template <int N, bool INV, typename R>
+__device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)[N / 2], int h,
+                                               const TwTable<R, N>& tw) {
+  using C = cplx<R>;
+  constexpr int M = N / 2, H = N / 4;
+  dft<M, N, INV, R>(a, tw);                                // E (lane 0) or O (lane 1)
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    const C recv = shfl_pair(h ? a[j] : a[H + j]);       // lane 0 gets O[j], lane 1 gets E[H + j]
+    const C ev = h ? recv : a[j];                        // E[hH + j]
+    const C od = h ? a[H + j] : recv;                    // O[hH + j]
+    const C w = csel<R>(h, twiddle_value<N, N, INV, R>(H + j, tw), twiddle_value<N, N, INV, R>(j, tw));
+    const C t = cmul(od, w);
+    y[j] = cadd(ev, t);
+    y[H + j] = csub(ev, t);
+  }
+}
 // Pass B for the large pencils (n_z >= 64), whose whole pencil per thread
 // spills: two lanes per z-pencil (lanes 2q, 2q+1 of a warp; 128 pencils per
 // block). Lane h holds the samples z = 2m + h and transforms them with a DFT of
@@ -580,7 +611,10 @@ template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
 // the shuffles cost more than the occupancy gains, so shorter pencils keep one
 // thread per pencil.
 constexpr int kBSplitPencils = 128;   // pencils per 256-thread block of the split pass B
-// FP64 pencils of 64+ points need the whole register file of a thread: one block per SM.
+// FP64 pencils of 64+ points need the whole register file of a thread: one
+// block per SM. FP32 pencils of 96 points spill a few hundred bytes at two
+// blocks per SM, which measured faster than one block without spills
+// (25.7 vs 31.7 ms of pass B per 96^3 build of 128 orbitals).
 template <typename R, int N> constexpr int kBSplitBlocks = sizeof(R) == 8 ? 1 : 2;
 template <int NZ> constexpr bool kSplitPencil = NZ >= 64 && NZ % 4 == 0;
 
@@ -605,21 +639,8 @@ pass_b_split_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
   C a[M];
 #pragma unroll
   for (int m = 0; m < M; ++m) a[m] = active ? s[(long long)(2 * m + h) * nxy] : zero;
-  dft<M, N, false, R>(a, P.tw);                            // E (lane 0) or O (lane 1)
-#pragma unroll
-  for (int k = 0; k < M; ++k) {                            // lane 1: w^k O[k]
-    const C t = twiddle<N, N, false, R>(a[k], k, P.tw);
-    a[k] = h ? t : a[k];
-  }
   C y[M];                                                  // y[j] = Y[hH + j], y[H + j] = Y[hH + j + M]
-#pragma unroll
-  for (int j = 0; j < H; ++j) {
-    const C recv = shfl_pair(h ? a[j] : a[H + j]);
-    const C ev = h ? recv : a[j];
-    const C od = h ? a[H + j] : recv;
-    y[j] = cadd(ev, od);
-    y[H + j] = csub(ev, od);
-  }
+  split_line_dft<N, false, R>(a, y, h, P.tw);
   R acc = R(0);
   const R* kt = P.Kt + G.kt_pencil(f);
 #pragma unroll
@@ -639,7 +660,8 @@ pass_b_split_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
 #pragma unroll
     for (int j = 0; j < H; ++j) {                          // k = hH + j
       const C sum = cadd(y[j], y[H + j]);
-      const C dif = twiddle<N, N, true, R>(csub(y[j], y[H + j]), h * H + j, P.tw);
+      const C w = csel<R>(h, twiddle_value<N, N, true, R>(H + j, P.tw), twiddle_value<N, N, true, R>(j, P.tw));
+      const C dif = cmul(csub(y[j], y[H + j]), w);
       const C recv = shfl_pair(h ? sum : dif);
       a[j] = h ? recv : sum;                               // lane 0: the sums, lane 1: the differences
       a[H + j] = h ? dif : recv;
@@ -663,31 +685,6 @@ pass_b_split_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
   }
 }
 
-// A length-N transform of a line held by two lanes (lanes 2q, 2q+1): lane h
-// holds the samples 2m + h in a[], and on return holds y[j] = Y[hN/4 + j] and
-// y[N/4 + j] = Y[hN/4 + j + N/2] (the forward or inverse DFT, unnormalised):
-// a DFT of N/2 per lane, the lane-1 twiddles w^{+-k}, one shuffle per value
-// and the radix-2 combine (decimation in time).
-template <int N, bool INV, typename R>
-__device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)[N / 2], int h,
-                                               const TwTable<R, N>& tw) {
-  using C = cplx<R>;
-  constexpr int M = N / 2, H = N / 4;
-  dft<M, N, INV, R>(a, tw);
-#pragma unroll
-  for (int k = 0; k < M; ++k) {
-    const C t = twiddle<N, N, INV, R>(a[k], k, tw);
-    a[k] = h ? t : a[k];
-  }
-#pragma unroll
-  for (int j = 0; j < H; ++j) {
-    const C recv = shfl_pair(h ? a[j] : a[H + j]);
-    const C ev = h ? recv : a[j];
-    const C od = h ? a[H + j] : recv;
-    y[j] = cadd(ev, od);
-    y[H + j] = csub(ev, od);
-  }
-}
 // Planes whose passes use the two-lane line transforms (one plane per block),
 // and the blocks per SM their launch bounds ask for: at 48^3 the half-length
 // lines need 72-95 registers, so six 96-thread blocks (18-27 warps) fit an SM
@@ -727,8 +724,8 @@ pass_a_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   C* buf = reinterpret_cast<C*>(smem_raw);
   griddep_launch();
   const int tid = threadIdx.x, q = tid >> 1, h = tid & 1;
-  const long long item = blockIdx.x;                      // one (pair, z) plane per block
-  const int p = (int)(item / P.nz), z = (int)(item % P.nz);
+  const long long item = blockIdx.x;                      // one (pair, z) plane per block, z-major:
+  const int z = (int)(item / P.npairs), p = (int)(item % P.npairs);   // pairs sharing a plane run together
   int l, r;
   decode_pair(P.tiles, P.ntiles, p, l, r);
   const C zero = cmk<C>(R(0), R(0));

@@ -146,3 +146,16 @@ def test_autotune_and_tuning_table(ace, tmp_path):
     ref = oracle.ace_build(phi, kern, s.dv)
     assert rel(_host(out["W"]), ref["W"]) < 1e-6
     assert rel(_host(out["Xi"]), ref["Xi"]) < 1e-5
+    # plan creation consults the registered tuned schedule (the last ace_autotune,
+    # the one behind the table's entry, registered it)
+    t2 = tab2.table[ace.TuningTable.key(n, N, "c64", "bare")]
+    default = ace.Plan(n, L, N, "c64", "bare").effective_schedule()
+    assert (default["tile"], default["max_pairs"], default["overlap"]) == (t2["tile"], t2["max_pairs"], t2["overlap"])
+    assert ace.TuningTable.key((n, n, n), N, "c64", "bare") == ace.TuningTable.key(n, N, "c64", "bare")
+    ace.tuning_clear()
+    ace.tuning_register(n, L, N, "c64", "bare", tile=4, max_pairs=48, lanes=3, overlap=False)
+    e = ace.Plan(n, L, N, "c64", "bare").effective_schedule()
+    assert (e["tile"], e["max_pairs"], e["lanes"], e["overlap"]) == (4, 48, 3, False)
+    assert ace.Plan(n, L, N, "c64", "bare", tile=8).effective_schedule()["tile"] == 8   # explicit knobs win
+    ace.tuning_clear()
+    assert ace.Plan(n, L, N, "c64", "bare").effective_schedule()["tile"] == 8
