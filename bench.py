@@ -568,6 +568,7 @@ def run_single(args):
         del xi_d, y_d, plan
         torch.cuda.empty_cache()
         line["xi_variants"] = xi_variants(ace, s, phi_d, reps=1, warm=s.n < 96)
+        line["gemm_variants"] = gemm_variants(ace, s, phi_d, psi_d, reps=1, warm=s.n < 96)
     del phi_d, psi_d
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_extras:
@@ -615,6 +616,45 @@ def xi_variants(ace, s, phi_d, reps, warm=True):
     return out
 
 
+def gemm_variants(ace, s, phi_d, psi_d, reps, warm=True):
+    """The dense products (M = dV Phi^* W, the apply) with the TF32 split (the
+    default) and the BF16 split (ACE_PREC_SPLIT_BF16): ms per ace_build and per
+    ace_apply with each, and the BF16 results' relative difference to the TF32
+    ones (M, V_ACE psi)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    out, res = {}, {}
+    for key, prec in (("tf32_split", "default"), ("bf16_split", "split_bf16")):
+        plan = ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega, prec=prec)
+        xi = plan.empty(s.n_occ)
+        y = plan.empty(s.n_bands)
+        if warm:
+            plan.build(phi_d, want_w=False, want_m=False, xi=xi)
+            plan.apply(xi, psi_d, out=y)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tb = ta = 0.0
+        for _ in range(reps):
+            ev[0].record(stream)
+            o = plan.build(phi_d, want_w=False, want_m=True, xi=xi)
+            ev[1].record(stream)
+            plan.apply(xi, psi_d, out=y)
+            ev[2].record(stream)
+            torch.cuda.synchronize()
+            tb += ev[0].elapsed_time(ev[1])
+            ta += ev[1].elapsed_time(ev[2])
+        out[key] = {"prec": prec, "ms_per_build": tb / reps, "ms_per_apply": ta / reps, "status": plan.status()[0]}
+        res[key] = (o["M"], y)
+        del plan, xi
+    for i, name in enumerate(("m", "apply")):
+        a, b = res["bf16_split"][i], res["tf32_split"][i]
+        out["bf16_split"][f"{name}_rel_diff_vs_tf32"] = float(torch.linalg.vector_norm(a - b) /
+                                                              torch.linalg.vector_norm(b))
+    del res
+    torch.cuda.empty_cache()
+    return out
+
+
 def si64_extra(ace, args, K=20):
     """The 48^3 workload: K timed steps, its pair-pipeline roofline, and the
     plain-FP64, cuFFT, entry-point and oversampled comparisons."""
@@ -644,6 +684,7 @@ def si64_extra(ace, args, K=20):
         return a.elapsed_time(b) / reps
 
     out["xi_variants"] = xi_variants(ace, s, phi_d, reps=3)
+    out["gemm_variants"] = gemm_variants(ace, s, phi_d, psi_d, reps=3)
     if not args.no_fp64:
         # plain-FP64 form of the same build: the denominator of the mixed-vs-FP64 ratio
         plan64 = ace.Plan(s.n, s.L, s.n_occ, dtype="c128", kernel=s.kernel, omega=s.omega)
@@ -681,13 +722,14 @@ def si64_extra(ace, args, K=20):
     return out
 
 
-def batched_systems_inputs(ace, args):
+def batched_systems_inputs(ace, args, engine=None):
     import torch
     systems = synth.batched_systems()[:args.systems]
+    engine = args.engine if engine is None else engine
     plans, phis_h, phis = [], [], []
     for i, s in enumerate(systems):
         plans.append(ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel="bare", max_pairs=args.max_pairs,
-                              tile=args.tile, overlap=not args.no_overlap))
+                              tile=args.tile, overlap=not args.no_overlap, engine=engine))
         d = synth.orbitals_device(s, synth.seed_for(3, i))
         phis.append(d)
         phis_h.append(d.cpu().pin_memory())
@@ -698,11 +740,11 @@ def batched_model_bytes(systems):
     return sum(pair_model_bytes(s) for s in systems)
 
 
-def batched_extra(ace, args, K=3):
-    """One batched step of the 64 uneven systems: ms per batch and its
-    roofline against the summed pair model."""
+def time_batch(ace, args, K, engine):
+    """ms per ace_build_batched step of the uneven systems (plans with or
+    without the persistent pair engine)."""
     import torch
-    systems, plans, _, phis = batched_systems_inputs(ace, args)
+    systems, plans, _, phis = batched_systems_inputs(ace, args, engine=engine)
     batch = ace.Batch(plans, chains=args.chains)
     xis = [p.empty(p.n_occ) for p in plans]
     for _ in range(3):
@@ -719,7 +761,16 @@ def batched_extra(ace, args, K=3):
         batch.build(phis, xis)
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b) / K
+    del batch, plans, phis, xis
+    return systems, a.elapsed_time(b) / K
+
+
+def batched_extra(ace, args, K=3):
+    """One batched step of the 64 uneven systems: ms per batch and its
+    roofline against the summed pair model; the same batch with every system's
+    pair solves as one persistent engine launch, for comparison."""
+    systems, ms = time_batch(ace, args, K, engine=args.engine)
+    _, ms_engine = time_batch(ace, args, K, engine=not args.engine)
     pairs = sum(unique_pairs(s.n_occ) for s in systems)
     hbm, peak_kind = peaks()
     alg = batched_model_bytes(systems)
@@ -729,8 +780,8 @@ def batched_extra(ace, args, K=3):
            "roofline": {"kernel": "whole batched build (pairs, GEMMs, Cholesky) vs the pair model",
                         "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                         "frac": achieved / hbm, "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
-                        "traffic": None}}
-    del batch, plans, phis, xis
+                        "traffic": None},
+           ("four_kernel_ms_per_build_batch" if args.engine else "engine_ms_per_build_batch"): ms_engine}
     return out
 
 
@@ -822,7 +873,10 @@ def run_batched(args):
                            "edges": sorted({s.n for s in systems}),
                            "n_occ_range": [min(s.n_occ for s in systems), max(s.n_occ for s in systems)],
                            "unique_pairs": pairs, "kernel": "bare",
-                           "precision": "fp32 pair/FFT path, TF32 3-term-split GEMMs, fp64 Cholesky and L^-1",
+                           "precision": "fp32 pair/FFT path, TF32 3-term-split M, fp64 Cholesky and L^-1, "
+                                        "Xi = W L^-* to fp64 accuracy (fp16 tensor-core slices)",
+                           "pair_solves": "persistent engine per system" if args.engine else
+                                          "four kernels per batch, captured graph",
                            "chains": args.chains or 3, "l2": "working set > L2 every step (no flush needed)"},
                 "ms_per_build_batch": elapsed_ms / K,
                 "roofline": {"kernel": "whole batched build (pairs, GEMMs, Cholesky) vs the pair model",

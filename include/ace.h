@@ -84,13 +84,20 @@ typedef enum {
  *    once to FP32: before that rounding the error of Xi_b(g) is below about
  *    2^-41 max_k |W_k(g)| sum_k |(L^{-*})_kb|.
  *  ACE_PREC_XI_FP64_SIMT: the same Xi with plain FP64 arithmetic on CUDA cores.
- *  ACE_PREC_FP32: all three products in FP32 on CUDA cores. */
+ *  ACE_PREC_FP32: all three products in FP32 on CUDA cores.
+ *  ACE_PREC_SPLIT_BF16: M = dV Phi^* W and the apply's two products on tcgen05
+ *    BF16 tensor cores, each FP32 operand split into two BF16 terms (hi = the
+ *    operand rounded to BF16, lo = the remainder rounded to BF16), three
+ *    products accumulated in FP32: about 16 significant bits per operand, so
+ *    these products carry relative errors near 2^-16 per term (the diagonal of
+ *    M, and so E_x, is still summed from FP32 products); Xi as ACE_PREC_XI_FP64. */
 typedef enum {
   ACE_PREC_DEFAULT = 0,
   ACE_PREC_SPLIT_TF32 = 1,
   ACE_PREC_FP32 = 2,
   ACE_PREC_XI_FP64 = 3,
-  ACE_PREC_XI_FP64_SIMT = 4
+  ACE_PREC_XI_FP64_SIMT = 4,
+  ACE_PREC_SPLIT_BF16 = 5
 } ace_prec;
 
 typedef struct {
@@ -109,8 +116,10 @@ typedef struct {
                         plan's calls take (Phi, Psi, W, Xi, Y, gradients, densities):
                         0 = N_g (packed), else >= N_g and even; elements between N_g
                         and ld are neither read nor written */
-  int max_pairs;     /* pair solves in flight per batch (0 = library default); sets the
-                        size of the pair-spectrum scratch in the workspace */
+  int max_pairs;     /* complex solves (scratch slots of N_g points) in flight per batch
+                        (0 = library default); sets the size of the pair-spectrum
+                        scratch in the workspace. A slot holds one pair for complex
+                        vectors, two for ACE_DTYPE_R64 (real and imaginary parts) */
   int tile;          /* orbitals per pair tile, 1..8 (0 = default 8) */
   int lanes;         /* concurrent batch streams inside one call with
                         ACE_FLAG_NO_OVERLAP, 1..8 (0 = default 2; at least 2

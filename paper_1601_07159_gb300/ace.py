@@ -37,7 +37,7 @@ OP_EXCHANGE_APPLY, OP_BUILD, OP_APPLY, OP_ENERGY_GRAD, OP_BUILD_OVERSAMPLED, OP_
 OP_ENERGY_GRAD_STORE = 6
 
 
-PRECS = {"default": 0, "split_tf32": 1, "fp32": 2, "xi_fp64": 3, "xi_fp64_simt": 4}
+PRECS = {"default": 0, "split_tf32": 1, "fp32": 2, "xi_fp64": 3, "xi_fp64_simt": 4, "split_bf16": 5}
 
 
 class Desc(ctypes.Structure):

@@ -102,6 +102,7 @@ struct ace_plan {
   bool graphs = true;
   bool engine = true;            // persistent pair engine (else four kernels per batch)
   bool tc = false;               // tensor-core GEMMs (complex FP32 storage)
+  bool bf16 = false;             // M and the apply with BF16 operands (ACE_PREC_SPLIT_BF16)
   bool overlap = false;          // graph mode: pass A of batch k+1 overlaps pass D of batch k
   unsigned eng_polls = kEngineSpinDefault;   // engine wait limit (ace_debug_engine_wait)
   unsigned eng_bias = 0;
@@ -177,7 +178,7 @@ cudaError_t upload(const ace_plan* p, Schedule& sc) {
 
 // Tournament ("circle") schedule over orbital blocks: every round pairs each
 // block with exactly one other, so the tiles of a round write disjoint outputs.
-Schedule make_sym_schedule(int N, int b, int max_pairs) {
+Schedule make_sym_schedule(int N, int b, int max_pairs, bool real) {
   const int B = (N + b - 1) / b;
   auto blk = [&](int I, int& o0, int& no) { o0 = I * b; no = (I * b + b <= N) ? b : N - I * b; };
   std::vector<std::vector<TileDesc>> rounds;
@@ -216,7 +217,7 @@ Schedule make_sym_schedule(int N, int b, int max_pairs) {
   for (auto& r : rounds) {
     Batch cur{};
     for (auto& t : r) {
-      const int np = tile_pairs(t);
+      const int np = tile_slots(t, real);
       if (cur.ntiles > 0 && (cur.npairs + np > max_pairs || cur.ntiles == kMaxTiles)) {
         out.batches.push_back(cur);
         out.round.push_back(rid);
@@ -235,14 +236,21 @@ Schedule make_sym_schedule(int N, int b, int max_pairs) {
   return out;
 }
 
-// One-sided schedule for V_X[Phi] Psi: r-blocks of Psi (<= b), l-chunks of Phi;
-// a round holds the tiles of one l-chunk, which write distinct Psi blocks.
-Schedule make_rect_schedule(int N, int nb, int b, int max_pairs) {
-  Schedule out;
-  const int nrb = (nb + b - 1) / b;
-  int lc = max_pairs / b;
+// Orbitals of Phi per l-chunk of a one-sided schedule: as many as fill a batch
+// of max_pairs slots with r-blocks of b (b / 2 slots per orbital for real vectors).
+int rect_chunk(int N, int b, int max_pairs, bool real) {
+  int lc = max_pairs / (real ? (b + 1) / 2 : b);
   if (lc < 1) lc = 1;
   if (lc > N) lc = N;
+  return lc;
+}
+
+// One-sided schedule for V_X[Phi] Psi: r-blocks of Psi (<= b), l-chunks of Phi;
+// a round holds the tiles of one l-chunk, which write distinct Psi blocks.
+Schedule make_rect_schedule(int N, int nb, int b, int max_pairs, bool real) {
+  Schedule out;
+  const int nrb = (nb + b - 1) / b;
+  const int lc = rect_chunk(N, b, max_pairs, real);
   int rid = 0;
   for (int l0 = 0; l0 < N; l0 += lc, ++rid) {
     const int nl = (l0 + lc <= N) ? lc : N - l0;
@@ -254,7 +262,7 @@ Schedule make_rect_schedule(int N, int nb, int b, int max_pairs) {
       t.r0 = R * b;
       t.nr = (R * b + b <= nb) ? b : nb - R * b;
       t.kind = 2;
-      const int np = tile_pairs(t);
+      const int np = tile_slots(t, real);
       if (cur.ntiles > 0 && (cur.npairs + np > max_pairs || cur.ntiles == kMaxTiles)) {
         out.batches.push_back(cur);
         out.round.push_back(rid);
@@ -294,9 +302,7 @@ int gram_parts(const ace_plan* p, int na, int nb) {
 // Upper bound on the batches of the one-sided schedule for n_b vectors.
 long long rect_batch_bound(const ace_plan* p, int nb) {
   const int N = p->d.n_occ, b = p->tile;
-  int lc = p->max_pairs / b;
-  if (lc < 1) lc = 1;
-  if (lc > N) lc = N;
+  const int lc = rect_chunk(N, b, p->max_pairs, p->real);
   return (long long)((N + lc - 1) / lc) * ((nb + b - 1) / b);
 }
 
@@ -581,7 +587,7 @@ PairLaunch base_launch(const ace_plan* p) {
 const Schedule* rect_schedule(ace_plan* p, int nb) {
   for (auto& c : p->rect)
     if (c.first == nb) return &c.second;
-  p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs));
+  p->rect.emplace_back(nb, make_rect_schedule(p->d.n_occ, nb, p->tile, p->max_pairs, p->real));
   if (upload(p, p->rect.back().second) != cudaSuccess) {
     free_schedule(p->rect.back().second);
     p->rect.pop_back();
@@ -594,7 +600,7 @@ const Schedule* rect_schedule(ace_plan* p, int nb) {
 const Schedule* poisson_schedule(ace_plan* p, int nb) {
   for (auto& c : p->pois)
     if (c.first == nb) return &c.second;
-  p->pois.emplace_back(nb, make_rect_schedule(1, nb, p->tile, p->max_pairs));
+  p->pois.emplace_back(nb, make_rect_schedule(1, nb, p->tile, p->max_pairs, p->real));
   if (upload(p, p->pois.back().second) != cudaSuccess) {
     free_schedule(p->pois.back().second);
     p->pois.pop_back();
@@ -647,7 +653,7 @@ long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* X
                             cudaStream_t cs) {
   const int N = p->d.n_occ;
   const int splits = gram_parts(p, N, N);
-  if (p->tc) launch_gram_tc(Phi, N, W, N, p->ld, p->ng, Wl.part, splits, p->status, cs);
+  if (p->tc) launch_gram_tc(Phi, N, W, N, p->ld, p->ng, Wl.part, splits, p->status, cs, p->bf16);
   else launch_gram(p->f64, p->real, Phi, N, W, N, p->ld, p->ng, Wl.part, splits, cs);
   const int kr = launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
   if (p->tc) launch_diag_exact(Phi, W, N, p->ld, p->ng, p->dv, Wl.part, p->Mc, cs);
@@ -761,7 +767,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   const long long ng_ = (long long)d->n[0] * d->n[1] * d->n[2];
   if (d->ld != 0 && (d->ld < ng_ || (d->ld & 1)))
     return fail(ACE_ERR_ARG, "ld must be 0 or an even count >= N_g");
-  if (d->prec < ACE_PREC_DEFAULT || d->prec > ACE_PREC_XI_FP64_SIMT) return fail(ACE_ERR_ARG, "bad prec");
+  if (d->prec < ACE_PREC_DEFAULT || d->prec > ACE_PREC_SPLIT_BF16) return fail(ACE_ERR_ARG, "bad prec");
   if (d->dtype != ACE_DTYPE_C64 && d->prec != ACE_PREC_DEFAULT)
     return fail(ACE_ERR_UNSUPPORTED, "FP64 plans compute in FP64: prec must be ACE_PREC_DEFAULT");
   if ((d->flags & ACE_FLAG_SIMT_GEMM) && d->prec != ACE_PREC_DEFAULT && d->prec != ACE_PREC_FP32)
@@ -805,7 +811,9 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->tc = !p->f64 && !(d->flags & ACE_FLAG_SIMT_GEMM) && d->prec != ACE_PREC_FP32;
   // C64 default: Xi to FP64 accuracy on the FP16 tensor cores (the triangular
   // product stays FP64-accurate, as the Cholesky factor it applies)
-  const bool xi_slices = d->prec == ACE_PREC_XI_FP64 || (d->prec == ACE_PREC_DEFAULT && p->tc);
+  p->bf16 = p->tc && d->prec == ACE_PREC_SPLIT_BF16;
+  const bool xi_slices = d->prec == ACE_PREC_XI_FP64 || d->prec == ACE_PREC_SPLIT_BF16 ||
+                         (d->prec == ACE_PREC_DEFAULT && p->tc);
   p->xi = xi_slices ? 1 : (d->prec == ACE_PREC_XI_FP64_SIMT ? 2 : 0);
   p->overlap = p->graphs && !p->engine && !(d->flags & ACE_FLAG_NO_OVERLAP);
   if (p->overlap && p->lanes < 2) p->lanes = 2;
@@ -909,7 +917,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
     ace_plan_destroy(p);
     return fail(ACE_ERR_CUDA, m);
   }
-  p->build = make_sym_schedule(N, p->tile, p->max_pairs);
+  p->build = make_sym_schedule(N, p->tile, p->max_pairs, p->real);
   e = upload(p, p->build);
   if (e != cudaSuccess) {
     std::string m = std::string("schedule upload: ") + cudaGetErrorString(e);
@@ -1058,7 +1066,7 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
   const uintptr_t kd[8] = {(uintptr_t)Phi, (uintptr_t)W, (uintptr_t)Xi_out, (uintptr_t)ws, (uintptr_t)n_phi, 6, 0, 0};
   s = run_graph(p, kd, st, false, [&](cudaStream_t cs) -> long long {
     const int splits = gram_parts(p, n_phi, n_phi);
-    if (p->tc) launch_gram_tc(Phi, n_phi, W, n_phi, p->ld, p->ng, Wl.part, splits, p->status, cs);
+    if (p->tc) launch_gram_tc(Phi, n_phi, W, n_phi, p->ld, p->ng, Wl.part, splits, p->status, cs, p->bf16);
     else launch_gram(p->f64, p->real, Phi, n_phi, W, n_phi, p->ld, p->ng, Wl.part, splits, cs);
     const int kr = launch_gram_reduce(Wl.part, splits, n_phi, n_phi, p->dv, true, false, Wl.Cm, nullptr, cs);
     if (p->tc) launch_diag_exact(Phi, W, n_phi, p->ld, p->ng, p->dv, Wl.part, Wl.Cm, cs);
@@ -1361,10 +1369,10 @@ ace_status ace_apply(ace_plan* p, const void* Xi, const void* Psi, int nb, void*
   const WsLayout Wl = layout(p, ACE_OP_APPLY, nb, (char*)ws);
   const int splits = gram_parts(p, N, nb);
   // C = dV Xi^* Psi, Y = -Xi C (Eq. ACE)
-  if (p->tc) launch_gram_tc(Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, p->status, st);
+  if (p->tc) launch_gram_tc(Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, p->status, st, p->bf16);
   else launch_gram(p->f64, p->real, Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, st);
   launch_gram_reduce(Wl.part, splits, N, nb, p->dv, false, false, Wl.Cm, nullptr, st);
-  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, p->status, st);
+  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, p->status, st, p->bf16);
   else launch_outer(p->f64, p->real, Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, st);
   p->launches += 3;
   return cuda_check("ace_apply");

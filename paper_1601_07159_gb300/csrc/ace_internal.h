@@ -28,6 +28,16 @@ struct Batch {
 __host__ __device__ inline int tile_pairs(const TileDesc& d) {
   return d.kind == 1 ? d.nl * (d.nl + 1) / 2 : d.nl * d.nr;
 }
+// Scratch slots of a tile. Complex vectors: one per pair. Real vectors: two
+// pairs (l, r), (l, r + 1) per slot, as the real and imaginary parts of one
+// complex solve (the kernel is real and even, so the two stay apart); on a
+// diagonal tile each row's pair (l, l) has a slot of its own, so that every
+// slot's pairs carry the same energy weight. Diagonal tile of n orbitals:
+// n + floor(n^2 / 4) slots; other tiles n_l ceil(n_r / 2).
+__host__ __device__ inline int tile_slots(const TileDesc& d, bool real) {
+  if (!real) return tile_pairs(d);
+  return d.kind == 1 ? d.nl + d.nl * d.nl / 4 : d.nl * ((d.nr + 1) / 2);
+}
 
 // Launchers (pair_f32.cu / pair_f64.cu). Return false if edge n is not compiled.
 struct PairLaunch {
@@ -110,13 +120,14 @@ void launch_outer(bool f64, bool real_io, const void* A, int nk, const double* C
 // M_out (n x n) and Ex_out = 1/2 Re of the first n_trace diagonal entries (all if < 0).
 int launch_m_outputs(const double* Mc, int n, bool real, double* M_out, double* Ex_out, cudaStream_t st,
                      int n_trace = -1);
-// Tensor-core (tcgen05 kind::tf32, 3-term split) GEMMs for complex FP32 (tc_gemm.cu).
+// Tensor-core GEMMs for complex FP32 with the 3-term split (tc_gemm.cu):
+// tcgen05 kind::tf32, or kind::f16 with BF16 operands when bf16 is set.
 bool tc_gemm_prepare();
 int gram_tc_splits(long long ng, int na, int nb);
 void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, long long ng, double* part,
-                    int splits, int* status, cudaStream_t st);
+                    int splits, int* status, cudaStream_t st, bool bf16 = false);
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
-                     void* Out, int* status, cudaStream_t st);
+                     void* Out, int* status, cudaStream_t st, bool bf16 = false);
 // Xi = W L^{-*} with FP64 arithmetic from complex FP32 W (dense.cu): C upper
 // triangular FP64 [nk][nb]; Out complex FP32 or FP64 [nb][ld].
 void launch_outer_f64acc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,

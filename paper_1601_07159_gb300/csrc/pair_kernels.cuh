@@ -97,6 +97,7 @@ template <typename R, int NZ> struct PencilParams {
   int khy, kzs;            // folded table: row length n_y/2 + 1, kz stride (n_x/2 + 1)(n_y/2 + 1)
   const TileDesc* tiles;
   int ntiles;
+  int packed;              // real vectors: two pairs per slot (energy weights by decode_slot_real)
   TwTable<R, NZ> tw;
 };
 
@@ -166,6 +167,40 @@ __device__ __forceinline__ int decode_pair(const TileDesc* __restrict__ tiles, i
   return t;
 }
 
+// Slot s of a batch of real vectors -> tile index and the slot's pairs (l, r)
+// (real part) and (l, r2) (imaginary part; r2 < 0: none). Diagonal tile row
+// li: the slot (l, l) alone, then (l, l + 1 + 2m), (l, l + 2 + 2m); other
+// tiles: row li holds (l, r0 + 2m), (l, r0 + 2m + 1).
+__device__ __forceinline__ int decode_slot_real(const TileDesc* __restrict__ tiles, int ntiles, int s, int& l,
+                                                int& r, int& r2) {
+  int t = 0;
+  while (t + 1 < ntiles && tiles[t + 1].slot0 <= s) ++t;
+  const TileDesc d = tiles[t];
+  int q = s - d.slot0;
+  if (d.kind == 1) {
+    int li = 0, len = 1 + d.nl / 2;
+    while (q >= len) { q -= len; ++li; len = 1 + (d.nl - li) / 2; }
+    l = d.l0 + li;
+    r = q == 0 ? l : l + 2 * q - 1;
+    r2 = (q != 0 && r + 1 < d.l0 + d.nl) ? r + 1 : -1;
+  } else {
+    const int w = (d.nr + 1) / 2;
+    l = d.l0 + q / w;
+    r = d.r0 + 2 * (q % w);
+    r2 = r + 1 < d.r0 + d.nr ? r + 1 : -1;
+  }
+  return t;
+}
+
+// Energy weight of slot p: 1 for the diagonal pair (l, l), 2 otherwise (the
+// pair and its mirror (r, l)).
+__device__ __forceinline__ double slot_weight(const TileDesc* __restrict__ tiles, int ntiles, int p, bool real) {
+  int l, r, r2;
+  if (real) decode_slot_real(tiles, ntiles, p, l, r, r2);
+  else decode_pair(tiles, ntiles, p, l, r);
+  return l == r ? 1.0 : 2.0;
+}
+
 template <typename R, bool REAL>
 __device__ __forceinline__ cplx<R> load_vec(const void* base, long long idx) {
   if constexpr (REAL) {
@@ -227,21 +262,34 @@ __device__ __forceinline__ void body_a(const PlaneParams<R, NX, NY>& P, const Ti
   cplx<R>* buf = smem + ty * NY * (NX + 1);
   const long long item = vb * IPB + ty;
   const bool active = ty < IPB && item < (long long)npairs * P.nz;
-  int p = 0, z = 0, l = 0, r = 0;
+  int p = 0, z = 0, l = 0, r = 0, r2 = -1;
   if (active) {   // z-plane major: the pairs of a tile that share an orbital plane run together
     z = (int)(item / npairs);
     p = (int)(item % npairs);
-    decode_pair(tiles, ntiles, p, l, r);
+    if constexpr (REAL) decode_slot_real(tiles, ntiles, p, l, r, r2);
+    else decode_pair(tiles, ntiles, p, l, r);
   }
   if (active && tx < NX) {
     cplx<R> a[NY];
     const long long xo = (long long)l * P.ld + (long long)z * NX * NY + tx;
     const long long yo = (long long)r * P.ld + (long long)z * NX * NY + tx;
+    if constexpr (REAL) {                     // x_l (y_r + i y_r2)
+      const R* Xr = static_cast<const R*>(P.X);
+      const R* Yr = static_cast<const R*>(P.Y);
+      const bool two = r2 >= 0;
+      const long long y2o = (long long)(two ? r2 : r) * P.ld + (long long)z * NX * NY + tx;
 #pragma unroll
-    for (int y = 0; y < NY; ++y) {
-      const cplx<R> xv = load_vec<R, REAL>(P.X, xo + y * NX);
-      const cplx<R> yv = load_vec<R, REAL>(P.Y, yo + y * NX);
-      a[y] = cmulc(xv, yv);                   // conj(x_l) * y_r
+      for (int y = 0; y < NY; ++y) {
+        const R xv = Xr[xo + y * NX];
+        a[y] = cmk<cplx<R>>(xv * Yr[yo + y * NX], two ? xv * Yr[y2o + y * NX] : R(0));
+      }
+    } else {
+#pragma unroll
+      for (int y = 0; y < NY; ++y) {
+        const cplx<R> xv = load_vec<R, REAL>(P.X, xo + y * NX);
+        const cplx<R> yv = load_vec<R, REAL>(P.Y, yo + y * NX);
+        a[y] = cmulc(xv, yv);                 // conj(x_l) * y_r
+      }
     }
     dft<NY, NY, false, R>(a, P.tw.ty());      // along y, column x = tx
 #pragma unroll
@@ -287,11 +335,7 @@ __device__ __forceinline__ void body_b(const PencilParams<R, NZ>& P, const TileD
       if (mode != 0) acc += k * (a[kz].x * a[kz].x + a[kz].y * a[kz].y);
       a[kz] = cscale(a[kz], k);
     }
-    if (mode != 0) {
-      int l, r;
-      decode_pair(tiles, ntiles, p, l, r);
-      e = (l == r ? 1.0 : 2.0) * (double)acc;
-    }
+    if (mode != 0) e = slot_weight(tiles, ntiles, p, P.packed) * (double)acc;
     if (mode != 1) {
       dft<NZ, NZ, true, R>(a, P.tw);
 #pragma unroll
@@ -469,11 +513,11 @@ __device__ __forceinline__ void d_split_off(const PointParams<R>& P, const TileD
   }
 }
 
-// Pass D for point block `vbx` (nthr points) of tile `d`; NGC = N_g at compile
-// time (cubic grids) or 0 (read from the parameters).
+// Pass D (complex vectors) for point block `vbx` (nthr points) of tile `d`;
+// NGC = N_g at compile time (cubic grids) or 0 (read from the parameters).
 template <typename R, bool REAL, bool COH, bool FULL_OFF, long long NGC>
-__device__ __forceinline__ void body_d(const PointParams<R>& P, const TileDesc& d, long long vbx, int tid,
-                                       int nthr) {
+__device__ __forceinline__ void body_d_cplx(const PointParams<R>& P, const TileDesc& d, long long vbx, int tid,
+                                            int nthr) {
   const long long NG = NGC ? NGC : P.ng;
   const long long g = vbx * nthr + tid;
   if (g >= NG) return;
@@ -547,6 +591,202 @@ __device__ __forceinline__ void body_d(const PointParams<R>& P, const TileDesc& 
 #pragma unroll
     for (int o = 0; o < kTileMax; ++o)
       if (o < d.nr) rmw_out<R, REAL, COH>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+  }
+}
+
+// ---- pass D for real vectors: a slot holds v = V_lr + i V_lr2 (decode_slot_real)
+template <typename R, bool COH>
+__device__ __forceinline__ void rmw_real(void* base, long long idx, R acc, R scale) {
+  R* o = static_cast<R*>(base) + idx;
+  stx<COH>(o, ldx<COH>(o) - scale * acc);
+}
+// full tiles read their potentials once, with the streaming hint
+template <bool FULL, bool COH, typename T> __device__ __forceinline__ T ldv(const T* p) {
+  if constexpr (FULL) return __ldcs(p);
+  else return ldx<COH>(p);
+}
+
+// Diagonal tile: Out_l -= sum over its pairs; a pair (l, r != l) feeds both
+// Out_r (x_l V_lr) and Out_l (x_r V_lr), the pair (l, l) Out_l once.
+template <typename R, bool COH, bool FULL, long long NGC>
+__device__ __forceinline__ void d_real_diag(const PointParams<R>& P, const TileDesc& d, const cplx<R>* V,
+                                            long long g) {
+  const long long NG = NGC ? NGC : P.ng;
+  constexpr int B = kTileMax;
+  const int n = FULL ? B : d.nl;
+  const R* X = static_cast<const R*>(P.X);
+  R x[B], acc[B];
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    acc[o] = R(0);
+    x[o] = (FULL || o < n) ? X[(long long)(d.l0 + o) * P.ld + g] : R(0);
+  }
+  int q = 0;
+#pragma unroll
+  for (int li = 0; li < B; ++li) {
+    if (FULL || li < n) {
+      const cplx<R> v0 = ldv<FULL, COH>(V + (long long)q * NG);
+      ++q;
+      acc[li] += x[li] * v0.x;
+#pragma unroll
+      for (int ri = li + 1; ri < B; ri += 2) {
+        if (FULL || ri < n) {
+          const cplx<R> v = ldv<FULL, COH>(V + (long long)q * NG);
+          ++q;
+          acc[ri] += x[li] * v.x;
+          acc[li] += v.x * x[ri];
+          if (ri + 1 < B && (FULL || ri + 1 < n)) {
+            acc[ri + 1] += x[li] * v.y;
+            acc[li] += v.y * x[ri + 1];
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < B; ++o)
+    if (FULL || o < n) rmw_real<R, COH>(P.OutY, (long long)(d.l0 + o) * P.ld + g, acc[o], P.scale);
+}
+
+// Off-diagonal tile of a symmetric schedule (one thread per point).
+template <typename R, bool COH, bool FULL, long long NGC>
+__device__ __forceinline__ void d_real_off(const PointParams<R>& P, const TileDesc& d, const cplx<R>* V,
+                                           long long g) {
+  const long long NG = NGC ? NGC : P.ng;
+  constexpr int B = kTileMax, W2 = kTileMax / 2;
+  const int nl = FULL ? B : d.nl, nr = FULL ? B : d.nr, w = FULL ? W2 : (d.nr + 1) / 2;
+  const R* X = static_cast<const R*>(P.X);
+  const R* Y = static_cast<const R*>(P.Y);
+  R xl[B], yr[B], al[B], ar[B];
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    al[o] = R(0);
+    ar[o] = R(0);
+    xl[o] = (FULL || o < nl) ? X[(long long)(d.l0 + o) * P.ld + g] : R(0);
+    yr[o] = (FULL || o < nr) ? Y[(long long)(d.r0 + o) * P.ld + g] : R(0);
+  }
+#pragma unroll
+  for (int li = 0; li < B; ++li) {
+#pragma unroll
+    for (int m = 0; m < W2; ++m) {
+      if ((FULL || li < nl) && (FULL || 2 * m < nr)) {
+        const cplx<R> v = ldv<FULL, COH>(V + (long long)(li * w + m) * NG);
+        ar[2 * m] += xl[li] * v.x;
+        al[li] += v.x * yr[2 * m];
+        if (FULL || 2 * m + 1 < nr) {
+          ar[2 * m + 1] += xl[li] * v.y;
+          al[li] += v.y * yr[2 * m + 1];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    if (FULL || o < nr) rmw_real<R, COH>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+    if (FULL || o < nl) rmw_real<R, COH>(P.OutX, (long long)(d.l0 + o) * P.ld + g, al[o], P.scale);
+  }
+}
+
+// One-sided tile (V_X[Phi] Psi, Poisson solves): Out_r -= sum_l x_l V_lr.
+template <typename R, bool COH, long long NGC>
+__device__ __forceinline__ void d_real_rect(const PointParams<R>& P, const TileDesc& d, const cplx<R>* V,
+                                            long long g) {
+  const long long NG = NGC ? NGC : P.ng;
+  constexpr int B = kTileMax, W2 = kTileMax / 2;
+  const int w = (d.nr + 1) / 2;
+  const R* X = static_cast<const R*>(P.X);
+  R ar[B];
+#pragma unroll
+  for (int o = 0; o < B; ++o) ar[o] = R(0);
+  for (int li = 0; li < d.nl; ++li) {
+    const R xv = X[(long long)(d.l0 + li) * P.ld + g];
+#pragma unroll
+    for (int m = 0; m < W2; ++m) {
+      if (2 * m < d.nr) {
+        const cplx<R> v = ldx<COH>(V + (long long)(li * w + m) * NG);
+        ar[2 * m] += xv * v.x;
+        if (2 * m + 1 < d.nr) ar[2 * m + 1] += xv * v.y;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < B; ++o)
+    if (o < d.nr) rmw_real<R, COH>(P.OutY, (long long)(d.r0 + o) * P.ld + g, ar[o], P.scale);
+}
+
+// Full off-diagonal tile of real vectors with two threads per point, as
+// d_split_off: half h takes the right orbitals r0 + 4h .. r0 + 4h + 3 (slots
+// li * 4 + 2h, li * 4 + 2h + 1 of each row).
+template <typename R, long long NGC>
+__device__ __forceinline__ void d_split_off_real(const PointParams<R>& P, const TileDesc& d, long long vbx, int tid,
+                                                 R* xch) {
+  const long long NG = NGC ? NGC : P.ng;
+  constexpr int B = kTileMax, H = kTileMax / 2, Q = H / 2;
+  const int h = (tid >> 5) & 1;
+  const int pt = ((tid >> 6) << 5) | (tid & 31);
+  const long long g = vbx * kDSplitPts + pt;
+  const bool act = g < NG;
+  const cplx<R>* V = P.S + (long long)d.slot0 * NG + g;
+  const R* X = static_cast<const R*>(P.X);
+  const R* Y = static_cast<const R*>(P.Y);
+  R xl[B], yr[H], al[B], ar[H];
+#pragma unroll
+  for (int o = 0; o < B; ++o) {
+    al[o] = R(0);
+    xl[o] = act ? X[(long long)(d.l0 + o) * P.ld + g] : R(0);
+  }
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    ar[o] = R(0);
+    yr[o] = act ? Y[(long long)(d.r0 + h * H + o) * P.ld + g] : R(0);
+  }
+  if (act) {
+#pragma unroll
+    for (int li = 0; li < B; ++li) {
+#pragma unroll
+      for (int m = 0; m < Q; ++m) {
+        const cplx<R> v = __ldcs(V + (long long)(li * H + h * Q + m) * NG);
+        ar[2 * m] += xl[li] * v.x;
+        ar[2 * m + 1] += xl[li] * v.y;
+        al[li] += v.x * yr[2 * m];
+        al[li] += v.y * yr[2 * m + 1];
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 0; o < H; ++o) xch[o * 256 + tid] = h ? al[o] : al[H + o];   // the partner's half
+  __syncthreads();
+  if (!act) return;
+  const int partner = tid ^ 32;
+#pragma unroll
+  for (int o = 0; o < H; ++o) {
+    const R own = h ? al[H + o] : al[o];
+    const R other = xch[o * 256 + partner];
+    const R lo = h ? other : own, hi = h ? own : other;                    // r-half 0 first, then 1
+    rmw_real<R, false>(P.OutX, (long long)(d.l0 + h * H + o) * P.ld + g, lo + hi, P.scale);
+    rmw_real<R, false>(P.OutY, (long long)(d.r0 + h * H + o) * P.ld + g, ar[o], P.scale);
+  }
+}
+
+// Pass D for point block `vbx` (nthr points) of tile `d`.
+template <typename R, bool REAL, bool COH, bool FULL_OFF, long long NGC>
+__device__ __forceinline__ void body_d(const PointParams<R>& P, const TileDesc& d, long long vbx, int tid,
+                                       int nthr) {
+  if constexpr (REAL) {
+    const long long g = vbx * nthr + tid;
+    if (g >= (NGC ? NGC : P.ng)) return;
+    const cplx<R>* V = P.S + (long long)d.slot0 * (NGC ? NGC : P.ng) + g;
+    if (d.kind == 1) {
+      if (d.nl == kTileMax) d_real_diag<R, COH, true, NGC>(P, d, V, g);
+      else d_real_diag<R, COH, false, NGC>(P, d, V, g);
+    } else if (d.kind == 0) {
+      if (FULL_OFF && d.nl == kTileMax && d.nr == kTileMax) d_real_off<R, COH, true, NGC>(P, d, V, g);
+      else d_real_off<R, COH, false, NGC>(P, d, V, g);
+    } else {
+      d_real_rect<R, COH, NGC>(P, d, V, g);
+    }
+  } else {
+    body_d_cplx<R, REAL, COH, FULL_OFF, NGC>(P, d, vbx, tid, nthr);
   }
 }
 
@@ -651,11 +891,7 @@ pass_b_split_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
     y[j] = cscale(y[j], k);
   }
   double e = 0.0;
-  if (mode != 0 && active) {
-    int l, r;
-    decode_pair(P.tiles, P.ntiles, p, l, r);
-    e = (l == r ? 1.0 : 2.0) * (double)acc;
-  }
+  if (mode != 0 && active) e = slot_weight(P.tiles, P.ntiles, p, P.packed) * (double)acc;
   if (mode != 1) {
 #pragma unroll
     for (int j = 0; j < H; ++j) {                          // k = hH + j
@@ -726,8 +962,9 @@ pass_a_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   const int tid = threadIdx.x, q = tid >> 1, h = tid & 1;
   const long long item = blockIdx.x;                      // one (pair, z) plane per block, z-major:
   const int z = (int)(item / P.npairs), p = (int)(item % P.npairs);   // pairs sharing a plane run together
-  int l, r;
-  decode_pair(P.tiles, P.ntiles, p, l, r);
+  int l, r, r2 = -1;
+  if constexpr (REAL) decode_slot_real(P.tiles, P.ntiles, p, l, r, r2);
+  else decode_pair(P.tiles, P.ntiles, p, l, r);
   const C zero = cmk<C>(R(0), R(0));
   {   // column x = q: samples y = 2m + h
     constexpr int M = NY / 2;
@@ -735,10 +972,23 @@ pass_a_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
     C a[M], y[M];
     const long long xo = (long long)l * P.ld + (long long)z * NX * NY + q;
     const long long yo = (long long)r * P.ld + (long long)z * NX * NY + q;
+    if constexpr (REAL) {                                  // x_l (y_r + i y_r2)
+      const R* Xr = static_cast<const R*>(P.X);
+      const R* Yr = static_cast<const R*>(P.Y);
+      const bool two = r2 >= 0;
+      const long long y2o = (long long)(two ? r2 : r) * P.ld + (long long)z * NX * NY + q;
 #pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const int yy = 2 * m + h;
-      a[m] = act ? cmulc(load_vec<R, REAL>(P.X, xo + yy * NX), load_vec<R, REAL>(P.Y, yo + yy * NX)) : zero;
+      for (int m = 0; m < M; ++m) {
+        const int yy = 2 * m + h;
+        const R xv = act ? Xr[xo + yy * NX] : R(0);
+        a[m] = act ? cmk<C>(xv * Yr[yo + yy * NX], two ? xv * Yr[y2o + yy * NX] : R(0)) : zero;
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        const int yy = 2 * m + h;
+        a[m] = act ? cmulc(load_vec<R, REAL>(P.X, xo + yy * NX), load_vec<R, REAL>(P.Y, yo + yy * NX)) : zero;
+      }
     }
     split_line_dft<NY, false, R>(a, y, h, P.tw.ty());     // along y
     if (act) {
@@ -803,6 +1053,151 @@ pass_c_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   }
 }
 
+// ---- four warps per 32 lines (pass B for FP32 pencils of 96)
+// A length-N line transform (N = 4M, decimation in time by 4) is spread over
+// four warps: the thread with phase h (warp-uniform) transforms the samples
+// 4m + h (a DFT of M in registers) and multiplies by w_N^{hk}; after a block
+// barrier the thread with phase h forms, for its M/4 frequencies k = hM/4 + j,
+// the radix-4 combination Y[k + qM] = sum_h' (w_4)^{h'q} U_h'[k] (q = 0..3) of
+// the four phases' values, read from shared memory. A thread holds a quarter of
+// a line (M values) and needs no shuffles or lane-dependent selects (the phase
+// is warp-uniform, so its twiddles are compile-time constants in one of four
+// code paths). For the plane passes the same scheme measured slower than the
+// two-lane form (six shared-memory accesses per point per pass: bound by the
+// shared-memory pipe), so only pass B uses it.
+template <int N, bool INV, typename R>
+__device__ __forceinline__ void quad_sub_dft(cplx<R> (&a)[N / 4], int h, const TwTable<R, N>& tw) {
+  constexpr int M = N / 4;
+  dft<M, N, INV, R>(a, tw);
+  if (h == 1) {
+#pragma unroll
+    for (int k = 1; k < M; ++k) a[k] = twiddle<N, N, INV, R>(a[k], k, tw);
+  } else if (h == 2) {
+#pragma unroll
+    for (int k = 1; k < M; ++k) a[k] = twiddle<N, N, INV, R>(a[k], 2 * k, tw);
+  } else if (h == 3) {
+#pragma unroll
+    for (int k = 1; k < M; ++k) a[k] = twiddle<N, N, INV, R>(a[k], 3 * k, tw);
+  }
+}
+
+// The radix-4 step for one line whose value U_h'[k] sits at
+// buf[base + (h'M + k) stride]: for j < M/4 and k = hM/4 + j,
+// out[4j + q] = Y[k + qM].
+template <int N, bool INV, typename R>
+__device__ __forceinline__ void quad_combine(const cplx<R>* __restrict__ buf, int base, int stride, int h,
+                                             cplx<R> (&out)[N / 4], const TwTable<R, N>& tw) {
+  constexpr int M = N / 4, Q = M / 4;
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+    cplx<R> u[4];
+#pragma unroll
+    for (int hh = 0; hh < 4; ++hh) u[hh] = buf[base + (hh * M + h * Q + j) * stride];
+    dft<4, N, INV, R>(u, tw);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[4 * j + q] = u[q];
+  }
+}
+
+// Pass B with four warps per 32 pencils (FP32 pencils of 96): warp h holds the
+// samples z = 4m + h of its lane's pencil, transforms them (quad_sub_dft) and
+// stores them to shared memory; after a barrier each thread forms the radix-4
+// combination for its M/4 frequencies k = hM/4 + j, which gives it the 24
+// spectrum values kz = k + qM (q = 0..3), multiplies them by K(G) (and sums
+// the energy), and takes the inverse radix-4 step right away: for each of its k,
+// Z_h'[k] = sum_q Y[k + qM] (w_4)^{-h'q} w_N^{-h'k}, h' = 0..3, written back to
+// the same shared-memory places it read. After a second barrier warp h reads
+// Z_h[k] for all k and an inverse DFT of M gives x[4m + h]. The 96-point pencil
+// thus needs a quarter of it in registers per thread (no spills, where the
+// two-lane form spills at two blocks per SM) and no shuffles.
+constexpr int kQuadPencils = 32;   // pencils per 128-thread block of the four-warp pass B
+template <typename R, int NZ> constexpr bool kQuadPencil = sizeof(R) == 4 && NZ == 96;
+
+// u[4j + h'] *= w_N^{-h'(HQ + j)} (inverse twiddles of warp phase H)
+template <int N, int H, typename R>
+__device__ __forceinline__ void quad_inv_twiddle(cplx<R> (&u)[N / 4], const TwTable<R, N>& tw) {
+  constexpr int Q = N / 16;
+#pragma unroll
+  for (int j = 0; j < Q; ++j)
+#pragma unroll
+    for (int hp = 1; hp < 4; ++hp) u[4 * j + hp] = twiddle<N, N, true, R>(u[4 * j + hp], hp * (H * Q + j), tw);
+}
+
+template <typename R, int NZ, bool CUBE>
+__global__ void __launch_bounds__(128, 5)
+pass_b_quad_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
+  using C = cplx<R>;
+  constexpr int N = NZ, M = N / 4, Q = M / 4, LP = kQuadPencils;
+  static_assert(M % 4 == 0, "M / 4 frequencies per thread");
+  __shared__ C buf[N * LP];                                // [phase h, k][pencil]
+  __shared__ double red[4];
+  griddep_launch();
+  griddep_wait();
+  const PencilGeom<R, NZ, CUBE> G(P);
+  const int nxy = G.nxy;
+  const int h = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long gid = (long long)blockIdx.x * LP + lane;
+  const bool active = gid < (long long)P.npairs * nxy;
+  const int p = active ? (int)(gid / nxy) : 0;
+  const int f = active ? (int)(gid % nxy) : 0;
+  C* s = P.S + (long long)p * N * nxy + f;
+  const C zero = cmk<C>(R(0), R(0));
+  C a[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) a[m] = active ? s[(long long)(4 * m + h) * nxy] : zero;
+  quad_sub_dft<N, false, R>(a, h, P.tw);
+#pragma unroll
+  for (int k = 0; k < M; ++k) buf[(h * M + k) * LP + lane] = a[k];
+  __syncthreads();
+  quad_combine<N, false, R>(buf, lane, LP, h, a, P.tw);    // a[4j + q] = Y[hQ + j + qM]
+  R acc = R(0);
+  const R* kt = P.Kt + G.kt_pencil(f);
+#pragma unroll
+  for (int j = 0; j < Q; ++j) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int kz = h * Q + j + q * M;
+      const R kv = kt[kfold<N>(kz) * G.kzs];
+      C& v = a[4 * j + q];
+      if (mode != 0) acc += kv * (v.x * v.x + v.y * v.y);
+      v = cscale(v, kv);
+    }
+  }
+  if (mode != 1) {
+#pragma unroll
+    for (int j = 0; j < Q; ++j) {                          // inverse radix-4 over q: outputs by phase h'
+      C u[4] = {a[4 * j], a[4 * j + 1], a[4 * j + 2], a[4 * j + 3]};
+      dft<4, N, true, R>(u, P.tw);
+#pragma unroll
+      for (int hp = 0; hp < 4; ++hp) a[4 * j + hp] = u[hp];
+    }
+    if (h == 0) quad_inv_twiddle<N, 0, R>(a, P.tw);
+    else if (h == 1) quad_inv_twiddle<N, 1, R>(a, P.tw);
+    else if (h == 2) quad_inv_twiddle<N, 2, R>(a, P.tw);
+    else quad_inv_twiddle<N, 3, R>(a, P.tw);
+#pragma unroll
+    for (int j = 0; j < Q; ++j)                            // the places quad_combine read
+#pragma unroll
+      for (int hp = 0; hp < 4; ++hp) buf[(hp * M + h * Q + j) * LP + lane] = a[4 * j + hp];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < M; ++k) a[k] = buf[(h * M + k) * LP + lane];   // Z_h[k], k < M
+    dft<M, N, true, R>(a, P.tw);                           // x[4m + h] = a[m]
+    if (active) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) s[(long long)(4 * m + h) * nxy] = a[m];
+    }
+  }
+  if (mode != 0) {
+    double e = active ? slot_weight(P.tiles, P.ntiles, p, P.packed) * (double)acc : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if (lane == 0) red[h] = e;
+    __syncthreads();
+    if (threadIdx.x == 0) P.Epart[blockIdx.x] += red[0] + red[1] + red[2] + red[3];   // one block per slot
+  }
+}
+
 template <typename R, int NZ, bool CUBE>
 __global__ void __launch_bounds__(256, 2)
 pass_b_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
@@ -835,7 +1230,8 @@ pass_d_kernel(const __grid_constant__ PointParams<R> P) {
   griddep_wait();
   const TileDesc d = P.tiles[blockIdx.y];
   if (d.kind == 0 && d.nl == kTileMax && d.nr == kTileMax) {
-    d_split_off<R, REAL, NGC>(P, d, blockIdx.x, threadIdx.x, xch);
+    if constexpr (REAL) d_split_off_real<R, NGC>(P, d, blockIdx.x, threadIdx.x, reinterpret_cast<R*>(xch));
+    else d_split_off<R, REAL, NGC>(P, d, blockIdx.x, threadIdx.x, xch);
     return;
   }
   // other tiles: one thread per point, 256 points per block (the grid is
@@ -981,6 +1377,7 @@ void fill_pencil(PencilParams<R, NZ>& P, const PairLaunch& L, const Batch& b) {
   P.kzs = (L.nx / 2 + 1) * (L.ny / 2 + 1);
   P.tiles = L.dtiles;
   P.ntiles = b.ntiles;
+  P.packed = L.real_io ? 1 : 0;
   for (int k = 0; k < NZ; ++k) {
     P.tw.w[k].x = (R)L.twz[2 * k];
     P.tw.w[k].y = (R)L.twz[2 * k + 1];
@@ -1065,7 +1462,10 @@ bool launch_plane(const PairLaunch& L, const Batch& b, int pass, cudaStream_t st
 // Pass B of one batch (the compile-time geometry on cubic grids).
 template <typename R, int NZ, bool CUBE>
 void launch_pencil_as(const PencilParams<R, NZ>& P, const PairLaunch& L, long long pencils, cudaStream_t st) {
-  if constexpr (kSplitPencil<NZ>) {
+  if constexpr (kQuadPencil<R, NZ>) {
+    const unsigned grid = (unsigned)((pencils + kQuadPencils - 1) / kQuadPencils);
+    launch_pdl(!L.no_pdl, pass_b_quad_kernel<R, NZ, CUBE>, dim3(grid), dim3(128), 0, st, P, L.mode);
+  } else if constexpr (kSplitPencil<NZ>) {
     const unsigned grid = (unsigned)((pencils + kBSplitPencils - 1) / kBSplitPencils);
     launch_pdl(!L.no_pdl, pass_b_split_kernel<R, NZ, CUBE>, dim3(grid), dim3(256), 0, st, P, L.mode);
   } else {

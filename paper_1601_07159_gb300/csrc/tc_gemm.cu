@@ -29,6 +29,15 @@
 // x 3 products of tcgen05.mma (M = 128, N = TN, K = 8) and commits them to the
 // stage's mbarrier; a stage is refilled only after its commit has been seen.
 //
+// BF16 split (the same kernels with BF = true, tcgen05 kind::f16 with BF16
+// operands): x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (round to
+// nearest), the same three products; 16 significant bits per operand, so a
+// product carries a relative error of about 2^-16 (the lo.lo term and the
+// rounding of lo) instead of FP32 rounding. The operand tiles hold 2-byte
+// elements (core matrices of 8 rows x 8 values; SBO = 512 B for the 32 real
+// K terms of a chunk), and a K-step of the MMA takes 16 terms, so a chunk is
+// two K-steps of 3 products instead of four.
+//
 // The tensor core's FP32 accumulation truncates, so a long chain of MMAs into
 // one accumulator drifts toward zero (about 2^-24 per accumulation). The
 // accumulator therefore restarts every kGroup chunks (12 MMAs each, drift
@@ -42,6 +51,7 @@
 
 #include "ace_internal.h"
 #include "tcgen05.cuh"
+#include <cuda_bf16.h>
 
 namespace ace {
 
@@ -54,39 +64,63 @@ using tc::mma_commit;
 constexpr int THREADS = 512;
 constexpr int TM = 128;                    // rows per CTA (M of the MMA)
 constexpr int KC = 32;                     // real K terms per stage
-constexpr int SBO = (KC / 4) * 128;        // bytes between 8-row groups = 1024
-constexpr int OPA_BYTES = TM * KC * 4;     // one A operand tile (128 x 32 FP32) = 16 KB
 constexpr int kGroup = 4;                  // chunks per accumulator group
 constexpr unsigned kWaitLimit = 1u << 24;
 
-template <int TN> struct Tile {
+// operand element bytes, bytes between 8-row groups (1024 TF32, 512 BF16),
+// one A operand tile (128 x 32: 16 KB TF32, 8 KB BF16)
+template <bool BF> constexpr int kES = BF ? 2 : 4;
+template <bool BF> constexpr int kSBO = (KC * kES<BF> / 16) * 128;
+template <bool BF> constexpr int kOPA = TM * KC * kES<BF>;
+
+template <int TN, bool BF> struct Tile {
   static_assert(TN == 128 || TN == 192 || TN == 256, "MMA width");
   static constexpr int BB = TN / 2;                          // complex output columns per tile
   static constexpr int NACC = TN / 4;                        // accumulator columns per thread
-  static constexpr int OPB_BYTES = TN * KC * 4;              // one B operand tile
+  static constexpr int OPA_BYTES = kOPA<BF>;
+  static constexpr int OPB_BYTES = TN * KC * kES<BF>;        // one B operand tile
   static constexpr int STAGE_BYTES = 2 * OPA_BYTES + 2 * OPB_BYTES;   // A_hi, A_lo, B_hi, B_lo
   static constexpr int NSTAGE = TN == 128 ? 3 : 2;           // chunk c uses stage c % NSTAGE
   static constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 64;
   static constexpr int TMEM_COLS = TN == 128 ? 256 : 512;    // two accumulators, a power of two
-  // instruction descriptor: D = F32, A = B = TF32, both K-major, N = TN, M = 128
-  static constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+  // instruction descriptor: D = F32, A = B = TF32 (format 2) or BF16 (format 1),
+  // both K-major, N = TN, M = 128
+  static constexpr uint32_t FMT = BF ? 1u : 2u;
+  static constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((uint32_t)(TN >> 3) << 17) |
                                     ((uint32_t)(TM >> 4) << 24);
 };
 
 // shared-memory matrix descriptor of an operand tile (K-major, no swizzle)
-__device__ __forceinline__ uint64_t mat_desc(uint32_t addr) { return tc::kmajor_desc(addr, SBO); }
+template <bool BF> __device__ __forceinline__ uint64_t mat_desc(uint32_t addr) {
+  return tc::kmajor_desc(addr, kSBO<BF>);
+}
 
-// byte offset of element (row r, real k) in an operand tile
-__device__ __forceinline__ int tile_off(int r, int k) {
-  return (r >> 3) * SBO + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4;
+// byte offset of element (row r, real k) in an operand tile: core matrices of
+// 8 rows x 16 bytes (4 TF32 or 8 BF16 values along K)
+template <bool BF> __device__ __forceinline__ int tile_off(int r, int k) {
+  constexpr int V = 16 / kES<BF>;
+  return (r >> 3) * kSBO<BF> + (k / V) * 128 + (r & 7) * 16 + (k % V) * kES<BF>;
 }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-__device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int off, float4 v) {
-  const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-  *reinterpret_cast<float4*>(hi + off) = h;
-  *reinterpret_cast<float4*>(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+__device__ __forceinline__ unsigned bf16_pair(float a, float b) {
+  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(a)) |
+         ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(b)) << 16);
+}
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// four consecutive K values of one row into the hi and lo tiles
+template <bool BF> __device__ __forceinline__ void split_store(unsigned char* hi, unsigned char* lo, int off, float4 v) {
+  if constexpr (BF) {
+    const float4 h = make_float4(bf16_round(v.x), bf16_round(v.y), bf16_round(v.z), bf16_round(v.w));
+    *reinterpret_cast<uint2*>(hi + off) = make_uint2(bf16_pair(h.x, h.y), bf16_pair(h.z, h.w));
+    *reinterpret_cast<uint2*>(lo + off) = make_uint2(bf16_pair(v.x - h.x, v.y - h.y), bf16_pair(v.z - h.z, v.w - h.w));
+  } else {
+    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+  }
 }
 
 // bounded wait for the phase with parity `parity`; false on timeout
@@ -94,14 +128,23 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
   return tc::mbar_wait(bar, parity, kWaitLimit);
 }
 
-template <int TN>
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(a), "l"(b), "r"(Tile<TN>::IDESC), "r"(accumulate)
-      : "memory");
+template <int TN, bool BF>
+__device__ __forceinline__ void mma_split(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  if constexpr (BF) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(Tile<TN, BF>::IDESC), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(Tile<TN, BF>::IDESC), "r"(accumulate)
+        : "memory");
+  }
 }
 
 // 32 consecutive accumulator columns of this thread's lane, added into acc[o .. o + 31]
@@ -151,9 +194,9 @@ struct TcState {
   unsigned char* stage; // NSTAGE stages
 };
 
-template <int TN>
+template <int TN, bool BF>
 __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
-  using T = Tile<TN>;
+  using T = Tile<TN, BF>;
   TcState s;
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
   s.stage = base;
@@ -175,27 +218,28 @@ __device__ __forceinline__ TcState tc_setup(unsigned char* smem) {
   return s;
 }
 
-template <int TN>
+template <int TN, bool BF>
 __device__ __forceinline__ void tc_teardown(uint32_t tmem) {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (threadIdx.x < 32)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Tile<TN>::TMEM_COLS)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Tile<TN, BF>::TMEM_COLS)
                  : "memory");
 }
 
-// One K chunk in a stage: 4 K-steps x 3 split products into accumulator `dtmem`,
-// committed to `bar`.
-template <int TN>
+// One K chunk in a stage: 4 (TF32) or 2 (BF16) K-steps x 3 split products into
+// accumulator `dtmem`, committed to `bar`.
+template <int TN, bool BF>
 __device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char* st, uint64_t* bar, bool first) {
-  const uint32_t ah = smem_u32(st), al = ah + OPA_BYTES, bh = ah + 2 * OPA_BYTES, bl = bh + Tile<TN>::OPB_BYTES;
+  using T = Tile<TN, BF>;
+  const uint32_t ah = smem_u32(st), al = ah + T::OPA_BYTES, bh = ah + 2 * T::OPA_BYTES, bl = bh + T::OPB_BYTES;
 #pragma unroll
-  for (int ks = 0; ks < KC / 8; ++ks) {
+  for (int ks = 0; ks < KC / (BF ? 16 : 8); ++ks) {
     const uint32_t o = ks * 256;   // two core matrices of 16 B along K per step
-    mma_tf32<TN>(dtmem, mat_desc(ah + o), mat_desc(bh + o), (first && ks == 0) ? 0u : 1u);
-    mma_tf32<TN>(dtmem, mat_desc(ah + o), mat_desc(bl + o), 1u);
-    mma_tf32<TN>(dtmem, mat_desc(al + o), mat_desc(bh + o), 1u);
+    mma_split<TN, BF>(dtmem, mat_desc<BF>(ah + o), mat_desc<BF>(bh + o), (first && ks == 0) ? 0u : 1u);
+    mma_split<TN, BF>(dtmem, mat_desc<BF>(ah + o), mat_desc<BF>(bl + o), 1u);
+    mma_split<TN, BF>(dtmem, mat_desc<BF>(al + o), mat_desc<BF>(bh + o), 1u);
   }
   mma_commit(bar);
 }
@@ -209,10 +253,10 @@ __device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char*
 // accumulator group when that commit is the group's last; one block barrier
 // per chunk hands the stage to the issuing thread. A lost wait sets s_fail,
 // which every thread reads after that barrier, so all leave the loop together.
-template <int TN, typename Regs, typename Load, typename Store>
+template <int TN, bool BF, typename Regs, typename Load, typename Store>
 __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int nchunks,
-                                            float (&acc)[Tile<TN>::NACC], Load load, Store store) {
-  using T = Tile<TN>;
+                                            float (&acc)[Tile<TN, BF>::NACC], Load load, Store store) {
+  using T = Tile<TN, BF>;
   constexpr int NS = T::NSTAGE;
   const int tid = threadIdx.x, w = tid >> 5;
   const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(T::NACC * (w >> 2));
@@ -255,7 +299,7 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
     const int group = c / kGroup;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      issue_chunk<TN>(tmem + (uint32_t)(TN * (group & 1)), st, &S.bar[s], (c % kGroup) == 0);
+      issue_chunk<TN, BF>(tmem + (uint32_t)(TN * (group & 1)), st, &S.bar[s], (c % kGroup) == 0);
     }
     issued |= 1u << s;
     if ((c % kGroup) == kGroup - 1 || c == nchunks - 1) drain |= (1u + (unsigned)(group & 1)) << (2 * s);
@@ -303,16 +347,16 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
 // Grid: (ceil(na/128), ceil(nb/BB), splits). part is FP64 complex [splits][na][nb].
 // Chunk element e (A: 0..1023, B: 0..8 BB - 1) -> row 8 (e / 64) + e % 8, complex
 // pair (e / 8) % 8 (four real K terms).
-template <int TN>
+template <int TN, bool BF>
 __global__ void __launch_bounds__(THREADS, 1)
 gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ B, int nb, long long ld,
                long long ng, double* __restrict__ part, long long chunk, int* status) {
-  using T = Tile<TN>;
+  using T = Tile<TN, BF>;
   constexpr int BB = T::BB, NACC = T::NACC;
   constexpr int NBE = 8 * BB;                           // B float4 elements per chunk
   constexpr int NBT = (NBE + THREADS - 1) / THREADS;    // per thread
   extern __shared__ unsigned char smem_raw[];
-  TcState S = tc_setup<TN>(smem_raw);
+  TcState S = tc_setup<TN, BF>(smem_raw);
   const uint32_t tmem = *S.tmem_slot;
   const int tid = threadIdx.x;
   const int a0 = blockIdx.x * TM, b0 = blockIdx.y * BB;
@@ -348,9 +392,9 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
     for (int i = 0; i < 2; ++i) {
       int r, q;
       rowq(tid + THREADS * i, r, q);
-      split_store(st, st + OPA_BYTES, tile_off(r, 4 * q), Rg.a[i]);
+      split_store<BF>(st, st + T::OPA_BYTES, tile_off<BF>(r, 4 * q), Rg.a[i]);
     }
-    unsigned char* bh = st + 2 * OPA_BYTES;
+    unsigned char* bh = st + 2 * T::OPA_BYTES;
     unsigned char* bl = bh + T::OPB_BYTES;
 #pragma unroll
     for (int i = 0; i < NBT; ++i) {
@@ -359,13 +403,13 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
         int r, q;
         rowq(e, r, q);
         const float4 vb = Rg.b[i];
-        split_store(bh, bl, tile_off(r, 4 * q), vb);
-        split_store(bh, bl, tile_off(r + BB, 4 * q), make_float4(vb.y, -vb.x, vb.w, -vb.z));
+        split_store<BF>(bh, bl, tile_off<BF>(r, 4 * q), vb);
+        split_store<BF>(bh, bl, tile_off<BF>(r + BB, 4 * q), make_float4(vb.y, -vb.x, vb.w, -vb.z));
       }
     }
   };
   float acc[NACC];
-  const bool ok = tc_mainloop<TN, Regs>(S, tmem, nchunks, acc, load, store);
+  const bool ok = tc_mainloop<TN, BF, Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -1;
@@ -379,23 +423,23 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
     for (int j = 0; j < NACC; ++j)
       if (b0 + bq + j < nb) out[2 * (b0 + bq + j)] = (double)acc[j];
   }
-  tc_teardown<TN>(tmem);
+  tc_teardown<TN, BF>(tmem);
 }
 
 // ---------------------------------------------------------------- outer
 // Grid: (ceil(nb/BB), ceil(ng/128)). C: FP64 complex [nk][nb].
 // A element e (0..1023): grid point g0 + e % 128, K pair e / 128 (k = 2 (e / 128)).
 // B element e (0..8 BB - 1): b = b0 + e % BB, K pair e / BB.
-template <int TN>
+template <int TN, bool BF>
 __global__ void __launch_bounds__(THREADS, 1)
 outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
                 long long ng, double alpha, float* __restrict__ Out, int* status) {
-  using T = Tile<TN>;
+  using T = Tile<TN, BF>;
   constexpr int BB = T::BB, NACC = T::NACC;
   constexpr int NBE = 8 * BB;
   constexpr int NBT = (NBE + THREADS - 1) / THREADS;
   extern __shared__ unsigned char smem_raw[];
-  TcState S = tc_setup<TN>(smem_raw);
+  TcState S = tc_setup<TN, BF>(smem_raw);
   const uint32_t tmem = *S.tmem_slot;
   const int tid = threadIdx.x;
   const int b0 = blockIdx.x * BB;
@@ -438,22 +482,22 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
       const int e = tid + THREADS * i, r = e & 127, kq = 4 * (e >> 7);
-      split_store(st, st + OPA_BYTES, tile_off(r, kq), Rg.a[i]);
+      split_store<BF>(st, st + T::OPA_BYTES, tile_off<BF>(r, kq), Rg.a[i]);
     }
-    unsigned char* bh = st + 2 * OPA_BYTES;
+    unsigned char* bh = st + 2 * T::OPA_BYTES;
     unsigned char* bl = bh + T::OPB_BYTES;
 #pragma unroll
     for (int i = 0; i < NBT; ++i) {
       const int e = tid + THREADS * i, j = e % BB, kq = 4 * (e / BB);
       if (e < NBE) {
         const float4 v = Rg.c[i];
-        split_store(bh, bl, tile_off(j, kq), make_float4(v.x, -v.y, v.z, -v.w));
-        split_store(bh, bl, tile_off(j + BB, kq), make_float4(v.y, v.x, v.w, v.z));
+        split_store<BF>(bh, bl, tile_off<BF>(j, kq), make_float4(v.x, -v.y, v.z, -v.w));
+        split_store<BF>(bh, bl, tile_off<BF>(j + BB, kq), make_float4(v.y, v.x, v.w, v.z));
       }
     }
   };
   float acc[NACC];
-  const bool ok = tc_mainloop<TN, Regs>(S, tmem, nchunks, acc, load, store);
+  const bool ok = tc_mainloop<TN, BF, Regs>(S, tmem, nchunks, acc, load, store);
   if (!ok && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -2;
@@ -466,7 +510,7 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
     for (int j = 0; j < NACC; ++j)
       if (b0 + bq + j < nb) Out[2 * ((long long)(b0 + bq + j) * ld + g) + ri] = (float)alpha * acc[j];
   }
-  tc_teardown<TN>(tmem);
+  tc_teardown<TN, BF>(tmem);
 }
 
 // Exact diagonal of the gram product: Mc[a][a] = (scale Re sum_g conj(A_a) B_a, 0),
@@ -524,19 +568,34 @@ int tc_width(int nb) {
   return best;
 }
 
-template <int TN> void set_smem(const void* k) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<TN>::SMEM_BYTES);
+template <int TN, bool BF> void set_smem() {
+  cudaFuncSetAttribute((const void*)gram_tc_kernel<TN, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Tile<TN, BF>::SMEM_BYTES);
+  cudaFuncSetAttribute((const void*)outer_tc_kernel<TN, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       Tile<TN, BF>::SMEM_BYTES);
+}
+
+template <int TN, bool BF>
+void gram_tn(dim3 grid, cudaStream_t st, const float2* a, int na, const float2* b, int nb, long long ld,
+             long long ng, double* part, long long chunk, int* status) {
+  gram_tc_kernel<TN, BF><<<grid, THREADS, Tile<TN, BF>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
+}
+
+template <int TN, bool BF>
+void outer_tn(dim3 grid, cudaStream_t st, const float2* a, int nk, const double* C, int nb, long long ld,
+              long long ng, double alpha, float* o, int* status) {
+  outer_tc_kernel<TN, BF><<<grid, THREADS, Tile<TN, BF>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
 }
 
 }  // namespace
 
 bool tc_gemm_prepare() {
-  set_smem<128>((const void*)gram_tc_kernel<128>);
-  set_smem<192>((const void*)gram_tc_kernel<192>);
-  set_smem<256>((const void*)gram_tc_kernel<256>);
-  set_smem<128>((const void*)outer_tc_kernel<128>);
-  set_smem<192>((const void*)outer_tc_kernel<192>);
-  set_smem<256>((const void*)outer_tc_kernel<256>);
+  set_smem<128, false>();
+  set_smem<192, false>();
+  set_smem<256, false>();
+  set_smem<128, true>();
+  set_smem<192, true>();
+  set_smem<256, true>();
   return cudaGetLastError() == cudaSuccess;
 }
 
@@ -551,27 +610,39 @@ int gram_tc_splits(long long ng, int na, int nb) {
 }
 
 void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, long long ng, double* part,
-                    int splits, int* status, cudaStream_t st) {
+                    int splits, int* status, cudaStream_t st, bool bf16) {
   long long chunk = (ng + splits - 1) / splits;
   chunk = (chunk + KC / 2 - 1) / (KC / 2) * (KC / 2);
   const int tn = tc_width(nb), bb = tn / 2;
   const dim3 grid((na + TM - 1) / TM, (nb + bb - 1) / bb, splits);
   const float2* a = static_cast<const float2*>(A);
   const float2* b = static_cast<const float2*>(B);
-  if (tn == 256) gram_tc_kernel<256><<<grid, THREADS, Tile<256>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
-  else if (tn == 192) gram_tc_kernel<192><<<grid, THREADS, Tile<192>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
-  else gram_tc_kernel<128><<<grid, THREADS, Tile<128>::SMEM_BYTES, st>>>(a, na, b, nb, ld, ng, part, chunk, status);
+  if (bf16) {
+    if (tn == 256) gram_tn<256, true>(grid, st, a, na, b, nb, ld, ng, part, chunk, status);
+    else if (tn == 192) gram_tn<192, true>(grid, st, a, na, b, nb, ld, ng, part, chunk, status);
+    else gram_tn<128, true>(grid, st, a, na, b, nb, ld, ng, part, chunk, status);
+  } else {
+    if (tn == 256) gram_tn<256, false>(grid, st, a, na, b, nb, ld, ng, part, chunk, status);
+    else if (tn == 192) gram_tn<192, false>(grid, st, a, na, b, nb, ld, ng, part, chunk, status);
+    else gram_tn<128, false>(grid, st, a, na, b, nb, ld, ng, part, chunk, status);
+  }
 }
 
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
-                     void* Out, int* status, cudaStream_t st) {
+                     void* Out, int* status, cudaStream_t st, bool bf16) {
   const int tn = tc_width(nb), bb = tn / 2;
   const dim3 grid((nb + bb - 1) / bb, (unsigned)((ng + TM - 1) / TM));
   const float2* a = static_cast<const float2*>(A);
   float* o = static_cast<float*>(Out);
-  if (tn == 256) outer_tc_kernel<256><<<grid, THREADS, Tile<256>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
-  else if (tn == 192) outer_tc_kernel<192><<<grid, THREADS, Tile<192>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
-  else outer_tc_kernel<128><<<grid, THREADS, Tile<128>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
+  if (bf16) {
+    if (tn == 256) outer_tn<256, true>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
+    else if (tn == 192) outer_tn<192, true>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
+    else outer_tn<128, true>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
+  } else {
+    if (tn == 256) outer_tn<256, false>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
+    else if (tn == 192) outer_tn<192, false>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
+    else outer_tn<128, false>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
+  }
 }
 
 size_t diag_dot_part_doubles(int na) { return (size_t)na * kDiagSplits; }

@@ -35,8 +35,10 @@
 // K runs in chunks of 32 real terms (16 orbitals) through three shared-memory
 // stages, each holding T - 1 A slices (split on the fly from the FP32 loads) and
 // the chunk's B slices (split once per call by oz_slice_b_kernel into the
-// stage layout, copied in with 16-byte loads). One thread issues the MMAs of a
-// chunk (2 K-steps per slice pair) and commits them to the stage's mbarrier;
+// stage layout, brought in by one bulk copy per chunk on the TMA unit, which
+// completes on the stage's second mbarrier). One thread issues the bulk copy
+// and, once it has landed, the MMAs of the chunk (2 K-steps per slice pair),
+// and commits them to the stage's first mbarrier;
 // the threads drain the accumulators after the last chunk of each group.
 // L^{-*} is upper triangular, so tile [b0, b0 + BB) runs k < b0 + BB only.
 // Every mbarrier wait is bounded: on timeout the CTA records ACE_ERR_TIMEOUT,
@@ -71,7 +73,7 @@ template <int T> struct Oz {
   static constexpr int A_SLICE = OZ_TM * OZ_KC * 2;
   static constexpr int B_SLICE = TN * OZ_KC * 2;
   static constexpr int STAGE = SA * A_SLICE + SB * B_SLICE;
-  static constexpr int SMEM = OZ_NSTAGE * STAGE + 1024 + 64;
+  static constexpr int SMEM = OZ_NSTAGE * STAGE + 1024 + 128;   // stages, alignment, 6 barriers + TMEM slot
   // instruction descriptor: D = F32, A = B = F16, both K-major, N = TN, M = 128
   static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(TN >> 3) << 17) | ((uint32_t)(OZ_TM >> 4) << 24);
 };
@@ -171,12 +173,16 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   constexpr int NACC = O::NACC;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(base + OZ_NSTAGE * O::STAGE);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + OZ_NSTAGE * O::STAGE + 32);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(base + OZ_NSTAGE * O::STAGE);        // MMAs of the stage done
+  uint64_t* full = bar + OZ_NSTAGE;                                                    // B slices of the stage landed
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + OZ_NSTAGE * O::STAGE + 64);
   __shared__ int s_fail;
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int i = 0; i < OZ_NSTAGE; ++i) tc::mbar_init(&bar[i], 1);
+    for (int i = 0; i < OZ_NSTAGE; ++i) {
+      tc::mbar_init(&bar[i], 1);
+      tc::mbar_init(&full[i], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
@@ -190,8 +196,9 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   const long long g0 = (long long)blockIdx.y * OZ_TM;
   const int kend = b0 + O::BB < nk ? b0 + O::BB : nk;
   const int nchunks = (kend + 15) / 16;
-  // this thread's A elements: row r = tid % 128, real K 4q .. 4q + 3 with q = tid / 128 and q + 4
-  const int r = tid & 127, q = tid >> 7;
+  // this thread's A elements: row r = 8 w + lane % 8, real K 4q .. 4q + 3 with q = lane / 8 and
+  // q + 4, so that a warp's 8-byte slice stores cover 256 contiguous bytes (no bank conflicts)
+  const int r = 8 * w + (lane & 7), q = lane >> 3;
   const long long g = g0 + r;
   const int er = g < ng ? erow[g] : 0;
   const float sa = ldexpf(1.0f, OZ_BETA - er);       // exact power of two
@@ -235,11 +242,11 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
       }
     }
   };
-  auto copy_b = [&](unsigned char* st, int c) {
-    const uint4* src = reinterpret_cast<const uint4*>(Bsl + (size_t)(bt * nch + c) * O::SB * (O::TN * OZ_KC));
-    uint4* dst = reinterpret_cast<uint4*>(st + O::SA * O::A_SLICE);
-    constexpr int N16 = O::SB * O::B_SLICE / 16;
-    for (int i = tid; i < N16; i += OZ_THREADS) dst[i] = src[i];
+  constexpr unsigned B_BYTES = O::SB * O::B_SLICE;
+  static_assert(B_BYTES % 16 == 0 && (O::SA * O::A_SLICE) % 16 == 0, "bulk copy alignment");
+  auto copy_b = [&](unsigned char* st, int c, int s) {   // thread 0
+    tc::mbar_arrive_expect_tx(&full[s], B_BYTES);
+    tc::bulk_g2s(st + O::SA * O::A_SLICE, Bsl + (size_t)(bt * nch + c) * O::SB * (O::TN * OZ_KC), B_BYTES, &full[s]);
   };
   auto issue = [&](const unsigned char* st, bool group_first) {
     const uint32_t a0 = tc::smem_u32(st), bb0 = a0 + O::SA * O::A_SLICE;
@@ -283,7 +290,14 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   };
 
   unsigned phase = 0, issued = 0;
+  unsigned fphase = 0, inflight = 0;   // thread 0: parity of each full barrier, bulk copies not yet seen
   bool ok = true;
+  auto landed = [&](int s) -> bool {   // thread 0: bounded wait for the bulk copy into stage s
+    if (!tc::mbar_wait(&full[s], (fphase >> s) & 1u, kOzWaitLimit)) return false;
+    fphase ^= 1u << s;
+    inflight &= ~(1u << s);
+    return true;
+  };
   auto settle = [&](int s) -> bool {
     if (!tc::mbar_wait(&bar[s], (phase >> s) & 1u, kOzWaitLimit)) return false;
     phase ^= 1u << s;
@@ -297,15 +311,22 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     unsigned char* st = base + s * O::STAGE;
     if (c + 1 < nchunks) load_a(c + 1, nxt);
     if (((issued >> s) & 1u) && !settle(s)) s_fail = 1;   // chunk c - NSTAGE read this stage
+    if (tid == 0 && !s_fail) {
+      copy_b(st, c, s);
+      inflight |= 1u << s;
+    }
     store_a(st, cur);
-    copy_b(st, c);
     tc::fence_async_smem();
     __syncthreads();
     if (s_fail) { ok = false; break; }
     if (tid == 0) {
-      tc::fence_after_sync();
-      issue(st, (c % OZ_GROUP) == 0);
-      tc::mma_commit(&bar[s]);
+      if (landed(s)) {
+        tc::fence_after_sync();
+        issue(st, (c % OZ_GROUP) == 0);
+        tc::mma_commit(&bar[s]);
+      } else {
+        s_fail = 1;   // seen by every thread after the next barrier; the stage's MMAs were not issued
+      }
     }
     issued |= 1u << s;
     if ((c % OZ_GROUP) == OZ_GROUP - 1 || c == nchunks - 1) {
@@ -319,9 +340,12 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     cur[0] = nxt[0];
     cur[1] = nxt[1];
   }
-  // commits still outstanding (bounded; also after a lost wait)
+  // commits and bulk copies still outstanding (bounded; also after a lost wait)
   for (int i = 0; i < OZ_NSTAGE; ++i)
     if (((issued >> i) & 1u) && !settle(i)) ok = false;
+  if (tid == 0)
+    for (int i = 0; i < OZ_NSTAGE; ++i)
+      if (((inflight >> i) & 1u) && !landed(i)) ok = false;
   __syncthreads();
   if ((!ok || s_fail) && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT

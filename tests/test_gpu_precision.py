@@ -7,6 +7,8 @@
   within 1e-10 (relative) in FP64 output; both against the FP64 oracle. On an
   ill-conditioned -M the TF32-split product (ACE_PREC_SPLIT_TF32) drifts from
   the FP64 product while the slice product does not.
+* ACE_PREC_SPLIT_BF16: M and the apply on BF16 tensor cores (hi/lo split),
+  against the oracle with their measured error.
 * ACE_PREC_FP32 is the CUDA-core FP32 path (bitwise the legacy flag).
 * A leading dimension ld > N_g: every entry point gives bitwise the packed
   results, and the elements between N_g and ld are never touched.
@@ -113,6 +115,38 @@ def test_xi_fp64_on_an_ill_conditioned_m(ace):
                  torch.linalg.vector_norm(res["xi_fp64_simt"]))
     print(f"ill-conditioned: TF32 split vs FP64 {d_tf32:.2e}, slices vs FP64 {d_oz:.2e} (max elementwise {worst:.2e})")
     assert ok and d_oz < 1e-7 and d_oz < d_tf32
+
+
+@pytest.mark.parametrize("n,L,nocc,nb,kernel,omega", [(24, 10.0, 13, 5, "erfc", 0.3),
+                                                      (48, 20.5, 128, 150, "erfc", 0.106),
+                                                      (20, 8.0, 40, 128, "bare", 0.0)])
+def test_split_bf16(ace, n, L, nocc, nb, kernel, omega):
+    """ACE_PREC_SPLIT_BF16: M = dV Phi^* W and the apply on BF16 tensor cores
+    with the hi/lo split (MMA widths 128, 192 and 256 by n_b and N). W is the
+    default plan's (same pair path), E_x is within FP32 rounding (the diagonal
+    of M is summed from FP32 products), and M, Xi and V_ACE psi stay within
+    1e-4 of the FP64 oracle (measured errors printed: about 2^-16 per product,
+    averaged over the N_g terms of each sum)."""
+    s, phi, psi = _inputs(n, L, nocc, nb, kernel, omega, seed=5200 + n)
+    kern = oracle.coulomb_kernel((n,) * 3, (L,) * 3, kernel, omega)
+    ref = oracle.ace_build(phi, kern, s.dv)
+    phi_d = torch.from_numpy(phi).to(torch.complex64).cuda()
+    psi_d = torch.from_numpy(psi).to(torch.complex64).cuda()
+    bf = ace.Plan(n, L, nocc, dtype="c64", kernel=kernel, omega=omega, prec="split_bf16")
+    tf = ace.Plan(n, L, nocc, dtype="c64", kernel=kernel, omega=omega)
+    ob, ot = bf.build(phi_d), tf.build(phi_d)
+    assert bf.status() == (0, 0)
+    assert torch.equal(ob["W"], ot["W"])
+    assert abs(ob["Ex"].item() - ref["Ex"]) < 1e-6 * abs(ref["Ex"])
+    e_m = rel(_host(ob["M"]), ref["M"])
+    e_xi = rel(_host(ob["Xi"]), ref["Xi"])
+    y = bf.apply(ob["Xi"], psi_d)
+    e_y = rel(_host(y), oracle.ace_apply(ref["Xi"], psi, s.dv))
+    e_m_tf = rel(_host(ot["M"]), ref["M"])
+    print(f"{n}^3 N={nocc} n_b={nb}: split_bf16 M {e_m:.2e} (TF32 split {e_m_tf:.2e}), Xi {e_xi:.2e}, "
+          f"apply {e_y:.2e}")
+    assert e_m < 1e-4 and e_xi < 1e-4 and e_y < 1e-4
+    assert e_m > e_m_tf                                  # BF16 really ran: coarser than TF32
 
 
 def test_prec_fp32_is_the_cuda_core_path(ace):
