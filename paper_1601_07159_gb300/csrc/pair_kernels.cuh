@@ -835,9 +835,9 @@ __device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)
     y[H + j] = csub(ev, t);
   }
 }
-// Pass B for the large pencils (n_z >= 64), whose whole pencil per thread
-// spills: two lanes per z-pencil (lanes 2q, 2q+1 of a warp; 128 pencils per
-// block). Lane h holds the samples z = 2m + h and transforms them with a DFT of
+// Pass B for the large FP64 pencils (n_z >= 64), whose whole pencil per thread
+// spills (FP32 pencils of 64 and 96 take the four-warp form, pass_b_quad_kernel):
+// two lanes per z-pencil (lanes 2q, 2q+1 of a warp; 128 pencils per block). Lane h holds the samples z = 2m + h and transforms them with a DFT of
 // N/2:
 //   forward  Y[k] = E[k] + w^k O[k], Y[k + N/2] = E[k] - w^k O[k]
 //            (E, O the half-length transforms of the even / odd samples,
@@ -852,9 +852,10 @@ __device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)
 // thread per pencil.
 constexpr int kBSplitPencils = 128;   // pencils per 256-thread block of the split pass B
 // FP64 pencils of 64+ points need the whole register file of a thread: one
-// block per SM. FP32 pencils of 96 points spill a few hundred bytes at two
-// blocks per SM, which measured faster than one block without spills
-// (25.7 vs 31.7 ms of pass B per 96^3 build of 128 orbitals).
+// block per SM. (For FP32 pencils of 96 this form spilled a few hundred bytes
+// at two blocks per SM, still faster than one block without spills: 25.7 vs
+// 31.7 ms of pass B per 96^3 build of 128 orbitals; the four-warp form takes
+// 19.3 ms.)
 template <typename R, int N> constexpr int kBSplitBlocks = sizeof(R) == 8 ? 1 : 2;
 template <int NZ> constexpr bool kSplitPencil = NZ >= 64 && NZ % 4 == 0;
 
@@ -1099,7 +1100,7 @@ __device__ __forceinline__ void quad_combine(const cplx<R>* __restrict__ buf, in
   }
 }
 
-// Pass B with four warps per 32 pencils (FP32 pencils of 96): warp h holds the
+// Pass B with four warps per 32 pencils (FP32 pencils of 64 and 96): warp h holds the
 // samples z = 4m + h of its lane's pencil, transforms them (quad_sub_dft) and
 // stores them to shared memory; after a barrier each thread forms the radix-4
 // combination for its M/4 frequencies k = hM/4 + j, which gives it the 24
@@ -1111,7 +1112,7 @@ __device__ __forceinline__ void quad_combine(const cplx<R>* __restrict__ buf, in
 // thus needs a quarter of it in registers per thread (no spills, where the
 // two-lane form spills at two blocks per SM) and no shuffles.
 constexpr int kQuadPencils = 32;   // pencils per 128-thread block of the four-warp pass B
-template <typename R, int NZ> constexpr bool kQuadPencil = sizeof(R) == 4 && NZ == 96;
+template <typename R, int NZ> constexpr bool kQuadPencil = sizeof(R) == 4 && (NZ == 96 || NZ == 64);
 
 // u[4j + h'] *= w_N^{-h'(HQ + j)} (inverse twiddles of warp phase H)
 template <int N, int H, typename R>

@@ -162,8 +162,9 @@ oz_slice_b_kernel(const double* __restrict__ C, int nk, int nb, int nch, unsigne
   }
 }
 
-// Grid: (ceil(nb / BB), ceil(ng / 128)). A: complex FP32 [nk][ld]; Out: complex
-// FP32 or FP64 [nb][ld].
+// Grid: one CTA per SM (or fewer), each taking the (column tile, 128-row
+// block) tiles blockIdx.x, blockIdx.x + gridDim.x, ... A: complex FP32 [nk][ld];
+// Out: complex FP32 or FP64 [nb][ld].
 template <int T, typename OUT>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
 oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long long ng,
@@ -192,21 +193,18 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  const int bt = blockIdx.x, b0 = bt * O::BB;
-  const long long g0 = (long long)blockIdx.y * OZ_TM;
-  const int kend = b0 + O::BB < nk ? b0 + O::BB : nk;
-  const int nchunks = (kend + 15) / 16;
+  // tiles (column tile bt, 128-row block) in bt-fastest order, strided over the
+  // resident CTAs (persistent: setup, TMEM allocation and barriers once per CTA)
+  const int nbt = (nb + O::BB - 1) / O::BB;
+  const long long ntiles = (long long)nbt * ((ng + OZ_TM - 1) / OZ_TM);
+  int bt = 0, b0 = 0, kend = 0, nchunks = 0;
+  long long g0 = 0, g = 0;
+  float sa = 1.f;
   // this thread's A elements: row r = 8 w + lane % 8, real K 4q .. 4q + 3 with q = lane / 8 and
   // q + 4, so that a warp's 8-byte slice stores cover 256 contiguous bytes (no bank conflicts)
   const int r = 8 * w + (lane & 7), q = lane >> 3;
-  const long long g = g0 + r;
-  const int er = g < ng ? erow[g] : 0;
-  const float sa = ldexpf(1.0f, OZ_BETA - er);       // exact power of two
   const uint32_t lane_col = ((uint32_t)(32 * (w & 3)) << 16) + (uint32_t)(NACC * (w >> 2));
-
   long long acc[NACC];
-#pragma unroll
-  for (int j = 0; j < NACC; ++j) acc[j] = 0;
 
   auto load_a = [&](int c, float4 (&v)[2]) {
 #pragma unroll
@@ -305,41 +303,72 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     return true;
   };
   float4 cur[2], nxt[2];
-  if (nchunks > 0) load_a(0, cur);
-  for (int c = 0; c < nchunks; ++c) {
-    const int s = c % OZ_NSTAGE;
-    unsigned char* st = base + s * O::STAGE;
-    if (c + 1 < nchunks) load_a(c + 1, nxt);
-    if (((issued >> s) & 1u) && !settle(s)) s_fail = 1;   // chunk c - NSTAGE read this stage
-    if (tid == 0 && !s_fail) {
-      copy_b(st, c, s);
-      inflight |= 1u << s;
-    }
-    store_a(st, cur);
-    tc::fence_async_smem();
-    __syncthreads();
-    if (s_fail) { ok = false; break; }
-    if (tid == 0) {
-      if (landed(s)) {
-        tc::fence_after_sync();
-        issue(st, (c % OZ_GROUP) == 0);
-        tc::mma_commit(&bar[s]);
-      } else {
-        s_fail = 1;   // seen by every thread after the next barrier; the stage's MMAs were not issued
+  int cc = 0;                          // chunks issued by this CTA (stage rotation)
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    bt = (int)(tile % nbt);
+    b0 = bt * O::BB;
+    g0 = (tile / nbt) * OZ_TM;
+    kend = b0 + O::BB < nk ? b0 + O::BB : nk;
+    nchunks = (kend + 15) / 16;
+    g = g0 + r;
+    sa = ldexpf(1.0f, OZ_BETA - (g < ng ? erow[g] : 0));   // exact power of two
+#pragma unroll
+    for (int j = 0; j < NACC; ++j) acc[j] = 0;
+    if (nchunks > 0) load_a(0, cur);
+    for (int c = 0; c < nchunks; ++c, ++cc) {
+      const int s = cc % OZ_NSTAGE;
+      unsigned char* st = base + s * O::STAGE;
+      if (c + 1 < nchunks) load_a(c + 1, nxt);
+      if (((issued >> s) & 1u) && !settle(s)) s_fail = 1;   // chunk c - NSTAGE read this stage
+      if (tid == 0 && !s_fail) {
+        copy_b(st, c, s);
+        inflight |= 1u << s;
       }
-    }
-    issued |= 1u << s;
-    if ((c % OZ_GROUP) == OZ_GROUP - 1 || c == nchunks - 1) {
-      // every MMA so far has completed; the warp drains only if all its threads saw it
-      const bool seen = __all_sync(0xffffffffu, settle(s));
-      if (seen) drain();
-      else s_fail = 1;
+      store_a(st, cur);
+      tc::fence_async_smem();
       __syncthreads();
       if (s_fail) { ok = false; break; }
+      if (tid == 0) {
+        if (landed(s)) {
+          tc::fence_after_sync();
+          issue(st, (c % OZ_GROUP) == 0);
+          tc::mma_commit(&bar[s]);
+        } else {
+          s_fail = 1;   // seen by every thread after the next barrier; the stage's MMAs were not issued
+        }
+      }
+      issued |= 1u << s;
+      if ((c % OZ_GROUP) == OZ_GROUP - 1 || c == nchunks - 1) {
+        // every MMA so far has completed; the warp drains only if all its threads saw it
+        const bool seen = __all_sync(0xffffffffu, settle(s));
+        if (seen) drain();
+        else s_fail = 1;
+        __syncthreads();
+        if (s_fail) { ok = false; break; }
+      }
+      cur[0] = nxt[0];
+      cur[1] = nxt[1];
     }
-    cur[0] = nxt[0];
-    cur[1] = nxt[1];
-  }
+    if (!ok) break;
+    {   // the tile's outputs
+      const int row = 32 * (w & 3) + lane;
+      const long long gg = g0 + row;
+      const int ergg = gg < ng ? erow[gg] : 0;
+      const int ri = (w >> 2) >= 2 ? 1 : 0;                 // column groups 0-1 real, 2-3 imaginary
+      const int jq = ((w >> 2) & 1) * NACC;
+      if (gg < ng) {
+#pragma unroll
+        for (int j = 0; j < NACC; ++j) {
+          const int b = b0 + jq + j;
+          if (b < nb) {
+            const double val = ldexp((double)acc[j], ergg + fcol[b] - OZ_BETA * T);
+            if constexpr (sizeof(OUT) == 8) reinterpret_cast<float*>(Out)[2 * ((long long)b * ld + gg) + ri] = (float)val;
+            else reinterpret_cast<double*>(Out)[2 * ((long long)b * ld + gg) + ri] = val;
+          }
+        }
+      }
+    }
+  }   // tiles
   // commits and bulk copies still outstanding (bounded; also after a lost wait)
   for (int i = 0; i < OZ_NSTAGE; ++i)
     if (((issued >> i) & 1u) && !settle(i)) ok = false;
@@ -350,24 +379,6 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   if ((!ok || s_fail) && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
     status[1] = -3;
-  }
-  if (ok && !s_fail) {
-    const int row = 32 * (w & 3) + lane;
-    const long long gg = g0 + row;
-    const int ergg = gg < ng ? erow[gg] : 0;
-    const int ri = (w >> 2) >= 2 ? 1 : 0;                 // column groups 0-1 real, 2-3 imaginary
-    const int jq = ((w >> 2) & 1) * NACC;
-    if (gg < ng) {
-#pragma unroll
-      for (int j = 0; j < NACC; ++j) {
-        const int b = b0 + jq + j;
-        if (b < nb) {
-          const double val = ldexp((double)acc[j], ergg + fcol[b] - OZ_BETA * T);
-          if constexpr (sizeof(OUT) == 8) reinterpret_cast<float*>(Out)[2 * ((long long)b * ld + gg) + ri] = (float)val;
-          else reinterpret_cast<double*>(Out)[2 * ((long long)b * ld + gg) + ri] = val;
-        }
-      }
-    }
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -413,7 +424,10 @@ int launch_xi_oz(const void* A, int nk, const double* C, int nb, long long ld, l
   using O = Oz<kOzT>;
   cudaMemsetAsync(bsl, 0, oz_bsl_bytes<kOzT>(nk, nb), st);
   oz_slice_b_kernel<kOzT><<<nb, 256, 0, st>>>(C, nk, nb, nch, bsl, fcol);
-  const dim3 grid((nb + O::BB - 1) / O::BB, (unsigned)((ng + OZ_TM - 1) / OZ_TM));
+  const long long ntiles = (long long)((nb + O::BB - 1) / O::BB) * ((ng + OZ_TM - 1) / OZ_TM);
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const dim3 grid((unsigned)(ntiles < sms ? ntiles : sms));   // one resident CTA per SM
   if (out_f64)
     oz_outer_kernel<kOzT, double2><<<grid, OZ_THREADS, O::SMEM, st>>>(a, nk, nb, ld, ng, erow, bsl, fcol, nch,
                                                                        static_cast<double2*>(Out), status);
