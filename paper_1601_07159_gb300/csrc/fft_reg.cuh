@@ -35,6 +35,21 @@ template <typename T> __device__ __forceinline__ T cmulc(T a, T b) {
   return cmk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 template <typename T> __device__ __forceinline__ T cscale(T a, decltype(T::x) s) { return cmk<T>(a.x * s, a.y * s); }
+// acc + a b and acc + conj(a) b as four fused multiply-adds (accumulations)
+template <typename T> __device__ __forceinline__ T cfma(T acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+template <typename T> __device__ __forceinline__ T cfmac(T acc, T a, T b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
 // multiply by -i (forward) or +i (inverse) -> "rotate by the forward quarter turn"
 template <bool INV, typename T> __device__ __forceinline__ T rot_q(T a) {
   return INV ? cmk<T>(-a.y, a.x) : cmk<T>(a.y, -a.x);

@@ -166,7 +166,8 @@ bool launch_engine_f64(const PairLaunch& L, const EngineLaunch& E, cudaStream_t 
 
 int energy_blocks(int nx, int ny, int nz, int npairs) {
   // pass B: one energy partial per block (256 pencils; 128 for the two-lane form of
-  // n_z >= 64; 32 for the four-warp form of n_z = 64 and 96, counted for either precision)
+  // n_z >= 64; 32 for the four-warp form of n_z = 64 and 96, counted for either
+  // precision)
   const long long pencils = (long long)npairs * nx * ny;
   const int per = (nz == 64 || nz == 96) ? 32 : (nz >= 64 && nz % 4 == 0) ? 128 : 256;
   return (int)((pencils + per - 1) / per);

@@ -421,8 +421,8 @@ __device__ __forceinline__ void d_full_diag(const PointParams<R>& P, const TileD
     for (int ri = li; ri < B; ++ri) {
       const int q = li * B - li * (li - 1) / 2 + (ri - li);
       const cplx<R> v = __ldcs(V + (long long)q * NG);
-      acc[ri] = cadd(acc[ri], cmul(x[li], v));
-      if (ri != li) acc[li] = cadd(acc[li], cmulc(v, x[ri]));
+      acc[ri] = cfma(acc[ri], x[li], v);
+      if (ri != li) acc[li] = cfmac(acc[li], v, x[ri]);
     }
   }
 #pragma unroll
@@ -447,8 +447,8 @@ __device__ __forceinline__ void d_full_off(const PointParams<R>& P, const TileDe
 #pragma unroll
     for (int ri = 0; ri < B; ++ri) {
       const cplx<R> v = __ldcs(V + (long long)(li * B + ri) * NG);
-      ar[ri] = cadd(ar[ri], cmul(xl[li], v));
-      al[li] = cadd(al[li], cmulc(v, yr[ri]));
+      ar[ri] = cfma(ar[ri], xl[li], v);
+      al[li] = cfmac(al[li], v, yr[ri]);
     }
   }
 #pragma unroll
@@ -493,8 +493,8 @@ __device__ __forceinline__ void d_split_off(const PointParams<R>& P, const TileD
 #pragma unroll
       for (int ri = 0; ri < H; ++ri) {
         const cplx<R> v = __ldcs(V + (long long)(li * B + h * H + ri) * NG);
-        ar[ri] = cadd(ar[ri], cmul(xl[li], v));
-        al[li] = cadd(al[li], cmulc(v, yr[ri]));
+        ar[ri] = cfma(ar[ri], xl[li], v);
+        al[li] = cfmac(al[li], v, yr[ri]);
       }
     }
   }
@@ -541,8 +541,8 @@ __device__ __forceinline__ void body_d_cplx(const PointParams<R>& P, const TileD
         if (li < d.nl && ri < d.nl) {
           const cplx<R> v = ldx<COH>(V + (long long)q * NG);
           ++q;
-          acc[ri] = cadd(acc[ri], cmul(x[li], v));
-          if (ri != li) acc[li] = cadd(acc[li], cmulc(v, x[ri]));   // x_r conj(v)
+          acc[ri] = cfma(acc[ri], x[li], v);
+          if (ri != li) acc[li] = cfmac(acc[li], v, x[ri]);   // x_r conj(v)
         }
       }
     }
@@ -564,8 +564,8 @@ __device__ __forceinline__ void body_d_cplx(const PointParams<R>& P, const TileD
       for (int ri = 0; ri < kTileMax; ++ri) {
         if (li < d.nl && ri < d.nr) {
           const cplx<R> v = ldx<COH>(V + (long long)(li * d.nr + ri) * NG);
-          ar[ri] = cadd(ar[ri], cmul(xl[li], v));
-          al[li] = cadd(al[li], cmulc(v, yr[ri]));
+          ar[ri] = cfma(ar[ri], xl[li], v);
+          al[li] = cfmac(al[li], v, yr[ri]);
         }
       }
     }
@@ -584,7 +584,7 @@ __device__ __forceinline__ void body_d_cplx(const PointParams<R>& P, const TileD
       for (int ri = 0; ri < kTileMax; ++ri) {
         if (ri < d.nr) {
           const cplx<R> v = ldx<COH>(V + (long long)(li * d.nr + ri) * NG);
-          ar[ri] = cadd(ar[ri], cmul(xv, v));
+          ar[ri] = cfma(ar[ri], xv, v);
         }
       }
     }
@@ -936,7 +936,8 @@ template <typename R, int NX, int NY> constexpr bool kSplitPlanes =
     NX % 4 == 0 && NY % 4 == 0 &&
     (sizeof(R) == 4 ? kMaxLine<NX, NY> >= kSplitMinEdge : kMaxLine<NX, NY> >= kSplitMinEdgeF64);
 template <typename R, int NX, int NY> constexpr int kSplitBlocks =
-    sizeof(R) == 8 ? (kMaxLine<NX, NY> >= 96 ? 1 : 2) : (kMaxLine<NX, NY> >= 96 ? 2 : 6);
+    sizeof(R) == 8 ? (kMaxLine<NX, NY> >= 96 ? 1 : 2)
+                   : (kMaxLine<NX, NY> >= 96 ? 2 : kMaxLine<NX, NY> >= 64 ? 4 : 6);
 template <typename R, int NX, int NY> constexpr int kSplitBlocksA =
     sizeof(R) == 4 && NX == 48 && NY == 48 ? 8 : kSplitBlocks<R, NX, NY>;
 template <typename R, int NX, int NY> constexpr size_t kSplitSmem = (size_t)NY * (NX + 1) * sizeof(cplx<R>);
@@ -1112,6 +1113,8 @@ __device__ __forceinline__ void quad_combine(const cplx<R>* __restrict__ buf, in
 // thus needs a quarter of it in registers per thread (no spills, where the
 // two-lane form spills at two blocks per SM) and no shuffles.
 constexpr int kQuadPencils = 32;   // pencils per 128-thread block of the four-warp pass B
+// (At n_z = 48 the whole pencil per thread measured faster: 2.63 vs 2.84 ps per
+// pair-point.)
 template <typename R, int NZ> constexpr bool kQuadPencil = sizeof(R) == 4 && (NZ == 96 || NZ == 64);
 
 // u[4j + h'] *= w_N^{-h'(HQ + j)} (inverse twiddles of warp phase H)
@@ -1199,8 +1202,10 @@ pass_b_quad_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
   }
 }
 
+// FP64 pencils of 48 hold 96 doubles: one block per SM (two would cap a thread
+// at 128 registers and spill about 3 KB).
 template <typename R, int NZ, bool CUBE>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : 2)
 pass_b_kernel(const __grid_constant__ PencilParams<R, NZ> P, int mode) {
   __shared__ double red[32];
   griddep_launch();
@@ -1223,6 +1228,16 @@ pass_c_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
 // four blocks per SM (64 registers): more warps and loads in flight per SM,
 // which measured faster than one thread per point at 2 or 3 blocks per SM
 // (and than streaming the potentials through shared memory with bulk copies).
+// The tiles other than full off-diagonal ones (diagonal, ragged, one-sided):
+// one thread per point, 256 points per block (the grid is sized for 128-point
+// blocks, so the upper half of the blocks has no work). Not inlined, so that
+// its larger register state does not spill into the full-tile path.
+template <typename R, bool REAL, long long NGC>
+__device__ __noinline__ void pass_d_other(const PointParams<R>& P, const TileDesc& d) {
+  if ((long long)blockIdx.x * 256 >= (NGC ? NGC : P.ng)) return;
+  body_d<R, REAL, false, false, NGC>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
 template <typename R, bool REAL, long long NGC>
 __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 4 : 2)
 pass_d_kernel(const __grid_constant__ PointParams<R> P) {
@@ -1235,10 +1250,7 @@ pass_d_kernel(const __grid_constant__ PointParams<R> P) {
     else d_split_off<R, REAL, NGC>(P, d, blockIdx.x, threadIdx.x, xch);
     return;
   }
-  // other tiles: one thread per point, 256 points per block (the grid is
-  // sized for 128-point blocks, so the upper half of the blocks has no work)
-  if ((long long)blockIdx.x * 256 >= (NGC ? NGC : P.ng)) return;
-  body_d<R, REAL, false, false, NGC>(P, d, blockIdx.x, threadIdx.x, blockDim.x);
+  pass_d_other<R, REAL, NGC>(P, d);
 }
 
 // ---------------------------------------------------------------- persistent engine
