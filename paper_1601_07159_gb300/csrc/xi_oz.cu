@@ -85,6 +85,13 @@ __device__ __forceinline__ int oz_off(int r, int k) {
 
 __device__ __forceinline__ unsigned short f16_bits(float d) { return __half_as_ushort(__float2half_rn(d)); }
 
+// rint(x) for |x| < 2^22 by two full-rate additions: adding 1.5 * 2^23 rounds x
+// to an integer (round to nearest, ties to even, as rint) in the low mantissa
+// bits, and subtracting it again is exact.
+__device__ __forceinline__ float round_int(float x) {
+  return __fadd_rn(__fadd_rn(x, 12582912.0f), -12582912.0f);
+}
+
 template <int T>
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
   asm volatile(
@@ -196,9 +203,9 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   // tiles (column tile bt, 128-row block) in bt-fastest order, strided over the
   // resident CTAs (persistent: setup, TMEM allocation and barriers once per CTA)
   const int nbt = (nb + O::BB - 1) / O::BB;
-  const long long ntiles = (long long)nbt * ((ng + OZ_TM - 1) / OZ_TM);
+  const int ntiles = nbt * (int)((ng + OZ_TM - 1) / OZ_TM);   // < 2^31 for every supported grid
   int bt = 0, b0 = 0, kend = 0, nchunks = 0;
-  long long g0 = 0, g = 0;
+  int g0 = 0, g = 0;
   float sa = 1.f;
   // this thread's A elements: row r = 8 w + lane % 8, real K 4q .. 4q + 3 with q = lane / 8 and
   // q + 4, so that a warp's 8-byte slice stores cover 256 contiguous bytes (no bank conflicts)
@@ -226,16 +233,16 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
       const int off = oz_off(r, 4 * (q + 4 * i));
 #pragma unroll
       for (int s = 0; s < O::SA; ++s) {
-        unsigned short h[4];
+        float d[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const float d = rintf(x[e]);
-          x[e] = (x[e] - d) * (float)(1 << OZ_BETA);
-          h[e] = f16_bits(d);
+          d[e] = round_int(x[e]);
+          x[e] = (x[e] - d[e]) * (float)(1 << OZ_BETA);
         }
+        const __half2 h01 = __floats2half2_rn(d[0], d[1]), h23 = __floats2half2_rn(d[2], d[3]);   // exact
         uint2 u;
-        u.x = (uint32_t)h[0] | ((uint32_t)h[1] << 16);
-        u.y = (uint32_t)h[2] | ((uint32_t)h[3] << 16);
+        u.x = *reinterpret_cast<const uint32_t*>(&h01);
+        u.y = *reinterpret_cast<const uint32_t*>(&h23);
         *reinterpret_cast<uint2*>(st + s * O::A_SLICE + off) = u;
       }
     }
@@ -304,8 +311,8 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
   };
   float4 cur[2], nxt[2];
   int cc = 0;                          // chunks issued by this CTA (stage rotation)
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    bt = (int)(tile % nbt);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    bt = tile % nbt;
     b0 = bt * O::BB;
     g0 = (tile / nbt) * OZ_TM;
     kend = b0 + O::BB < nk ? b0 + O::BB : nk;
