@@ -61,8 +61,12 @@ UNIT = "pair-solves/s"
 # the current kernels on the default schedule, scaled from the captured pair
 # batches to a whole build (workload -> (bytes, how it was taken)).
 TRAFFIC = {
-    SI64: (27.05e9, "ncu dram__bytes_read.sum + dram__bytes_write.sum of passes A-D on one warm 64-pair "
-                    "batch at 48^3 (209.7 MB), x 129 batch equivalents of the default schedule"),
+    LARGE: (25.80e12, "ncu dram__bytes_read.sum + dram__bytes_write.sum (--cache-control none) of passes A-D "
+                      "on one off-diagonal 64-pair batch of the 96^3 grid (3146 MB; profile_run --n 96 --n-occ 24 "
+                      "--eager, second batch), x 8200 batch equivalents (524,800 pairs / 64)"),
+    SI64: (12.07e9, "ncu dram__bytes_read.sum + dram__bytes_write.sum (--cache-control none) of passes A-D "
+                    "on the second off-diagonal 64-pair batch at 48^3 (93.5 MB; profile_run --n 48 --n-occ 128 "
+                    "--eager), x 129 batch equivalents (8256 pairs / 64)"),
 }
 
 

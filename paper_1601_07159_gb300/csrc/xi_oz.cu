@@ -294,16 +294,18 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     tc::fence_before_sync();
   };
 
+  // Thread 0 alone waits on the barriers: the MMA commits (bit s of `issued`:
+  // a commit on stage s not yet seen) and the bulk copies (`inflight`).
   unsigned phase = 0, issued = 0;
-  unsigned fphase = 0, inflight = 0;   // thread 0: parity of each full barrier, bulk copies not yet seen
+  unsigned fphase = 0, inflight = 0;
   bool ok = true;
-  auto landed = [&](int s) -> bool {   // thread 0: bounded wait for the bulk copy into stage s
+  auto landed = [&](int s) -> bool {   // bounded wait for the bulk copy into stage s
     if (!tc::mbar_wait(&full[s], (fphase >> s) & 1u, kOzWaitLimit)) return false;
     fphase ^= 1u << s;
     inflight &= ~(1u << s);
     return true;
   };
-  auto settle = [&](int s) -> bool {
+  auto settle = [&](int s) -> bool {   // bounded wait for the MMAs last committed on stage s
     if (!tc::mbar_wait(&bar[s], (phase >> s) & 1u, kOzWaitLimit)) return false;
     phase ^= 1u << s;
     issued &= ~(1u << s);
@@ -323,16 +325,21 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     for (int j = 0; j < NACC; ++j) acc[j] = 0;
     if (nchunks > 0) load_a(0, cur);
     for (int c = 0; c < nchunks; ++c, ++cc) {
+      // stage s is free: thread 0 saw its previous MMAs (chunk cc - 3) complete
+      // before the barrier of chunk cc - 1, or at the last drain
       const int s = cc % OZ_NSTAGE;
       unsigned char* st = base + s * O::STAGE;
       if (c + 1 < nchunks) load_a(c + 1, nxt);
-      if (((issued >> s) & 1u) && !settle(s)) s_fail = 1;   // chunk c - NSTAGE read this stage
-      if (tid == 0 && !s_fail) {
+      if (tid == 0) {
         copy_b(st, c, s);
         inflight |= 1u << s;
       }
       store_a(st, cur);
       tc::fence_async_smem();
+      if (tid == 0) {                  // the stage the next chunk writes: its MMAs (chunk cc - 2)
+        const int sn = (s + 1) % OZ_NSTAGE;
+        if (((issued >> sn) & 1u) && !settle(sn)) s_fail = 1;
+      }
       __syncthreads();
       if (s_fail) { ok = false; break; }
       if (tid == 0) {
@@ -340,18 +347,19 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
           tc::fence_after_sync();
           issue(st, (c % OZ_GROUP) == 0);
           tc::mma_commit(&bar[s]);
+          issued |= 1u << s;
         } else {
-          s_fail = 1;   // seen by every thread after the next barrier; the stage's MMAs were not issued
+          s_fail = 1;                  // seen by every thread after the next barrier
         }
       }
-      issued |= 1u << s;
       if ((c % OZ_GROUP) == OZ_GROUP - 1 || c == nchunks - 1) {
-        // every MMA so far has completed; the warp drains only if all its threads saw it
-        const bool seen = __all_sync(0xffffffffu, settle(s));
-        if (seen) drain();
-        else s_fail = 1;
+        // thread 0 sees every MMA so far complete, then all threads drain
+        if (tid == 0 && !s_fail)
+          for (int i = 0; i < OZ_NSTAGE; ++i)
+            if (((issued >> i) & 1u) && !settle(i)) s_fail = 1;
         __syncthreads();
         if (s_fail) { ok = false; break; }
+        drain();
       }
       cur[0] = nxt[0];
       cur[1] = nxt[1];
@@ -377,11 +385,12 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
     }
   }   // tiles
   // commits and bulk copies still outstanding (bounded; also after a lost wait)
-  for (int i = 0; i < OZ_NSTAGE; ++i)
-    if (((issued >> i) & 1u) && !settle(i)) ok = false;
-  if (tid == 0)
+  if (tid == 0) {
     for (int i = 0; i < OZ_NSTAGE; ++i)
-      if (((inflight >> i) & 1u) && !landed(i)) ok = false;
+      if (((issued >> i) & 1u) && !settle(i)) s_fail = 1;
+    for (int i = 0; i < OZ_NSTAGE; ++i)
+      if (((inflight >> i) & 1u) && !landed(i)) s_fail = 1;
+  }
   __syncthreads();
   if ((!ok || s_fail) && tid == 0) {
     status[0] = -6;   // ACE_ERR_TIMEOUT
