@@ -29,7 +29,9 @@
 //   rounding; after each group the accumulators are read back (tcgen05.ld),
 //   converted to int32 exactly and added into per-thread int64 sums shifted by
 //   8 (T - w) bits (below 2^60: no overflow). The final value is
-//   ldexp((double)sum, e_g + f_b - 8 T), rounded once to the output type.
+//   sum 2^(e_g + f_b - 8 T): the integer sum is rounded once to the output type
+//   and scaled by the power of two (exact), in FP32 for FP32 outputs (no FP64
+//   arithmetic, which is slow on this part).
 //
 // Per CTA (512 threads, one per SM): T - 1 accumulators of TN columns in TMEM;
 // K runs in chunks of 32 real terms (16 orbitals) through three shared-memory
@@ -376,9 +378,11 @@ oz_outer_kernel(const float2* __restrict__ A, int nk, int nb, long long ld, long
         for (int j = 0; j < NACC; ++j) {
           const int b = b0 + jq + j;
           if (b < nb) {
-            const double val = ldexp((double)acc[j], ergg + fcol[b] - OZ_BETA * T);
-            if constexpr (sizeof(OUT) == 8) reinterpret_cast<float*>(Out)[2 * ((long long)b * ld + gg) + ri] = (float)val;
-            else reinterpret_cast<double*>(Out)[2 * ((long long)b * ld + gg) + ri] = val;
+            const int e = ergg + fcol[b] - OZ_BETA * T;
+            if constexpr (sizeof(OUT) == 8)   // one rounding of the exact integer, then an exact power of two
+              reinterpret_cast<float*>(Out)[2 * ((long long)b * ld + gg) + ri] = ldexpf(__ll2float_rn(acc[j]), e);
+            else
+              reinterpret_cast<double*>(Out)[2 * ((long long)b * ld + gg) + ri] = ldexp(__ll2double_rn(acc[j]), e);
           }
         }
       }
