@@ -623,14 +623,20 @@ void zero_vectors(const ace_plan* p, void* X, long long count, cudaStream_t st) 
 
 // Xi = W L^{-*} (Eq. Wtilde) for `nk` vectors on `cs` by the plan's Xi mode;
 // returns the kernel count.
-int issue_xi(ace_plan* p, const void* W, int nk, const double* LinvH, void* Xi, char* xis, cudaStream_t cs) {
+// c32: scratch of nk * nk * 8 bytes for the TF32 product's FP32 copy of L^{-*}
+// (the gram partials, dead by then).
+int issue_xi(ace_plan* p, const void* W, int nk, const double* LinvH, void* Xi, char* xis, void* c32,
+             cudaStream_t cs) {
   if (p->xi == 1) return launch_xi_oz(W, nk, LinvH, nk, p->ld, p->ng, Xi, false, xis, p->status, cs);
   if (p->xi == 2) {
     launch_outer_f64acc(W, nk, LinvH, nk, p->ld, p->ng, Xi, false, cs);
     return 1;
   }
-  if (p->tc) launch_outer_tc(W, nk, LinvH, nk, p->ld, p->ng, 1.0, Xi, p->status, cs);
-  else launch_outer(p->f64, p->real, W, nk, LinvH, nk, p->ld, p->ng, 1.0, Xi, cs);
+  if (p->tc) {
+    launch_outer_tc(W, nk, LinvH, nk, p->ld, p->ng, 1.0, Xi, c32, p->status, cs);
+    return 2;
+  }
+  launch_outer(p->f64, p->real, W, nk, LinvH, nk, p->ld, p->ng, 1.0, Xi, cs);
   return 1;
 }
 
@@ -658,7 +664,7 @@ long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* X
   const int kr = launch_gram_reduce(Wl.part, splits, N, N, p->dv, true, false, p->Mc, nullptr, cs);
   if (p->tc) launch_diag_exact(Phi, W, N, p->ld, p->ng, p->dv, Wl.part, p->Mc, cs);
   const int kc = launch_cholesky_inv(p->Mc, N, p->work, p->LinvH, p->status, cs);
-  const int kx = issue_xi(p, W, N, p->LinvH, Xi, Wl.xis, cs);
+  const int kx = issue_xi(p, W, N, p->LinvH, Xi, Wl.xis, Wl.part, cs);
   return 1 + kr + (p->tc ? 2 : 0) + kc + kx;
 }
 
@@ -1071,7 +1077,7 @@ ace_status ace_build_oversampled(ace_plan* p, const void* Phi, int n_phi, void* 
     const int kr = launch_gram_reduce(Wl.part, splits, n_phi, n_phi, p->dv, true, false, Wl.Cm, nullptr, cs);
     if (p->tc) launch_diag_exact(Phi, W, n_phi, p->ld, p->ng, p->dv, Wl.part, Wl.Cm, cs);
     const int kc = launch_cholesky_inv(Wl.Cm, n_phi, Wl.work, Wl.LinvH, p->status, cs);
-    const int kx = issue_xi(p, W, n_phi, Wl.LinvH, Xi_out, Wl.xis, cs);
+    const int kx = issue_xi(p, W, n_phi, Wl.LinvH, Xi_out, Wl.xis, Wl.part, cs);
     return 1 + kr + (p->tc ? 2 : 0) + kc + kx;
   });
   if (s != ACE_OK) return s;
@@ -1372,9 +1378,9 @@ ace_status ace_apply(ace_plan* p, const void* Xi, const void* Psi, int nb, void*
   if (p->tc) launch_gram_tc(Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, p->status, st, p->bf16);
   else launch_gram(p->f64, p->real, Xi, N, Psi, nb, p->ld, p->ng, Wl.part, splits, st);
   launch_gram_reduce(Wl.part, splits, N, nb, p->dv, false, false, Wl.Cm, nullptr, st);
-  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, p->status, st, p->bf16);
+  if (p->tc) launch_outer_tc(Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, Wl.part, p->status, st, p->bf16);
   else launch_outer(p->f64, p->real, Xi, N, Wl.Cm, nb, p->ld, p->ng, -1.0, Y, st);
-  p->launches += 3;
+  p->launches += p->tc ? 4 : 3;
   return cuda_check("ace_apply");
 }
 

@@ -126,8 +126,10 @@ bool tc_gemm_prepare();
 int gram_tc_splits(long long ng, int na, int nb);
 void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, long long ng, double* part,
                     int splits, int* status, cudaStream_t st, bool bf16 = false);
+// launch_outer_tc: C is complex FP64 [nk][nb]; c32 is scratch for its FP32
+// copy (nk * nb * 8 bytes), made once per call.
 void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
-                     void* Out, int* status, cudaStream_t st, bool bf16 = false);
+                     void* Out, void* c32, int* status, cudaStream_t st, bool bf16 = false);
 // Xi = W L^{-*} with FP64 arithmetic from complex FP32 W (dense.cu): C upper
 // triangular FP64 [nk][nb]; Out complex FP32 or FP64 [nb][ld].
 void launch_outer_f64acc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, void* Out,

@@ -427,12 +427,13 @@ gram_tc_kernel(const float2* __restrict__ A, int na, const float2* __restrict__ 
 }
 
 // ---------------------------------------------------------------- outer
-// Grid: (ceil(nb/BB), ceil(ng/128)). C: FP64 complex [nk][nb].
+// Grid: (ceil(nb/BB), ceil(ng/128)). C: complex [nk][nb] rounded to FP32 once
+// per call (c_to_f32_kernel), so the CTAs of every row block read FP32.
 // A element e (0..1023): grid point g0 + e % 128, K pair e / 128 (k = 2 (e / 128)).
 // B element e (0..8 BB - 1): b = b0 + e % BB, K pair e / BB.
 template <int TN, bool BF>
 __global__ void __launch_bounds__(THREADS, 1)
-outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__ C, int nb, long long ld,
+outer_tc_kernel(const float2* __restrict__ A, int nk, const float2* __restrict__ C, int nb, long long ld,
                 long long ng, double alpha, float* __restrict__ Out, int* status) {
   using T = Tile<TN, BF>;
   constexpr int BB = T::BB, NACC = T::NACC;
@@ -465,14 +466,14 @@ outer_tc_kernel(const float2* __restrict__ A, int nk, const double* __restrict__
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (e < NBE && b0 + j < nb) {
         if (k < nk) {
-          const long long o = 2 * ((long long)k * nb + b0 + j);
-          v.x = (float)C[o];
-          v.y = (float)C[o + 1];
+          const float2 t = C[(long long)k * nb + b0 + j];
+          v.x = t.x;
+          v.y = t.y;
         }
         if (k + 1 < nk) {
-          const long long o = 2 * ((long long)(k + 1) * nb + b0 + j);
-          v.z = (float)C[o];
-          v.w = (float)C[o + 1];
+          const float2 t = C[(long long)(k + 1) * nb + b0 + j];
+          v.z = t.x;
+          v.w = t.y;
         }
       }
       Rg.c[i] = v;   // (Re C_k, Im C_k, Re C_k+1, Im C_k+1)
@@ -553,6 +554,12 @@ __global__ void diag_fix_kernel(const double* __restrict__ part, int na, int spl
   Mc[2 * ((long long)a * na + a) + 1] = 0.0;
 }
 
+// complex FP64 -> FP32 (the outer products' right operand, converted once)
+__global__ void c_to_f32_kernel(const double2* __restrict__ C, long long count, float2* __restrict__ Cf) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < count) Cf[i] = make_float2((float)C[i].x, (float)C[i].y);
+}
+
 // MMA width for nb output columns: the fewest MMA columns over the b tiles,
 // ties to the wider tile.
 int tc_width(int nb) {
@@ -582,7 +589,7 @@ void gram_tn(dim3 grid, cudaStream_t st, const float2* a, int na, const float2* 
 }
 
 template <int TN, bool BF>
-void outer_tn(dim3 grid, cudaStream_t st, const float2* a, int nk, const double* C, int nb, long long ld,
+void outer_tn(dim3 grid, cudaStream_t st, const float2* a, int nk, const float2* C, int nb, long long ld,
               long long ng, double alpha, float* o, int* status) {
   outer_tc_kernel<TN, BF><<<grid, THREADS, Tile<TN, BF>::SMEM_BYTES, st>>>(a, nk, C, nb, ld, ng, alpha, o, status);
 }
@@ -628,12 +635,15 @@ void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, 
   }
 }
 
-void launch_outer_tc(const void* A, int nk, const double* C, int nb, long long ld, long long ng, double alpha,
-                     void* Out, int* status, cudaStream_t st, bool bf16) {
+void launch_outer_tc(const void* A, int nk, const double* C64, int nb, long long ld, long long ng, double alpha,
+                     void* Out, void* c32, int* status, cudaStream_t st, bool bf16) {
   const int tn = tc_width(nb), bb = tn / 2;
   const dim3 grid((nb + bb - 1) / bb, (unsigned)((ng + TM - 1) / TM));
   const float2* a = static_cast<const float2*>(A);
   float* o = static_cast<float*>(Out);
+  const long long nc = (long long)nk * nb;
+  float2* C = static_cast<float2*>(c32);
+  c_to_f32_kernel<<<(unsigned)((nc + 255) / 256), 256, 0, st>>>(reinterpret_cast<const double2*>(C64), nc, C);
   if (bf16) {
     if (tn == 256) outer_tn<256, true>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
     else if (tn == 192) outer_tn<192, true>(grid, st, a, nk, C, nb, ld, ng, alpha, o, status);
