@@ -818,12 +818,15 @@ template <typename T> __device__ __forceinline__ T shfl_pair(T v) {
 template <typename R> __device__ __forceinline__ cplx<R> csel(bool c, cplx<R> a, cplx<R> b) {
   return cmk<cplx<R>>(c ? a.x : b.x, c ? a.y : b.y);
 }
-template <int N, bool INV, typename R>
-__device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)[N / 2], int h,
-                                               const TwTable<R, N>& tw) {
+// The radix-2 step alone, on a[] already holding the half-length transform:
+// each output goes to sink(j, Y) as soon as it is formed (y index j as in
+// split_line_dft), so a caller that stores it right away frees the registers
+// of a[j], a[H + j] within the loop instead of holding a second array.
+template <int N, bool INV, typename R, typename Sink>
+__device__ __forceinline__ void split_combine(const cplx<R> (&a)[N / 2], int h, const TwTable<R, N>& tw,
+                                              Sink sink) {
   using C = cplx<R>;
-  constexpr int M = N / 2, H = N / 4;
-  dft<M, N, INV, R>(a, tw);                                // E (lane 0) or O (lane 1)
+  constexpr int H = N / 4;
 #pragma unroll
   for (int j = 0; j < H; ++j) {
     const C recv = shfl_pair(h ? a[j] : a[H + j]);       // lane 0 gets O[j], lane 1 gets E[H + j]
@@ -831,9 +834,15 @@ __device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)
     const C od = h ? a[H + j] : recv;                    // O[hH + j]
     const C w = csel<R>(h, twiddle_value<N, N, INV, R>(H + j, tw), twiddle_value<N, N, INV, R>(j, tw));
     const C t = cmul(od, w);
-    y[j] = cadd(ev, t);
-    y[H + j] = csub(ev, t);
+    sink(j, cadd(ev, t));
+    sink(H + j, csub(ev, t));
   }
+}
+template <int N, bool INV, typename R>
+__device__ __forceinline__ void split_line_dft(cplx<R> (&a)[N / 2], cplx<R> (&y)[N / 2], int h,
+                                               const TwTable<R, N>& tw) {
+  dft<N / 2, N, INV, R>(a, tw);                            // E (lane 0) or O (lane 1)
+  split_combine<N, INV, R>(a, h, tw, [&](int j, cplx<R> v) { y[j] = v; });
 }
 // Pass B for the large FP64 pencils (n_z >= 64), whose whole pencil per thread
 // spills (FP32 pencils of 64 and 96 take the four-warp form, pass_b_quad_kernel):
@@ -971,7 +980,7 @@ pass_a_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   {   // column x = q: samples y = 2m + h
     constexpr int M = NY / 2;
     const bool act = q < NX;
-    C a[M], y[M];
+    C a[M];
     const long long xo = (long long)l * P.ld + (long long)z * NX * NY + q;
     const long long yo = (long long)r * P.ld + (long long)z * NX * NY + q;
     if constexpr (REAL) {                                  // x_l (y_r + i y_r2)
@@ -992,26 +1001,24 @@ pass_a_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
         a[m] = act ? cmulc(load_vec<R, REAL>(P.X, xo + yy * NX), load_vec<R, REAL>(P.Y, yo + yy * NX)) : zero;
       }
     }
-    split_line_dft<NY, false, R>(a, y, h, P.tw.ty());     // along y
-    if (act) {
-#pragma unroll
-      for (int j = 0; j < M; ++j) buf[split_index<NY>(j, h) * (NX + 1) + q] = y[j];
-    }
+    dft<M, NY, false, R>(a, P.tw.ty());                   // along y
+    split_combine<NY, false, R>(a, h, P.tw.ty(), [&](int j, C v) {
+      if (act) buf[split_index<NY>(j, h) * (NX + 1) + q] = v;
+    });
   }
   __syncthreads();
   {   // row ky = q: samples x = 2m + h
     constexpr int M = NX / 2;
     const bool act = q < NY;
-    C a[M], y[M];
+    C a[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) a[m] = act ? buf[q * (NX + 1) + 2 * m + h] : zero;
-    split_line_dft<NX, false, R>(a, y, h, P.tw.tx());     // along x
+    dft<M, NX, false, R>(a, P.tw.tx());                   // along x
     griddep_wait();                                        // the previous batch's pass D still reads S
-    if (act) {
-      C* out = P.S + ((long long)p * P.nz + z) * NX * NY + q;
-#pragma unroll
-      for (int j = 0; j < M; ++j) out[(long long)split_index<NX>(j, h) * NY] = y[j];
-    }
+    C* out = P.S + ((long long)p * P.nz + z) * NX * NY + q;
+    split_combine<NX, false, R>(a, h, P.tw.tx(), [&](int j, C v) {
+      if (act) out[(long long)split_index<NX>(j, h) * NY] = v;
+    });
   }
 }
 
@@ -1031,27 +1038,25 @@ pass_c_split_kernel(const __grid_constant__ PlaneParams<R, NX, NY> P) {
   {   // row ky = q of the spectrum: samples kx = 2m + h, inverse along x
     constexpr int M = NX / 2;
     const bool act = q < NY;
-    C a[M], y[M];
+    C a[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) a[m] = act ? plane[(long long)(2 * m + h) * NY + q] : zero;
-    split_line_dft<NX, true, R>(a, y, h, P.tw.tx());
-    if (act) {
-#pragma unroll
-      for (int j = 0; j < M; ++j) buf[q * (NX + 1) + split_index<NX>(j, h)] = y[j];   // row ky, column x
-    }
+    dft<M, NX, true, R>(a, P.tw.tx());
+    split_combine<NX, true, R>(a, h, P.tw.tx(), [&](int j, C v) {
+      if (act) buf[q * (NX + 1) + split_index<NX>(j, h)] = v;   // row ky, column x
+    });
   }
   __syncthreads();
   {   // column x = q: samples ky = 2m + h, inverse along y
     constexpr int M = NY / 2;
     const bool act = q < NX;
-    C a[M], y[M];
+    C a[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) a[m] = act ? buf[(2 * m + h) * (NX + 1) + q] : zero;
-    split_line_dft<NY, true, R>(a, y, h, P.tw.ty());
-    if (act) {
-#pragma unroll
-      for (int j = 0; j < M; ++j) plane[(long long)split_index<NY>(j, h) * NX + q] = y[j];
-    }
+    dft<M, NY, true, R>(a, P.tw.ty());
+    split_combine<NY, true, R>(a, h, P.tw.ty(), [&](int j, C v) {
+      if (act) plane[(long long)split_index<NY>(j, h) * NX + q] = v;
+    });
   }
 }
 
