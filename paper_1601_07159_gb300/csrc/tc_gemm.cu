@@ -606,14 +606,27 @@ bool tc_gemm_prepare() {
   return cudaGetLastError() == cudaSuccess;
 }
 
+// Split-K count for `tiles` output tiles on 152 SMs (one CTA per SM): the one
+// that minimises waves / splits (the time of a CTA's K range times the number
+// of waves). 1 tile -> 152 splits (one wave); 64 tiles -> 7 (448 CTAs, 98 % of
+// three waves, where 2 splits left 24 SMs idle); 96 tiles -> 11 (1 split used
+// 96 of 152 SMs). Ties within 2 % go to fewer splits (fewer partial sums).
 int gram_tc_splits(long long ng, int na, int nb) {
+  constexpr long long kSMs = 152, kMaxSplits = 1024;
   const int bb = tc_width(nb) / 2;
   const long long tiles = (long long)((na + TM - 1) / TM) * ((nb + bb - 1) / bb);
-  long long s = 152 / tiles;   // one wave of one CTA per SM
-  const long long max_s = (ng + KC / 2 - 1) / (KC / 2);
-  if (s > max_s) s = max_s;
-  if (s < 1) s = 1;
-  return (int)s;
+  long long max_s = (ng + KC / 2 - 1) / (KC / 2);
+  if (max_s > kMaxSplits) max_s = kMaxSplits;
+  long long best = 1;
+  double best_cost = 1e300;
+  for (long long s = 1; s <= max_s; ++s) {
+    const double cost = (double)((tiles * s + kSMs - 1) / kSMs) / (double)s;
+    if (cost < best_cost * 0.98) {
+      best_cost = cost;
+      best = s;
+    }
+  }
+  return (int)best;
 }
 
 void launch_gram_tc(const void* A, int na, const void* B, int nb, long long ld, long long ng, double* part,
