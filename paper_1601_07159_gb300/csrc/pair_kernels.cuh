@@ -26,9 +26,15 @@
 // pencil's (kx, ky) position is a run-time index), the accumulate pass once per
 // precision; a grid n_x x n_y x n_z runs when its plane and its pencil length
 // are compiled in. On cubic grids passes B and D use instances with the grid
-// compiled in (strides and offsets folded into the instructions). At the larger edges a line is held by two lanes instead of
-// one thread (split_line_dft): the plane passes when the longer plane edge is
-// >= 48 (FP64: >= 64), pass B from n_z = 64.
+// compiled in (strides and offsets folded into the instructions). At the
+// larger edges a line is held by two lanes instead of one thread
+// (split_line_dft): the plane passes when the longer plane edge is >= 48
+// (FP64: >= 64), FP64 pass B from n_z = 64; FP32 pencils of 64 and 96 are
+// spread over four warps (pass_b_quad_kernel).
+//
+// Real vectors (R64) pack two pairs into one complex solve: a slot holds
+// rho_lr + i rho_lr' (decode_slot_real), the kernel being real and even keeps
+// V_lr and V_lr' in the real and imaginary parts, and pass D splits them.
 //
 // Two ways to run a schedule of batches:
 //  * four kernels per batch (pass_*_kernel), chained with programmatic
