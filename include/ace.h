@@ -150,6 +150,13 @@ typedef struct {
  * raised to at least 2). This flag turns that off: the batches of a round are
  * then spread over `lanes` streams instead. Results are bitwise the same. */
 #define ACE_FLAG_NO_OVERLAP 16
+/* Radix order of the line transforms (ACE_DTYPE_C64 plans): by default a
+ * transform of length n takes a radix 4 first, then 2, 3, 5; with this flag it
+ * takes the odd radix (3, then 5) first, for the lengths where the orders
+ * differ (those with a factor 3 or 5 beside a power of two: 12, 20, 24, 36,
+ * 40, 48, 96). Results agree to FP32 rounding. A schedule choice of
+ * ace_autotune; ignored by FP64 plans and by ACE_FLAG_ENGINE. */
+#define ACE_FLAG_RADIX_ODD_FIRST 32
 
 typedef struct ace_plan ace_plan;
 
@@ -249,7 +256,8 @@ ace_status ace_build_batched(ace_plan* const* plans, const void* const* Phi, voi
  * to FP32 rounding order): times ace_build of the descriptor's problem on the
  * current device for each candidate schedule -- tile edge 8, 6 or 4 orbitals,
  * pair-batch scratch of about 36, 72 or 144 MiB, the two-stream overlapped
- * pair schedule or two lanes without overlap -- on seeded pseudo-random
+ * pair schedule or two lanes without overlap, and (C64 plans) the radix order
+ * of the line transforms (ACE_FLAG_RADIX_ODD_FIRST) -- on seeded pseudo-random
  * orbitals, `reps` timed builds each (0 = 3) after one untimed build, and
  * writes the fastest into *best (a copy of *d with tile, max_pairs, lanes and
  * flags set) and its milliseconds per build into *ms_out (nullable), and
@@ -261,7 +269,8 @@ ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_
 /* Tuned schedules, process-wide: ace_autotune registers its result, and
  * ace_tuning_register adds one found earlier (for instance from a saved
  * tuning table); ace_plan_create then takes the registered max_pairs, tile,
- * lanes and ACE_FLAG_NO_OVERLAP for a descriptor with the same grid, n_occ,
+ * lanes, ACE_FLAG_NO_OVERLAP and ACE_FLAG_RADIX_ODD_FIRST for a descriptor
+ * with the same grid, n_occ,
  * dtype, prec and kernel whose max_pairs, tile and lanes are all 0.
  * ace_tuning_clear forgets every registered schedule. ace_plan_desc writes the
  * plan's effective descriptor (the schedule it runs, the resolved ld). */

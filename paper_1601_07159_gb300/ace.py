@@ -165,9 +165,10 @@ class Plan:
                  omega: float = 0.0, g0: float | None = None, alpha: float = 1.0,
                  max_pairs: int = 0, tile: int = 0, lanes: int = 0, graphs: bool = True,
                  engine: bool = False, pdl: bool = True, tensor_cores: bool = True,
-                 overlap: bool = True, prec: str = "default", ld: int = 0):
+                 overlap: bool = True, prec: str = "default", ld: int = 0, radix: int = 0):
         """n: grid edge or (n_x, n_y, n_z); L: cell edge or (L_x, L_y, L_z);
-        ld: elements from one vector to the next (0 = N_g)."""
+        ld: elements from one vector to the next (0 = N_g); radix: order of
+        the FP32 line transforms (0: radix 4 first, 1: odd radix first)."""
         if isinstance(L, (int, float)):
             L = (float(L),) * 3
         grid = _grid(n)
@@ -185,8 +186,9 @@ class Plan:
         d.max_pairs = max_pairs
         d.tile = tile
         d.lanes = lanes
-        d.flags = (0 if graphs else 1) | (2 if engine else 0) | (0 if pdl else 4) | (0 if tensor_cores else 8) | (0 if overlap else 16)
-        self.schedule = {"tile": tile, "max_pairs": max_pairs, "lanes": lanes, "overlap": overlap}
+        d.flags = ((0 if graphs else 1) | (2 if engine else 0) | (0 if pdl else 4) | (0 if tensor_cores else 8) |
+                   (0 if overlap else 16) | (32 if radix else 0))
+        self.schedule = {"tile": tile, "max_pairs": max_pairs, "lanes": lanes, "overlap": overlap, "radix": radix}
         h = _vp()
         _check(_lib.ace_plan_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -363,7 +365,7 @@ class Plan:
         d = Desc()
         _check(_lib.ace_plan_desc(self._h, ctypes.byref(d)))
         return {"tile": d.tile, "max_pairs": d.max_pairs, "lanes": d.lanes, "overlap": not (d.flags & 16),
-                "ld": d.ld}
+                "radix": 1 if d.flags & 32 else 0, "ld": d.ld}
 
     def debug_engine_wait(self, polls: int = 0, unreachable: bool = False):
         """ace_debug_engine_wait: bound (or make unreachable) the engine's waits."""
@@ -415,17 +417,17 @@ def autotune(n: int, L, n_occ: int, dtype: str = "c64", kernel: str = "bare", om
     ms = ctypes.c_double(0.0)
     _check(_lib.ace_autotune(ctypes.byref(d), reps, ctypes.byref(best), ctypes.byref(ms)))
     return {"tile": best.tile, "max_pairs": best.max_pairs, "lanes": best.lanes,
-            "overlap": not (best.flags & 16), "ms": ms.value}
+            "overlap": not (best.flags & 16), "radix": 1 if best.flags & 32 else 0, "ms": ms.value}
 
 
 def tuning_register(n, L, n_occ: int, dtype: str, kernel: str, tile: int, max_pairs: int, lanes: int,
-                    overlap: bool, omega: float = 0.0, prec: str = "default"):
+                    overlap: bool, omega: float = 0.0, prec: str = "default", radix: int = 0):
     """ace_tuning_register: later plans of this problem with default schedule
     knobs run this schedule."""
     d = _desc(n, L, n_occ, dtype, kernel, omega, None, 1.0)
     d.prec = PRECS[prec]
     d.tile, d.max_pairs, d.lanes = tile, max_pairs, lanes
-    d.flags = 0 if overlap else 16
+    d.flags = (0 if overlap else 16) | (32 if radix else 0)
     _check(_lib.ace_tuning_register(ctypes.byref(d)))
 
 
@@ -449,7 +451,7 @@ class TuningTable:
             for k, t in self.table.items():
                 n, n_occ, dtype, kernel = k.split("|")
                 tuning_register(tuple(int(v) for v in n.split("x")), 1.0, int(n_occ), dtype, kernel,
-                                t["tile"], t["max_pairs"], t["lanes"], t["overlap"])
+                                t["tile"], t["max_pairs"], t["lanes"], t["overlap"], radix=t.get("radix", 0))
 
     @staticmethod
     def key(n, n_occ, dtype, kernel) -> str:
@@ -470,7 +472,8 @@ class TuningTable:
     def plan(self, n, L, n_occ, dtype="c64", kernel="bare", omega=0.0, g0=None, alpha=1.0) -> "Plan":
         t = self.schedule(n, L, n_occ, dtype, kernel, omega, g0, alpha)
         return Plan(n, L, n_occ, dtype=dtype, kernel=kernel, omega=omega, g0=g0, alpha=alpha,
-                    tile=t["tile"], max_pairs=t["max_pairs"], lanes=t["lanes"], overlap=t["overlap"])
+                    tile=t["tile"], max_pairs=t["max_pairs"], lanes=t["lanes"], overlap=t["overlap"],
+                    radix=t.get("radix", 0))
 
 
 class Batch:

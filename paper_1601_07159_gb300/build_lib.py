@@ -25,11 +25,13 @@ PLAIN = ["pair_dispatch.cu", "pair_point.cu", "dense.cu", "chol.cu", "tc_gemm.cu
 
 
 def shape_lists():
-    """The compiled edges and non-square planes per precision, read from the
-    lists in csrc/pair_dispatch.cu (the one place they are written down)."""
+    """The compiled edges and non-square planes per precision (and, as
+    "f32_r1", the FP32 ones also compiled with the odd-radix-first order), read
+    from the lists in csrc/pair_dispatch.cu (the one place they are written
+    down)."""
     text = open(os.path.join(CSRC, "pair_dispatch.cu")).read()
     out = {}
-    for prec in ("F32", "F64"):
+    for prec in ("F32", "F64", "F32_R1"):
         edges = re.search(rf"#define ACE_EDGES_{prec}\(X\)(.*)", text).group(1)
         planes = re.search(rf"#define ACE_PLANES_{prec}\(X\)(.*)", text).group(1)
         out[prec.lower()] = (tuple(int(v) for v in re.findall(r"X\((\d+)\)", edges)),
@@ -40,7 +42,18 @@ def shape_lists():
 def units():
     """(source, object name, extra flags) for every translation unit."""
     out = [(s, s.replace(".cu", ".o"), []) for s in PLAIN]
-    for prec, (edges, planes) in shape_lists().items():
+    lists = shape_lists()
+    r1_edges, r1_planes = lists.pop("f32_r1")
+    for nx, ny in [(n, n) for n in r1_edges] + list(r1_planes):   # odd-radix-first FP32 instances
+        tag = f"f32_{nx}_{ny}_r1"
+        out.append(("pair_plane.cu", f"pair_plane_{tag}.o",
+                    ["-DACE_PLANE_R=float", f"-DACE_PX={nx}", f"-DACE_PY={ny}", f"-DACE_PLANE_TAG={tag}",
+                     "-DACE_RADIX_ORDER=1"]))
+    for n in r1_edges:
+        tag = f"f32_{n}_r1"
+        out.append(("pair_pencil.cu", f"pair_pencil_{tag}.o",
+                    ["-DACE_PENCIL_R=float", f"-DACE_PZ={n}", f"-DACE_PENCIL_TAG={tag}", "-DACE_RADIX_ORDER=1"]))
+    for prec, (edges, planes) in lists.items():
         typ = "float" if prec == "f32" else "double"
         for nx, ny in [(n, n) for n in edges] + list(planes):
             tag = f"{prec}_{nx}_{ny}"

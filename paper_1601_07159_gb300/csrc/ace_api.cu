@@ -104,6 +104,7 @@ struct ace_plan {
   bool tc = false;               // tensor-core GEMMs (complex FP32 storage)
   bool bf16 = false;             // M and the apply with BF16 operands (ACE_PREC_SPLIT_BF16)
   bool overlap = false;          // graph mode: pass A of batch k+1 overlaps pass D of batch k
+  int radix = 0;                 // line-transform radix order (ACE_FLAG_RADIX_ODD_FIRST)
   unsigned eng_polls = kEngineSpinDefault;   // engine wait limit (ace_debug_engine_wait)
   unsigned eng_bias = 0;
   cudaEvent_t ov_ev[2] = {};
@@ -579,6 +580,7 @@ PairLaunch base_launch(const ace_plan* p) {
   L.scale = 1.0;
   L.prepare_only = false;
   L.no_pdl = (p->d.flags & ACE_FLAG_NO_PDL) != 0;
+  L.radix = p->radix;
   return L;
 }
 
@@ -673,7 +675,7 @@ long long issue_build_dense(ace_plan* p, const void* Phi, const void* W, void* X
 // descriptor leaves max_pairs, tile and lanes at 0.
 std::mutex g_tune_mu;
 std::vector<ace_desc> g_tuned;
-constexpr int kScheduleFlags = ACE_FLAG_NO_OVERLAP;
+constexpr int kScheduleFlags = ACE_FLAG_NO_OVERLAP | ACE_FLAG_RADIX_ODD_FIRST;
 
 bool same_problem(const ace_desc& a, const ace_desc& b) {
   return a.n[0] == b.n[0] && a.n[1] == b.n[1] && a.n[2] == b.n[2] && a.n_occ == b.n_occ && a.dtype == b.dtype &&
@@ -823,6 +825,7 @@ ace_status ace_plan_create(const ace_desc* d, ace_plan** out) {
   p->xi = xi_slices ? 1 : (d->prec == ACE_PREC_XI_FP64_SIMT ? 2 : 0);
   p->overlap = p->graphs && !p->engine && !(d->flags & ACE_FLAG_NO_OVERLAP);
   if (p->overlap && p->lanes < 2) p->lanes = 2;
+  p->radix = (!p->f64 && (d->flags & ACE_FLAG_RADIX_ODD_FIRST)) ? 1 : 0;
   const size_t slot = (size_t)p->ng * p->csize;
   const int tt = p->tile * p->tile;
   if (d->max_pairs) {
@@ -1265,16 +1268,19 @@ ace_status ace_autotune(const ace_desc* d, int reps, ace_desc* best, double* ms_
       if (mp > (long long)kMaxTiles * tt) mp = (long long)kMaxTiles * tt;
       if (mp < tt) mp = tt;
       for (int ov = 1; ov >= 0; --ov) {
-        ace_desc c = *d;
-        c.tile = tile;
-        c.max_pairs = (int)mp;
-        c.lanes = 2;
-        c.flags = (d->flags & ~(ACE_FLAG_NO_OVERLAP | ACE_FLAG_NO_GRAPH | ACE_FLAG_ENGINE)) |
-                  (ov ? 0 : ACE_FLAG_NO_OVERLAP);
-        bool dup = false;
-        for (const auto& o : cand)
-          dup = dup || (o.tile == c.tile && o.max_pairs == c.max_pairs && o.flags == c.flags);
-        if (!dup) cand.push_back(c);
+        for (int rx = 0; rx < (f64 ? 1 : 2); ++rx) {   // radix orders (FP32 line transforms)
+          ace_desc c = *d;
+          c.tile = tile;
+          c.max_pairs = (int)mp;
+          c.lanes = 2;
+          c.flags = (d->flags & ~(ACE_FLAG_NO_OVERLAP | ACE_FLAG_NO_GRAPH | ACE_FLAG_ENGINE |
+                                  ACE_FLAG_RADIX_ODD_FIRST)) |
+                    (ov ? 0 : ACE_FLAG_NO_OVERLAP) | (rx ? ACE_FLAG_RADIX_ODD_FIRST : 0);
+          bool dup = false;
+          for (const auto& o : cand)
+            dup = dup || (o.tile == c.tile && o.max_pairs == c.max_pairs && o.flags == c.flags);
+          if (!dup) cand.push_back(c);
+        }
       }
     }
   }

@@ -61,6 +61,7 @@ struct PairLaunch {
   const TileDesc* dtiles;  // device copy of the batch's tile descriptors
   bool no_pdl;           // launch the passes without programmatic dependent launch
   int pass_mask;         // passes to launch: bit 0 A, 1 B, 2 C, 3 D (0 = all)
+  int radix;             // line-transform radix order: 0 radix 4 first, 1 odd radix first (FP32)
 };
 // Persistent engine counters: a queue head and one completion counter per
 // (batch, pass), each on its own 128-byte line so that polling blocks do not

@@ -12,10 +12,28 @@
 // This is the Poisson solver's transform (Sec. 2: each solve is
 // O(N_g log N_g) with FFTs); the 3-D transform is built from these line
 // transforms in pair_kernels.cu.
+//
+// Radix order, fixed per translation unit by ACE_RADIX_ORDER: 0 (default)
+// takes a radix 4 first, then 2, 3, 5; 1 takes the odd radix (3, then 5)
+// first when the length has one, so 48 = 3 x 16 instead of 4 x 12 (other
+// twiddle sets, other instruction schedules). The code of each order sits in
+// its own inline namespace, so instances of both orders link into one library.
 #pragma once
 #include <cuda_runtime.h>
 
+#ifndef ACE_RADIX_ORDER
+#define ACE_RADIX_ORDER 0
+#endif
+#if ACE_RADIX_ORDER == 0
+#define ACE_RADIX_NS radix0
+#elif ACE_RADIX_ORDER == 1
+#define ACE_RADIX_NS radix1
+#else
+#error "ACE_RADIX_ORDER must be 0 or 1"
+#endif
+
 namespace ace {
+inline namespace ACE_RADIX_NS {
 
 template <typename R> struct cplx_t;
 template <> struct cplx_t<float> { using type = float2; };
@@ -91,6 +109,8 @@ __device__ __forceinline__ cplx<R> twiddle_value(int e, const TwTable<R, NTOP>& 
 }
 
 template <int N> __host__ __device__ constexpr int first_radix() {
+  if constexpr (ACE_RADIX_ORDER == 1 && N % 3 == 0 && N != 3) return 3;
+  if constexpr (ACE_RADIX_ORDER == 1 && N % 5 == 0 && N != 5) return 5;
   return (N % 4 == 0 && N != 4) ? 4 : (N % 2 == 0 ? 2 : (N % 3 == 0 ? 3 : (N % 5 == 0 ? 5 : N)));
 }
 
@@ -182,4 +202,5 @@ __device__ __forceinline__ void dft(cplx<R> (&a)[N], const TwTable<R, NTOP>& tw)
   }
 }
 
+}  // namespace ACE_RADIX_NS
 }  // namespace ace

@@ -13,6 +13,11 @@
 // Non-square planes (n_x, n_y) compiled beside the square ones.
 #define ACE_PLANES_F32(X) X(12, 16) X(16, 12) X(16, 24) X(24, 16) X(40, 48) X(48, 40)
 #define ACE_PLANES_F64(X) X(12, 16) X(16, 12) X(16, 24) X(24, 16) X(40, 48) X(48, 40)
+// FP32 edges and planes also compiled with the odd-radix-first order
+// (ACE_RADIX_ORDER = 1): the lengths with a factor 3 or 5 beside a power of
+// two, where the two orders differ.
+#define ACE_EDGES_F32_R1(X) X(12) X(20) X(24) X(36) X(40) X(48) X(96)
+#define ACE_PLANES_F32_R1(X) X(12, 16) X(16, 12) X(16, 24) X(24, 16) X(40, 48) X(48, 40)
 
 namespace ace {
 
@@ -35,13 +40,29 @@ ACE_EDGES_F32(DECL_SQ32)
 ACE_EDGES_F64(DECL_SQ64)
 ACE_PLANES_F32(DECL_PL32)
 ACE_PLANES_F64(DECL_PL64)
+#define DECL_SQ32R1(E)                                                                      \
+  bool plane_launch_f32_##E##_##E##_r1(const PairLaunch&, const Batch&, int, cudaStream_t); \
+  bool pencil_launch_f32_##E##_r1(const PairLaunch&, const Batch&, cudaStream_t);
+#define DECL_PL32R1(X_, Y_) bool plane_launch_f32_##X_##_##Y_##_r1(const PairLaunch&, const Batch&, int, cudaStream_t);
+ACE_EDGES_F32_R1(DECL_SQ32R1)
+ACE_PLANES_F32_R1(DECL_PL32R1)
 
 bool launch_point_f32(const PairLaunch& L, const Batch& b, cudaStream_t st);
 bool launch_point_f64(const PairLaunch& L, const Batch& b, cudaStream_t st);
 
 namespace {
 
-PlaneFn find_plane(bool f64, int nx, int ny) {
+// radix order 1 falls back to order 0 where no such instance is compiled (the
+// two orders coincide there)
+PlaneFn find_plane(bool f64, int nx, int ny, int radix) {
+  if (!f64 && radix == 1) {
+#define SQ32R1(E) if (nx == E && ny == E) return plane_launch_f32_##E##_##E##_r1;
+#define PL32R1(X_, Y_) if (nx == X_ && ny == Y_) return plane_launch_f32_##X_##_##Y_##_r1;
+    ACE_EDGES_F32_R1(SQ32R1)
+    ACE_PLANES_F32_R1(PL32R1)
+#undef SQ32R1
+#undef PL32R1
+  }
 #define SQ32(E) if (nx == E && ny == E) return plane_launch_f32_##E##_##E;
 #define SQ64(E) if (nx == E && ny == E) return plane_launch_f64_##E##_##E;
 #define PL32(X_, Y_) if (nx == X_ && ny == Y_) return plane_launch_f32_##X_##_##Y_;
@@ -60,7 +81,12 @@ PlaneFn find_plane(bool f64, int nx, int ny) {
   return nullptr;
 }
 
-PencilFn find_pencil(bool f64, int nz) {
+PencilFn find_pencil(bool f64, int nz, int radix) {
+  if (!f64 && radix == 1) {
+#define PE32R1(E) if (nz == E) return pencil_launch_f32_##E##_r1;
+    ACE_EDGES_F32_R1(PE32R1)
+#undef PE32R1
+  }
 #define PE32(E) if (nz == E) return pencil_launch_f32_##E;
 #define PE64(E) if (nz == E) return pencil_launch_f64_##E;
   if (f64) {
@@ -92,8 +118,8 @@ PencilFn find_point(bool f64, int nx, int ny, int nz) {
 // Passes A-D of one batch (or, with prepare_only, the kernels' attributes),
 // with the profiling events around each pass when L.ev is set.
 bool launch_batch(bool f64, const PairLaunch& L, const Batch& b, cudaStream_t st) {
-  const PlaneFn plane = find_plane(f64, L.nx, L.ny);
-  const PencilFn pencil = find_pencil(f64, L.nz);
+  const PlaneFn plane = find_plane(f64, L.nx, L.ny, L.radix);
+  const PencilFn pencil = find_pencil(f64, L.nz, L.radix);
   if (!plane || !pencil) return false;
   if (L.prepare_only) return plane(L, b, 0, st) && pencil(L, b, st);
   auto mark = [&](int k) { if (L.ev) cudaEventRecord(L.ev[k], st); };
@@ -119,7 +145,7 @@ bool launch_batch(bool f64, const PairLaunch& L, const Batch& b, cudaStream_t st
 }  // namespace
 
 bool pair_grid_supported(bool f64, int nx, int ny, int nz) {
-  return find_plane(f64, nx, ny) != nullptr && find_pencil(f64, nz) != nullptr;
+  return find_plane(f64, nx, ny, 0) != nullptr && find_pencil(f64, nz, 0) != nullptr;
 }
 
 bool launch_pair_batch_f32(const PairLaunch& L, const Batch& b, cudaStream_t st) { return launch_batch(false, L, b, st); }

@@ -59,6 +59,7 @@
 
 
 namespace ace {
+inline namespace ACE_RADIX_NS {   // radix order of this translation unit (fft_reg.cuh)
 
 // Twiddle tables of a plane: one per axis, shared when the plane is square.
 template <typename R, int NX, int NY> struct PlaneTw {
@@ -1618,4 +1619,5 @@ bool launch_engine(const PairLaunch& L, const EngineLaunch& EL, cudaStream_t st)
   }
 }
 
+}  // namespace ACE_RADIX_NS
 }  // namespace ace

@@ -1,7 +1,9 @@
 // One (precision, plane n_x x n_y) instance of the plane passes A and C. The
 // build compiles this file once per compiled plane with
 // -DACE_PLANE_R=<float|double> -DACE_PX=<n_x> -DACE_PY=<n_y>
-// -DACE_PLANE_TAG=<f32_nx_ny|f64_nx_ny>; pair_dispatch.cu maps planes to them.
+// -DACE_PLANE_TAG=<f32_nx_ny|f64_nx_ny> (and FP32 planes again with
+// -DACE_RADIX_ORDER=1 -DACE_PLANE_TAG=f32_nx_ny_r1); pair_dispatch.cu maps
+// planes to them.
 #include "pair_kernels.cuh"
 
 #if !defined(ACE_PLANE_R) || !defined(ACE_PX) || !defined(ACE_PY) || !defined(ACE_PLANE_TAG)

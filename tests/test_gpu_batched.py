@@ -134,6 +134,7 @@ def test_autotune_and_tuning_table(ace, tmp_path):
     n, L, N = 16, 6.0, 12
     t = ace.autotune(n, L, N, "c64", "bare")
     assert t["tile"] in (4, 6, 8) and t["max_pairs"] >= t["tile"] ** 2 and t["ms"] > 0
+    assert t["radix"] in (0, 1)                      # radix order is one of the searched knobs
     path = str(tmp_path / "tune.json")
     tab = ace.TuningTable(path)
     plan = tab.plan(n, L, N, "c64", "bare")
@@ -153,9 +154,9 @@ def test_autotune_and_tuning_table(ace, tmp_path):
     assert (default["tile"], default["max_pairs"], default["overlap"]) == (t2["tile"], t2["max_pairs"], t2["overlap"])
     assert ace.TuningTable.key((n, n, n), N, "c64", "bare") == ace.TuningTable.key(n, N, "c64", "bare")
     ace.tuning_clear()
-    ace.tuning_register(n, L, N, "c64", "bare", tile=4, max_pairs=48, lanes=3, overlap=False)
+    ace.tuning_register(n, L, N, "c64", "bare", tile=4, max_pairs=48, lanes=3, overlap=False, radix=1)
     e = ace.Plan(n, L, N, "c64", "bare").effective_schedule()
-    assert (e["tile"], e["max_pairs"], e["lanes"], e["overlap"]) == (4, 48, 3, False)
+    assert (e["tile"], e["max_pairs"], e["lanes"], e["overlap"], e["radix"]) == (4, 48, 3, False, 1)
     assert ace.Plan(n, L, N, "c64", "bare", tile=8).effective_schedule()["tile"] == 8   # explicit knobs win
     ace.tuning_clear()
     assert ace.Plan(n, L, N, "c64", "bare").effective_schedule()["tile"] == 8

@@ -34,3 +34,16 @@ def test_named_workloads():
     assert synth.SI64_48.kernel == "erfc" and math.isclose(synth.SI64_48.omega, 0.106)
     assert (synth.DIFF_64.n, synth.DIFF_64.n_occ) == (64, 256)
     assert (synth.SI512_96.n, synth.SI512_96.n_occ, synth.SI512_96.n_bands) == (96, 1024, 1536)
+
+
+def test_odd_radix_first_instances():
+    """The FP32 grids compiled a second time with the odd radix first are
+    compiled grids whose lengths have a factor 3 or 5 beside a power of two
+    (where the two radix orders differ)."""
+    lists = build_lib.shape_lists()
+    edges, planes = lists["f32_r1"]
+    assert set(edges) <= set(lists["f32"][0]) and set(planes) <= set(lists["f32"][1])
+    for n in edges:
+        assert (n % 3 == 0 or n % 5 == 0) and n % 4 == 0
+    units = [u[1] for u in build_lib.units()]
+    assert all(f"pair_plane_f32_{n}_{n}_r1.o" in units and f"pair_pencil_f32_{n}_r1.o" in units for n in edges)
