@@ -94,13 +94,15 @@ def parse(argv=None):
     p.add_argument("--no-overlap", action="store_true",
                    help="spread a round's batches over lanes instead of overlapping pass A with pass D")
     p.add_argument("--chains", type=int, default=0, help="concurrent stream chains of a batch (0 = default)")
+    p.add_argument("--radix", type=int, default=0, choices=[0, 1],
+                   help="FFT radix order: 0 radix 4 first (default), 1 odd radix first")
     p.add_argument("--systems", type=int, default=64, help="systems of the batched workload")
     return p.parse_args(argv)
 
 
 def default_schedule(args):
-    return (args.max_pairs, args.tile, args.lanes, args.eager, args.engine, args.no_pdl, args.no_overlap) == \
-        (0, 0, 0, False, False, False, False)
+    return (args.max_pairs, args.tile, args.lanes, args.eager, args.engine, args.no_pdl, args.no_overlap,
+            args.radix) == (0, 0, 0, False, False, False, False, 0)
 
 
 def workload_config(name, s):
@@ -385,7 +387,7 @@ def make_plan(ace, s, args):
     return ace.Plan(s.n, s.L, s.n_occ, dtype="c64", kernel=s.kernel, omega=s.omega,
                     max_pairs=args.max_pairs, tile=args.tile, lanes=args.lanes,
                     graphs=not args.eager, engine=args.engine and not args.eager,
-                    pdl=not args.no_pdl, overlap=not args.no_overlap)
+                    pdl=not args.no_pdl, overlap=not args.no_overlap, radix=args.radix)
 
 
 def device_inputs(s, seed):
