@@ -245,8 +245,12 @@ __device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char*
 }
 
 // Main loop shared by both kernels: load(c, regs) fetches chunk c from global
-// memory, store(stage, regs) splits it into the stage. Chunks are fetched
-// NSTAGE - 1 ahead (two register sets in flight at TN = 128, one otherwise).
+// memory, store(stage, regs) splits it into the stage. At TN = 128 (three
+// stages) chunks are fetched two ahead in two register sets. At TN = 192 / 256
+// one register set serves: chunk c + 1 is fetched into it as soon as chunk c
+// is stored, and arrives while the thread waits on the MMAs of chunk c - 1.
+// (A second set held across the iteration pushed TN = 256 past the 128-register
+// cap of 512 threads, and its spills exposed the loads' latency: 23 % slower.)
 // On return thread (warp w, lane) holds acc[j] = D[row 32 (w % 4) + lane][col
 // NACC (w / 4) + j]. Each thread waits (bounded) for the commit of the chunk
 // that last used a stage before storing into it, and drains a finished
@@ -288,11 +292,13 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
     }
     return true;
   };
-  // chunk c from registers into its stage, then the MMAs; false once a wait was lost
-  auto step = [&](int c, int s, const Regs& cur) -> bool {
+  // chunk c from registers into its stage (with `reload`, chunk c + 1 then
+  // fetched into the same registers), then the MMAs; false once a wait was lost
+  auto step = [&](int c, int s, Regs& cur, bool reload) -> bool {
     unsigned char* st = S.stage + s * T::STAGE_BYTES;
     if ((issued >> s) & 1u) settle(s);   // the MMAs of chunk c - NSTAGE read this stage
     store(st, cur);
+    if (reload && c + 1 < nchunks) load(c + 1, cur);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (s_fail) return false;
@@ -313,7 +319,7 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
     if (nchunks > 1) load(1, r1);
     for (int c = 0; c < nchunks; ++c) {
       if (c + 2 < nchunks) load(c + 2, r2);
-      if (!step(c, s, r0)) {
+      if (!step(c, s, r0, false)) {
         ok = false;
         break;
       }
@@ -322,15 +328,13 @@ __device__ __forceinline__ bool tc_mainloop(const TcState& S, uint32_t tmem, int
       s = s + 1 == NS ? 0 : s + 1;
     }
   } else {
-    Regs r0, r1;       // chunks c, c + 1
+    Regs r0;           // chunk c, then (once stored) chunk c + 1
     if (nchunks > 0) load(0, r0);
     for (int c = 0; c < nchunks; ++c) {
-      if (c + 1 < nchunks) load(c + 1, r1);
-      if (!step(c, s, r0)) {
+      if (!step(c, s, r0, true)) {
         ok = false;
         break;
       }
-      r0 = r1;
       s = s + 1 == NS ? 0 : s + 1;
     }
   }
