@@ -250,7 +250,7 @@ __device__ __forceinline__ void issue_chunk(uint32_t dtmem, const unsigned char*
 // one register set serves: chunk c + 1 is fetched into it as soon as chunk c
 // is stored, and arrives while the thread waits on the MMAs of chunk c - 1.
 // (A second set held across the iteration pushed TN = 256 past the 128-register
-// cap of 512 threads, and its spills exposed the loads' latency: 23 % slower.)
+// cap of 512 threads, and its spills exposed the loads' latency: 29 % slower.)
 // On return thread (warp w, lane) holds acc[j] = D[row 32 (w % 4) + lane][col
 // NACC (w / 4) + j]. Each thread waits (bounded) for the commit of the chunk
 // that last used a stage before storing into it, and drains a finished
