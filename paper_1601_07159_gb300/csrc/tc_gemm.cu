@@ -19,8 +19,9 @@
 // below FP32 rounding).
 //
 // Per CTA (512 threads, one per SM): two 128 x TN FP32 accumulators in TMEM.
-// K runs in chunks of 32 real terms: the threads load the next chunk(s) into
-// registers while the current one is split and stored, in the canonical
+// K runs in chunks of 32 real terms: the threads split a chunk from registers
+// and store it (then fetch the next one into the same registers at TN = 192 /
+// 256; at TN = 128 two more chunks are already in flight), in the canonical
 // K-major no-swizzle layout (core matrices of 8 rows x 16 bytes; LBO = 128 B
 // between core matrices along K, SBO = 1024 B between 8-row groups; eight
 // consecutive threads fill one core matrix, so the 16-byte stores are free of
